@@ -1,0 +1,439 @@
+"""FP64 CPU oracle for diag(H(i w_k)^-1): the exact diagonal and the paper's
+Lanczos-based low-rank correction method (Carrier, Tang, Saad, Freericks,
+"Lanczos-based Low-Rank Correction Method for Solving the Dyson Equation in
+Inhomogeneous Dynamical Mean-Field Theory").
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product path may import or call
+this module: only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline
+leg use it.  It shares no code with the CUDA path; inputs come in as plain
+numpy arrays.
+
+Everything is complex128 / float64.  Library primitives used as single steps:
+numpy matmul and numpy.linalg.inv for small dense blocks, numpy sqrt for the
+principal complex square root.  There is no blocking, fusion or reordering
+beyond what the paper's formulas state.
+
+Site order: natural, x fastest, i = x + Lx*(y + Ly*z).
+
+Readings of the paper taken here (the paper is silent or garbled there):
+  * H = z I + t A with A the nearest-neighbour adjacency and
+    z_i = i w + mu - V_i - Sigma_i(i w)                       (Eq. 1, Sec. 1 text)
+  * domain decomposition: the slowest axis is cut into p strips (2D) or
+    slabs (3D) separated by single interface lines/planes; the first
+    (L_slow - p + 1) mod p strips get one extra layer        (Sec. 2.2, Fig. 1)
+  * the start vector q1 is a caller-supplied real vector, normalised in the
+    bilinear form                                             (Sec. 2.3)
+  * diag(Q T Q^T) = sum_j alpha_j q_j*q_j + 2 sum_{j>=2} beta_j q_{j-1}*q_j
+    with T = tridiag(beta_j, alpha_j, beta_{j+1})             (Eq. 9 text)
+  * stop when |beta_{j+1}| <= 1e-12 max|T| (invariant subspace reached);
+    breakdown when |r^T r| <= 1e-14 ||r||_2^2                 (Sec. 2.1, 2.3)
+  * the H solve of Eq. 6 is a direct block-LU solve of the full lattice
+    (the paper does not say which solver it used).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+STATUS_OK = 0
+STATUS_TERMINATED = 1      # invariant subspace reached before the rank cap
+STATUS_BREAKDOWN = 2       # (r, r)_C vanished for a non-zero r
+
+# --------------------------------------------------------------------------
+# Lattice and the Dyson matrix  (Eq. 1 and the text that follows it)
+# --------------------------------------------------------------------------
+
+
+def site_count(L) -> int:
+    return int(np.prod(L))
+
+
+def dyson_diagonal(omega: float, mu: float, V: np.ndarray, sigma: np.ndarray) -> np.ndarray:
+    """H_ii(i w) = i w + mu - V_i - Sigma_i(i w)   (Eq. 1; Sec. 1, the noninteracting inverse)."""
+    return 1j * omega + mu - V - sigma
+
+
+def _axis_pairs(dims, periodic):
+    """Nearest-neighbour pairs (i, j) of a box with dims (first fastest)."""
+    n = int(np.prod(dims))
+    idx = np.arange(n).reshape(tuple(reversed(dims)))      # idx[..., x]
+    pairs = []
+    nd = len(dims)
+    for a in range(nd):
+        ax = nd - 1 - a                                     # numpy axis of dim a
+        lo = np.take(idx, np.arange(dims[a] - 1), axis=ax).ravel()
+        hi = np.take(idx, np.arange(1, dims[a]), axis=ax).ravel()
+        pairs.append(np.stack([lo, hi], 1))
+        if periodic[a]:
+            if dims[a] < 3:
+                raise ValueError("periodic axes need at least 3 sites")
+            lo = np.take(idx, [dims[a] - 1], axis=ax).ravel()
+            hi = np.take(idx, [0], axis=ax).ravel()
+            pairs.append(np.stack([lo, hi], 1))
+    return np.concatenate(pairs, 0) if pairs else np.zeros((0, 2), dtype=int)
+
+
+def adjacency(dims, periodic) -> np.ndarray:
+    """Dense 0/1 nearest-neighbour adjacency of a box (first dim fastest)."""
+    n = int(np.prod(dims))
+    A = np.zeros((n, n))
+    for i, j in _axis_pairs(list(dims), list(periodic)):
+        A[i, j] = 1.0
+        A[j, i] = 1.0
+    return A
+
+
+def dense_H(L, periodic, t: float, z: np.ndarray) -> np.ndarray:
+    """H_ij = t_ij + z_i delta_ij with t_ij = t on nearest neighbours (Eq. 1)."""
+    return np.diag(z).astype(np.complex128) + t * adjacency(L, periodic)
+
+
+# --------------------------------------------------------------------------
+# Dense inverse by LU with partial pivoting (the LAPACK route of Sec. 3,
+# written out) -- for small N only.
+# --------------------------------------------------------------------------
+
+
+def lu_factor(Ain: np.ndarray):
+    """Doolittle LU with row partial pivoting: P A = L U, stored in one array."""
+    A = np.array(Ain, dtype=np.complex128, copy=True)
+    n = A.shape[0]
+    perm = np.arange(n)
+    for k in range(n):
+        piv = k + int(np.argmax(np.abs(A[k:, k])))
+        if piv != k:
+            A[[k, piv]] = A[[piv, k]]
+            perm[[k, piv]] = perm[[piv, k]]
+        A[k + 1:, k] /= A[k, k]
+        A[k + 1:, k + 1:] -= np.outer(A[k + 1:, k], A[k, k + 1:])
+    return A, perm
+
+
+def lu_inverse(Ain: np.ndarray) -> np.ndarray:
+    """G = U^-1 L^-1 P: solve L U X = P I column block by forward/back substitution."""
+    LU, perm = lu_factor(Ain)
+    n = LU.shape[0]
+    X = np.eye(n, dtype=np.complex128)[perm]
+    for i in range(n):                      # forward: unit lower triangle
+        X[i] -= LU[i, :i] @ X[:i]
+    for i in range(n - 1, -1, -1):          # backward: upper triangle
+        X[i] = (X[i] - LU[i, i + 1:] @ X[i + 1:]) / LU[i, i]
+    return X
+
+
+def dense_diag_inverse(L, periodic, t, z) -> np.ndarray:
+    """diag(H^-1) from the dense LU inverse (Sec. 3, the original LAPACK route)."""
+    return np.diag(lu_inverse(dense_H(L, periodic, t, z))).copy()
+
+
+# --------------------------------------------------------------------------
+# Block-tridiagonal structure along x: slice s = all sites with x = s.
+# Within a slice the local index is j = y + Ly*z, so site = s + Lx*j.
+# Consecutive slices couple through t*I.
+# --------------------------------------------------------------------------
+
+
+def slice_blocks(Lx: int, trans_dims, periodic_trans, t: float, z_slices):
+    """D_s = diag(z on slice s) + t * (in-slice adjacency), s = 0..Lx-1."""
+    A = adjacency(trans_dims, periodic_trans)
+    return [np.diag(z_slices[s]).astype(np.complex128) + t * A for s in range(Lx)]
+
+
+def block_tridiag_factor(D, t: float):
+    """Left-connected inverses g_s = (D_s - t^2 g_{s-1})^-1 and diag(G_ss).
+
+    Backward pass G_ss = g_s + t^2 g_s G_{s+1,s+1} g_s (the recursion that
+    gives the diagonal blocks of a block-tridiagonal inverse; used for the
+    exact diagonal and for diag(B^-1), Sec. 2.3 after Eq. 8).
+    """
+    g = []
+    prev = None
+    for Ds in D:
+        A = Ds if prev is None else Ds - (t * t) * prev
+        prev = np.linalg.inv(A)
+        g.append(prev)
+    n = len(D)
+    diags = [None] * n
+    G = g[-1]
+    diags[-1] = np.diag(G).copy()
+    for s in range(n - 2, -1, -1):
+        G = g[s] + (t * t) * (g[s] @ G @ g[s])
+        diags[s] = np.diag(G).copy()
+    return g, diags
+
+
+def block_tridiag_solve(g, t: float, rhs):
+    """Block forward/back substitution with the stored g_s (rhs: list of slice vectors)."""
+    n = len(g)
+    y = [None] * n
+    prev = None
+    for s in range(n):
+        zs = rhs[s] if prev is None else rhs[s] - t * prev
+        prev = g[s] @ zs
+        y[s] = prev
+    x = [None] * n
+    x[-1] = y[-1]
+    for s in range(n - 2, -1, -1):
+        x[s] = y[s] - t * (g[s] @ x[s + 1])
+    return x
+
+
+def _check_x_open(periodic):
+    if periodic[0]:
+        raise ValueError("the slice recursion runs along x, which must be open")
+
+
+def exact_diag(L, periodic, t, z) -> np.ndarray:
+    """Exact diag(H^-1) by the full-lattice block-tridiagonal recursion along x."""
+    _check_x_open(periodic)
+    Lx = L[0]
+    trans = list(L[1:])
+    zz = np.asarray(z).reshape(-1, Lx)            # zz[j, x]
+    D = slice_blocks(Lx, trans, periodic[1:len(L)], t, [zz[:, s] for s in range(Lx)])
+    _, diags = block_tridiag_factor(D, t)
+    out = np.empty((zz.shape[0], Lx), dtype=np.complex128)
+    for s in range(Lx):
+        out[:, s] = diags[s]
+    return out.ravel()
+
+
+# --------------------------------------------------------------------------
+# Domain decomposition ordering (Sec. 2.2, Fig. 1; Eq. 3)
+# --------------------------------------------------------------------------
+
+
+def dd_partition(L, p: int):
+    """Split the slowest axis into p subdomains separated by p-1 single layers.
+
+    Returns (starts, heights, interface_layers): subdomain i covers slow
+    coordinates [starts[i], starts[i] + heights[i]); interface layer l sits
+    at slow coordinate interface_layers[l] between subdomains l and l+1.
+    The first (L_slow - p + 1) mod p subdomains get one extra layer.
+    """
+    Ls = L[-1]
+    if p < 1 or Ls - (p - 1) < p:
+        raise ValueError("too many subdomains for this lattice")
+    base, extra = divmod(Ls - (p - 1), p)
+    heights = [base + (1 if i < extra else 0) for i in range(p)]
+    starts, layers = [], []
+    c = 0
+    for i in range(p):
+        starts.append(c)
+        c += heights[i]
+        if i < p - 1:
+            layers.append(c)
+            c += 1
+    assert c == Ls
+    return starts, heights, layers
+
+
+def dd_sites(L, p: int):
+    """Natural indices in domain-decomposition order (Fig. 1 right).
+
+    Subdomain i lists its sites slice by slice (x = 0..Lx-1); inside a slice
+    the order is tr + T*sl, tr the transverse coordinate (y in 3D, absent in
+    2D, T = 1 then) and sl the slow coordinate relative to the subdomain
+    start.  Interface layers follow, each in order x + Lx*tr.
+    """
+    Lx = L[0]
+    T = 1 if len(L) == 2 else L[1]
+    A = Lx * T
+    starts, heights, layers = dd_partition(L, p)
+    sub = []
+    for i in range(p):
+        s0, h = starts[i], heights[i]
+        idx = np.empty((Lx, T * h), dtype=np.int64)
+        for x in range(Lx):
+            for sl in range(h):
+                for tr in range(T):
+                    idx[x, tr + T * sl] = x + Lx * tr + A * (s0 + sl)
+        sub.append(idx)
+    iface = [np.array([x + Lx * tr + A * yl for tr in range(T) for x in range(Lx)],
+                      dtype=np.int64) for yl in layers]
+    return sub, iface
+
+
+class Subdomains:
+    """The B blocks of Eq. 3: per-subdomain slice factors g_s and diag(B^-1)."""
+
+    def __init__(self, L, periodic, t, z, p):
+        _check_x_open(periodic)
+        if len(L) == 3 and periodic[2] and p > 1:
+            raise ValueError("the split axis must be open")
+        if len(L) == 2 and periodic[1] and p > 1:
+            raise ValueError("the split axis must be open")
+        self.L, self.t, self.p = L, t, p
+        self.sub, self.iface = dd_sites(L, p)
+        _, heights, _ = dd_partition(L, p)
+        Lx = L[0]
+        trans_p = [periodic[1]] if len(L) == 3 else []
+        slow_p = periodic[len(L) - 1] if p == 1 else False
+        self.g = []
+        self.diagB = np.zeros(site_count(L), dtype=np.complex128)
+        for i, idx in enumerate(self.sub):
+            dims = ([L[1]] if len(L) == 3 else []) + [heights[i]]
+            D = slice_blocks(Lx, dims, trans_p + [slow_p], t, [z[idx[s]] for s in range(Lx)])
+            g, diags = block_tridiag_factor(D, t)
+            self.g.append(g)
+            for s in range(Lx):
+                self.diagB[idx[s]] = diags[s]
+
+    def solve(self, q: np.ndarray) -> np.ndarray:
+        """w = blkdiag(B^-1, 0) q   (Eq. 7): subdomain solves, zero on the interface."""
+        w = np.zeros_like(q, dtype=np.complex128)
+        for g, idx in zip(self.g, self.sub):
+            x = block_tridiag_solve(g, self.t, [q[idx[s]] for s in range(idx.shape[0])])
+            for s in range(idx.shape[0]):
+                w[idx[s]] = x[s]
+        return w
+
+
+class FullLattice:
+    """Direct solver for H v = q (Eq. 6) by block LU along x of the whole lattice."""
+
+    def __init__(self, L, periodic, t, z):
+        _check_x_open(periodic)
+        self.L, self.t = L, t
+        Lx = L[0]
+        zz = np.asarray(z).reshape(-1, Lx)
+        D = slice_blocks(Lx, list(L[1:]), periodic[1:len(L)], t, [zz[:, s] for s in range(Lx)])
+        self.g, _ = block_tridiag_factor(D, t)
+
+    def solve(self, q: np.ndarray) -> np.ndarray:
+        Lx = self.L[0]
+        qq = np.asarray(q, dtype=np.complex128).reshape(-1, Lx)
+        x = block_tridiag_solve(self.g, self.t, [qq[:, s] for s in range(Lx)])
+        return np.stack(x, 1).ravel()
+
+
+# --------------------------------------------------------------------------
+# Complex-symmetric Lanczos in the bilinear form (Sec. 2.1 after Freund et al.;
+# Sec. 2.3 Eqs. 5, 9 and the stopping discussion)
+# --------------------------------------------------------------------------
+
+
+def cs_lanczos(matvec, q1, k_max: int, term_tol: float = 1e-12, brk_tol: float = 1e-14,
+               branch: int = 1):
+    """Lanczos on a complex-symmetric operator with (q, u)_C = q^T u.
+
+    Full re-orthogonalisation, classical Gram-Schmidt applied twice, in the
+    same bilinear form.  Accumulates diag(Q_k T_k Q_k^T) with the three-vector
+    update of Sec. 2.3 while the recurrence runs.
+
+    Returns (diag_QTQ, alphas, betas, Q, status) where betas[j] couples
+    q_{j+1} and q_{j+2} (0-based Q columns j and j+1).  branch = -1 takes the
+    other square root for every beta (the result must not change).
+    """
+    q1 = np.asarray(q1, dtype=np.complex128)
+    N = q1.shape[0]
+    acc = np.zeros(N, dtype=np.complex128)
+    alphas, betas = [], []
+    if k_max <= 0:
+        return acc, np.array(alphas), np.array(betas), np.zeros((N, 0), complex), STATUS_OK
+    Q = np.zeros((N, k_max + 1), dtype=np.complex128)
+    Q[:, 0] = q1 / np.sqrt(q1 @ q1)
+    beta_prev = 0.0
+    status = STATUS_OK
+    for j in range(k_max):
+        qj = Q[:, j]
+        u = matvec(qj)
+        a = qj @ u
+        r = u - a * qj
+        if j > 0:
+            r = r - beta_prev * Q[:, j - 1]
+        for _ in range(2):                       # CGS2 in the bilinear form
+            h = Q[:, :j + 1].T @ r
+            r = r - Q[:, :j + 1] @ h
+        acc += a * qj * qj
+        if j > 0:
+            acc += 2.0 * beta_prev * Q[:, j - 1] * qj
+        alphas.append(a)
+        rr = r @ r
+        b = branch * np.sqrt(rr)
+        maxT = max(max(abs(x) for x in alphas), max((abs(x) for x in betas), default=0.0))
+        if j == k_max - 1:
+            break
+        if abs(b) <= term_tol * maxT:
+            status = STATUS_TERMINATED
+            break
+        if abs(rr) <= brk_tol * np.vdot(r, r).real:
+            status = STATUS_BREAKDOWN
+            break
+        betas.append(b)
+        Q[:, j + 1] = r / b
+        beta_prev = b
+    steps = len(alphas)
+    return acc, np.array(alphas), np.array(betas), Q[:, :steps], status
+
+
+# --------------------------------------------------------------------------
+# The low-rank correction method (Sec. 2.3, Eqs. 4-9)
+# --------------------------------------------------------------------------
+
+
+def lowrank_diag(L, periodic, t, mu, V, sigma_k, omega_k, q1, p: int, k_max: int,
+                 return_info: bool = False):
+    """diag(H^-1) = diag(blkdiag(B^-1, 0)) + diag(Q_k T_k Q_k^T)   (Eq. 9).
+
+    X q = H^-1 q - blkdiag(B^-1, 0) q by one direct H solve and the
+    subdomain solves (Eqs. 6-8); p = 1 has no interface, X = 0 and the
+    result is the exact recursion.
+    """
+    z = dyson_diagonal(omega_k, mu, V, sigma_k)
+    subs = Subdomains(L, periodic, t, z, p)
+    if p == 1:
+        acc = np.zeros(site_count(L), dtype=np.complex128)
+        info = dict(alphas=np.zeros(0, complex), betas=np.zeros(0, complex), steps=0,
+                    status=STATUS_OK, diagB=subs.diagB)
+        return (subs.diagB + acc, info) if return_info else subs.diagB + acc
+    full = FullLattice(L, periodic, t, z)
+
+    def xmatvec(q):
+        v = full.solve(q)          # Eq. 6
+        w = subs.solve(q)          # Eq. 7
+        return v - w               # Eq. 8
+
+    acc, al, be, Q, status = cs_lanczos(xmatvec, q1, k_max)
+    res = subs.diagB + acc
+    if return_info:
+        return res, dict(alphas=al, betas=be, steps=len(al), status=status,
+                         diagB=subs.diagB, Q=Q)
+    return res
+
+
+def xmatvec(L, periodic, t, mu, V, sigma_k, omega_k, p, q):
+    """One X-'matvec' u = H^-1 q - blkdiag(B^-1, 0) q (Eqs. 6-8), natural order."""
+    z = dyson_diagonal(omega_k, mu, V, sigma_k)
+    subs = Subdomains(L, periodic, t, z, p)
+    full = FullLattice(L, periodic, t, z)
+    return full.solve(q) - subs.solve(q)
+
+
+def apply_H(L, periodic, t, mu, V, sigma_k, omega_k, x):
+    """y = H x by the stencil (Eq. 1), natural order, without forming H."""
+    z = dyson_diagonal(omega_k, mu, V, sigma_k)
+    y = z * x
+    for i, j in _axis_pairs(list(L), list(periodic[:len(L)])):
+        y[i] += t * x[j]
+        y[j] += t * x[i]
+    return y
+
+
+# --------------------------------------------------------------------------
+# Batched drivers over frequencies
+# --------------------------------------------------------------------------
+
+
+def exact_diag_batch(L, periodic, t, mu, V, sigma, omega):
+    return np.stack([exact_diag(L, periodic, t, dyson_diagonal(w, mu, V, sigma[k]))
+                     for k, w in enumerate(omega)])
+
+
+def lowrank_diag_batch(L, periodic, t, mu, V, sigma, omega, q1, p, k_max):
+    return np.stack([lowrank_diag(L, periodic, t, mu, V, sigma[k], w, q1, p, k_max)
+                     for k, w in enumerate(omega)])
+
+
+def subdomain_diag_batch(L, periodic, t, mu, V, sigma, omega, p):
+    """diag(blkdiag(B^-1, 0)) per frequency (Eq. 9 first term), natural order."""
+    return np.stack([Subdomains(L, periodic, t, dyson_diagonal(w, mu, V, sigma[k]), p).diagB
+                     for k, w in enumerate(omega)])

@@ -1,0 +1,389 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Every check here compares the oracle with something other than itself:
+a library dense inverse, a closed form, an exact identity of Sec. 2.2-2.3,
+the paper's worked example (tests/golden/fig1_5x5.json), or an invariant of
+the Lanczos recurrence.  No GPU is needed.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import dyson_oracle as O
+from paper_1102_3137_gb300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def rand_z(N, rng, omega=0.4, spread=3.0):
+    """An inhomogeneous Dyson diagonal with Im > 0 (random a_i, b_i, a trap-like real part)."""
+    return (rng.uniform(-spread, spread, N) + 1j * (omega + rng.uniform(0, 0.5, N)))
+
+
+# --------------------------------------------------------------------------- dense LU
+
+
+def test_hand_lu_inverse_matches_library():
+    rng = np.random.default_rng(0)
+    A = rng.normal(size=(40, 40)) + 1j * rng.normal(size=(40, 40))
+    G = O.lu_inverse(A)
+    ref = np.linalg.inv(A)
+    assert np.max(np.abs(G - ref)) / np.max(np.abs(ref)) < 1e-12
+
+
+def test_hand_lu_pivots_on_zero_leading_entry():
+    A = np.array([[0, 1, 2], [1, 0, 3], [4, -3, 8]], dtype=complex)
+    assert np.allclose(O.lu_inverse(A) @ A, np.eye(3), atol=1e-13)
+
+
+# ------------------------------------------------------------------ exact recursion
+
+
+@pytest.mark.parametrize("L,periodic", [
+    ((7, 6), (False, False, False)),
+    ((5, 6), (False, True, False)),
+    ((4, 3, 3), (False, False, False)),
+    ((3, 4, 3), (False, True, True)),
+    ((1, 9), (False, False, False)),
+    ((9, 1), (False, False, False)),
+])
+def test_exact_recursion_matches_dense_inverse(L, periodic):
+    rng = np.random.default_rng(1)
+    N = O.site_count(L)
+    z = rand_z(N, rng)
+    ref = np.diag(np.linalg.inv(O.dense_H(L, periodic, -1.0, z)))
+    got = O.exact_diag(L, periodic, -1.0, z)
+    assert np.max(np.abs(got - ref) / np.abs(ref)) < 1e-12
+    lu = O.dense_diag_inverse(L, periodic, -1.0, z)
+    assert np.max(np.abs(lu - ref) / np.abs(ref)) < 1e-12
+
+
+def _open_closed_form(L, t, z0):
+    """G_ii = sum_q prod_d (2/(L_d+1)) sin^2(q_d x_d) / (z0 + 2t sum_d cos q_d), x_d 1-based."""
+    ks = [np.pi * np.arange(1, n + 1) / (n + 1) for n in L]
+    xs = [np.arange(1, n + 1) for n in L]
+    # mode weights per axis: w_d[x, n] = 2/(L+1) sin^2(q_n x)
+    w = [2.0 / (n + 1) * np.sin(np.outer(x, k)) ** 2 for n, x, k in zip(L, xs, ks)]
+    out = np.zeros(tuple(reversed(L)), dtype=complex)
+    if len(L) == 2:
+        E = 2 * t * (np.cos(ks[0])[:, None] + np.cos(ks[1])[None, :])        # [nx, ny]
+        R = 1.0 / (z0 + E)
+        for y in range(L[1]):
+            for x in range(L[0]):
+                out[y, x] = np.sum(np.outer(w[0][x], w[1][y]) * R)
+    else:
+        E = 2 * t * (np.cos(ks[0])[:, None, None] + np.cos(ks[1])[None, :, None]
+                     + np.cos(ks[2])[None, None, :])
+        R = 1.0 / (z0 + E)
+        for zc in range(L[2]):
+            for y in range(L[1]):
+                for x in range(L[0]):
+                    out[zc, y, x] = np.einsum("a,b,c,abc->", w[0][x], w[1][y], w[2][zc], R)
+    return out.ravel()
+
+
+@pytest.mark.parametrize("L", [(7, 5), (4, 3, 5)])
+def test_exact_recursion_open_closed_form(L):
+    z0 = 0.3 + 0.25j
+    got = O.exact_diag(L, (False, False, False), -1.0, np.full(O.site_count(L), z0))
+    ref = _open_closed_form(L, -1.0, z0)
+    assert np.max(np.abs(got - ref) / np.abs(ref)) < 1e-12
+
+
+def test_periodic_closed_form_dense():
+    """Homogeneous periodic lattice: G_ii = (1/N) sum_q 1/(i w + mu - Sigma - eps_q)."""
+    L = (6, 5)
+    w, mu, sig = math.pi / 10, 0.2, 0.4 - 0.3j
+    z0 = 1j * w + mu - sig
+    t = -1.0
+    qs = [2 * np.pi * np.arange(n) / n for n in L]
+    eps = -2 * t * (np.cos(qs[0])[:, None] + np.cos(qs[1])[None, :])
+    ref = np.mean(1.0 / (z0 - eps))
+    got = O.dense_diag_inverse(L, (True, True, False), t, np.full(30, z0))
+    assert np.max(np.abs(got - ref) / abs(ref)) < 1e-12
+
+
+def test_transverse_periodic_closed_form_recursion():
+    """Open along x, periodic along y: sine modes in x times plane waves in y."""
+    Lx, Ly = 6, 5
+    z0 = -0.2 + 0.3j
+    t = -1.0
+    kx = np.pi * np.arange(1, Lx + 1) / (Lx + 1)
+    ky = 2 * np.pi * np.arange(Ly) / Ly
+    R = 1.0 / (z0 + 2 * t * (np.cos(kx)[:, None] + np.cos(ky)[None, :]))   # [nx, ny]
+    ref = np.array([np.sum(2.0 / (Lx + 1) * np.sin(kx * (x + 1)) ** 2 * R.mean(1))
+                    for x in range(Lx)])
+    got = O.exact_diag((Lx, Ly), (False, True, False), t, np.full(Lx * Ly, z0)).reshape(Ly, Lx)
+    for y in range(Ly):
+        assert np.max(np.abs(got[y] - ref) / np.abs(ref)) < 1e-12
+
+
+def test_zero_hopping_gives_local_inverse():
+    rng = np.random.default_rng(2)
+    z = rand_z(48, rng)
+    got = O.exact_diag((8, 6), (False, False, False), 0.0, z)
+    assert np.max(np.abs(got - 1 / z) / np.abs(1 / z)) < 1e-15
+
+
+def test_imaginary_part_negative_and_symmetric():
+    rng = np.random.default_rng(3)
+    L = (6, 6)
+    z = rand_z(36, rng)
+    G = O.lu_inverse(O.dense_H(L, (False,) * 3, -1.0, z))
+    assert np.all(np.diag(G).imag < 0)
+    assert np.max(np.abs(G - G.T)) < 1e-13 * np.max(np.abs(G))
+    assert np.all(O.exact_diag(L, (False,) * 3, -1.0, z).imag < 0)
+
+
+def test_large_frequency_limit():
+    L = (5, 4)
+    w = 1e4
+    omega, V, sigma, q1 = I.homogeneous_inputs(L, [w], 0.3 - 0.1j)
+    z = O.dyson_diagonal(w, 0.0, V, sigma[0])
+    G = O.exact_diag(L, (False,) * 3, -1.0, z)
+    assert np.max(np.abs(G * 1j * w - 1)) < 1e-3
+
+
+def test_stencil_matches_dense():
+    rng = np.random.default_rng(4)
+    L = (5, 4, 3)
+    N = 60
+    V = rng.uniform(0, 2, N)
+    sig = rng.normal(size=N) + 1j * rng.normal(size=N)
+    x = rng.normal(size=N) + 1j * rng.normal(size=N)
+    per = (True, False, True)
+    y = O.apply_H(L, per, -1.0, 0.1, V, sig, 0.7, x)
+    H = O.dense_H(L, per, -1.0, O.dyson_diagonal(0.7, 0.1, V, sig))
+    assert np.max(np.abs(y - H @ x)) < 1e-13
+
+
+# ------------------------------------------------------------------ decomposition
+
+
+@pytest.mark.parametrize("L,p,heights,m", [
+    ((16, 16), 2, [8, 7], 16),
+    ((128, 128), 4, [32, 31, 31, 31], 384),
+    ((32, 32, 32), 8, [4] + [3] * 7, 7168),
+    ((512, 512), 16, [32] + [31] * 15, 7680),
+    ((64, 64), 4, [16, 15, 15, 15], 192),
+])
+def test_partition_sizes(L, p, heights, m):
+    starts, h, layers = O.dd_partition(L, p)
+    assert h == heights
+    A = L[0] * (L[1] if len(L) == 3 else 1)
+    assert len(layers) * A == m
+    sub, iface = O.dd_sites(L, p)
+    allidx = np.concatenate([s.ravel() for s in sub] + list(iface))
+    assert np.array_equal(np.sort(allidx), np.arange(O.site_count(L)))
+
+
+def _dd_dense(L, p, z, t=-1.0):
+    sub, iface = O.dd_sites(L, p)
+    order = np.concatenate([s.ravel() for s in sub] + list(iface))
+    H = O.dense_H(L, (False,) * 3, t, z)[np.ix_(order, order)]
+    nb = sum(s.size for s in sub)
+    return H, order, nb, sub
+
+
+@pytest.mark.parametrize("L,p", [((6, 7), 2), ((5, 9), 3), ((3, 3, 5), 2)])
+def test_block_inverse_identity_and_rank(L, p):
+    """Eq. 5 and Eq. 6: H^-1 = blkdiag(B^-1,0) + [B^-1 E; -I] S^-1 [E^T B^-1, -I]; rank X = m."""
+    rng = np.random.default_rng(5)
+    z = rand_z(O.site_count(L), rng)
+    H, order, nb, sub = _dd_dense(L, p, z)
+    B, E, C = H[:nb, :nb], H[:nb, nb:], H[nb:, nb:]
+    # B has no coupling between different subdomains (Eq. 3)
+    off = 0
+    for s in sub:
+        n = s.size
+        assert np.all(B[off:off + n, :off] == 0) and np.all(B[off:off + n, off + n:] == 0)
+        off += n
+    Binv = np.linalg.inv(B)
+    S = C - E.T @ Binv @ E                                        # Eq. 4
+    Y = np.vstack([Binv @ E, -np.eye(C.shape[0])])
+    Hinv = np.linalg.inv(H)
+    base = np.zeros_like(H)
+    base[:nb, :nb] = Binv
+    X = Hinv - base                                                # Eq. 6
+    assert np.max(np.abs(X - Y @ np.linalg.inv(S) @ Y.T)) < 1e-12 * np.max(np.abs(Hinv))
+    sv = np.linalg.svd(X, compute_uv=False)
+    m = C.shape[0]
+    assert np.sum(sv > 1e-10 * sv[0]) == m
+    assert np.max(np.abs(X - X.T)) < 1e-13
+
+
+def test_subdomain_factors_match_dense_blocks():
+    rng = np.random.default_rng(6)
+    L, p = (7, 11), 3
+    z = rand_z(77, rng)
+    subs = O.Subdomains(L, (False,) * 3, -1.0, z, p)
+    H = O.dense_H(L, (False,) * 3, -1.0, z)
+    iface = np.concatenate(subs.iface)
+    mask = np.ones(77, bool)
+    mask[iface] = False
+    keep = np.where(mask)[0]
+    Binv = np.zeros((77, 77), complex)
+    Binv[np.ix_(keep, keep)] = np.linalg.inv(H[np.ix_(keep, keep)])
+    assert np.max(np.abs(subs.diagB - np.diag(Binv))) < 1e-13
+    q = rng.normal(size=77) + 1j * rng.normal(size=77)
+    assert np.max(np.abs(subs.solve(q) - Binv @ q)) < 1e-12
+    full = O.FullLattice(L, (False,) * 3, -1.0, z)
+    assert np.max(np.abs(full.solve(q) - np.linalg.solve(H, q))) < 1e-12
+
+
+# ------------------------------------------------------------------ Lanczos on X
+
+
+def _dense_X(H, interface):
+    n = H.shape[0]
+    keep = np.setdiff1d(np.arange(n), interface)
+    base = np.zeros_like(H)
+    base[np.ix_(keep, keep)] = np.linalg.inv(H[np.ix_(keep, keep)])
+    return np.linalg.inv(H) - base, base
+
+
+def test_fig1_worked_example():
+    """5x5 grid, four 2x2 subdomains, cross-shaped interface of 9 points (Fig. 1)."""
+    gold = json.load(open(os.path.join(GOLDEN, "fig1_5x5.json")))
+    Lx, Ly = gold["L"]
+    rng = np.random.default_rng(7)
+    z = rand_z(Lx * Ly, rng)
+    H = O.dense_H((Lx, Ly), (False,) * 3, -1.0, z)
+    interface = np.array(sorted({x + Lx * 2 for x in range(Lx)} | {2 + Lx * y for y in range(Ly)}))
+    assert interface.size == gold["interface_last_label"] - gold["interface_first_label"] + 1
+    keep = np.setdiff1d(np.arange(Lx * Ly), interface)
+    # the kept sites split into four decoupled 2x2 blocks
+    Hk = H[np.ix_(keep, keep)]
+    n_comp = 0
+    seen = set()
+    for a in range(keep.size):
+        if a in seen:
+            continue
+        n_comp += 1
+        stack = [a]
+        while stack:
+            c = stack.pop()
+            if c in seen:
+                continue
+            seen.add(c)
+            stack += [d for d in range(keep.size) if d != c and Hk[c, d] != 0]
+    assert n_comp == gold["subdomains"]
+    X, base = _dense_X(H, interface)
+    sv = np.linalg.svd(X, compute_uv=False)
+    assert np.sum(sv > 1e-10 * sv[0]) == gold["m"]
+    exact = np.diag(np.linalg.inv(H))
+    # a start vector inside range(X): the Krylov space closes after m steps
+    q1 = X @ rng.normal(size=25)
+    acc, al, be, Q, st = O.cs_lanczos(lambda q: X @ q, q1, 25)
+    assert st == O.STATUS_TERMINATED and len(al) == gold["lanczos_steps"]
+    assert np.max(np.abs(np.diag(base) + acc - exact) / np.abs(exact)) < 1e-11
+    # a generic real start vector needs at most one extra step
+    acc, al, be, Q, st = O.cs_lanczos(lambda q: X @ q, rng.uniform(-1, 1, 25), 25)
+    assert st == O.STATUS_TERMINATED and len(al) <= gold["lanczos_steps"] + 1
+    assert np.max(np.abs(np.diag(base) + acc - exact) / np.abs(exact)) < 1e-11
+
+
+def test_lanczos_invariants_truncated():
+    """Q^T Q = I and Q^T X Q = T in the bilinear form; the three-vector sum is diag(Q T Q^T)."""
+    rng = np.random.default_rng(8)
+    L, p = (10, 12), 3
+    z = rand_z(120, rng)
+    H, order, nb, sub = _dd_dense(L, p, z)
+    X, _ = _dense_X(H, np.arange(nb, 120))
+    k = 8
+    acc, al, be, Q, st = O.cs_lanczos(lambda q: X @ q, rng.uniform(-1, 1, 120), k)
+    assert Q.shape[1] == k and st == O.STATUS_OK
+    T = np.diag(al) + np.diag(be[:k - 1], 1) + np.diag(be[:k - 1], -1)
+    assert np.max(np.abs(Q.T @ Q - np.eye(k))) < 1e-10
+    assert np.max(np.abs(Q.T @ X @ Q - T)) < 1e-10 * np.max(np.abs(T))
+    assert np.max(np.abs(np.diag(Q @ T @ Q.T) - acc)) < 1e-13 * np.max(np.abs(acc))
+
+
+def test_lanczos_sqrt_branch_invariance():
+    rng = np.random.default_rng(9)
+    M = rng.normal(size=(30, 30)) + 1j * rng.normal(size=(30, 30))
+    X = M + M.T
+    q1 = rng.uniform(-1, 1, 30)
+    a1 = O.cs_lanczos(lambda q: X @ q, q1, 10)[0]
+    a2 = O.cs_lanczos(lambda q: X @ q, q1, 10, branch=-1)[0]
+    assert np.max(np.abs(a1 - a2)) < 1e-11 * np.max(np.abs(a1))
+
+
+def test_structured_xmatvec_matches_dense_X():
+    rng = np.random.default_rng(10)
+    L, p = (9, 10), 3
+    omega, V, sigma, q1 = I.make_inputs(I.Workload("t", L, -1.0, 0.0, 0.01, 0.5, 10.0, 2, p, 4, 3))
+    z = O.dyson_diagonal(omega[0], 0.0, V, sigma[0])
+    H = O.dense_H(L, (False,) * 3, -1.0, z)
+    _, iface = O.dd_sites(L, p)
+    X, _ = _dense_X(H, np.concatenate(iface))
+    q = rng.normal(size=90) + 1j * rng.normal(size=90)
+    u = O.xmatvec(L, (False,) * 3, -1.0, 0.0, V, sigma[0], omega[0], p, q)
+    assert np.max(np.abs(u - X @ q)) < 1e-12 * np.max(np.abs(X @ q))
+
+
+def test_lowrank_structured_equals_brute_force_truncated():
+    """Brute force: Lanczos on the explicitly formed dense X gives the same truncated diagonal."""
+    w = I.Workload("t", (12, 12), -1.0, 0.0, 0.01, 0.5, 10.0, 3, 2, 5, 11)
+    omega, V, sigma, q1 = I.make_inputs(w)
+    for k in range(w.K):
+        res, info = O.lowrank_diag(w.L, (False,) * 3, w.t, w.mu, V, sigma[k], omega[k], q1,
+                                   w.p, w.k, return_info=True)
+        z = O.dyson_diagonal(omega[k], w.mu, V, sigma[k])
+        H = O.dense_H(w.L, (False,) * 3, w.t, z)
+        _, iface = O.dd_sites(w.L, w.p)
+        X, base = _dense_X(H, np.concatenate(iface))
+        acc, al, be, Q, st = O.cs_lanczos(lambda q: X @ q, q1, w.k)
+        assert np.max(np.abs(al - info["alphas"])) < 1e-11 * np.max(np.abs(al))
+        assert np.max(np.abs(np.diag(base) + acc - res) / np.abs(res)) < 1e-11
+
+
+def test_lowrank_exact_after_termination():
+    """k >= m+1 on an inhomogeneous lattice: the correction is exact (Eq. 10, Eq. 9)."""
+    w = I.Workload("t", (16, 16), -1.0, 0.0, 0.01, 0.5, 10.0, 2, 2, 24, 1)
+    omega, V, sigma, q1 = I.make_inputs(w)
+    for k in range(w.K):
+        res, info = O.lowrank_diag(w.L, (False,) * 3, w.t, w.mu, V, sigma[k], omega[k], q1,
+                                   w.p, w.k, return_info=True)
+        z = O.dyson_diagonal(omega[k], w.mu, V, sigma[k])
+        ex = O.exact_diag(w.L, (False,) * 3, w.t, z)
+        assert info["status"] == O.STATUS_TERMINATED and info["steps"] <= 16 + 3
+        assert np.max(np.abs(res - ex) / np.abs(ex)) < 1e-10
+        # invariance in k once terminated
+        res2 = O.lowrank_diag(w.L, (False,) * 3, w.t, w.mu, V, sigma[k], omega[k], q1, w.p, 40)
+        assert np.max(np.abs(res2 - res) / np.abs(res)) < 1e-13
+
+
+def test_lowrank_single_domain_is_exact():
+    w = I.Workload("t", (8, 9), -1.0, 0.0, 0.01, 0.5, 10.0, 2, 1, 4, 5)
+    omega, V, sigma, q1 = I.make_inputs(w)
+    z = O.dyson_diagonal(omega[0], 0.0, V, sigma[0])
+    a = O.lowrank_diag(w.L, (False,) * 3, -1.0, 0.0, V, sigma[0], omega[0], q1, 1, 4)
+    assert np.max(np.abs(a - O.exact_diag(w.L, (False,) * 3, -1.0, z))) == 0.0
+
+
+def test_lowrank_3d_exact_after_termination():
+    w = I.Workload("t", (4, 4, 7), -1.0, 0.0, 0.005, 1.0, 40.0, 1, 2, 40, 3)
+    omega, V, sigma, q1 = I.make_inputs(w)
+    res, info = O.lowrank_diag(w.L, (False,) * 3, -1.0, 0.0, V, sigma[0], omega[0], q1, 2, 40,
+                               return_info=True)
+    z = O.dyson_diagonal(omega[0], 0.0, V, sigma[0])
+    ex = np.diag(np.linalg.inv(O.dense_H(w.L, (False,) * 3, -1.0, z)))
+    assert info["status"] == O.STATUS_TERMINATED and info["steps"] <= 16 + 3
+    assert np.max(np.abs(res - ex) / np.abs(ex)) < 1e-10
+
+
+def test_inputs_reproducible_and_physical():
+    w = I.WORKLOADS["square16_K8_p2_k16"]
+    a = I.make_inputs(w)
+    b = I.make_inputs(w)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+    omega, V, sigma, q1 = a
+    assert omega.shape == (8,) and np.allclose(omega, (2 * np.arange(8) + 1) * np.pi / 10)
+    assert V[0] == pytest.approx(0.01 * 2 * 7.5 ** 2)
+    z = 1j * omega[:, None] - V[None] - sigma
+    assert np.all(z.imag > 0)
