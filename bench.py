@@ -1,0 +1,368 @@
+#!/usr/bin/env python
+"""Benchmark: site-frequencies/s of diag(H(i w_k)^-1) by the Lanczos-based
+low-rank correction method on one GB300 (per GPU: one replica of the workload).
+
+Workload (default): 128x128 open square lattice, t = -1, mu = 0, trap
+V_i = 0.01 r_i^2, Sigma_i = a_i - i b_i sign(w_k) (a ~ U[-1,1], b ~ U[0,0.5]),
+64 Matsubara frequencies at beta = 20, p = 4 strip subdomains, Lanczos rank
+cap k = 32; all 64 frequencies in one batched, graph-replayed launch sequence.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--form mixed|fp64]
+    python bench.py --impl reference      # the FP64 CPU oracle on the host cores
+
+Prints ONE JSON line (rank 0).  A "step" is one full solve of all frequencies
+with inputs resident on the device; `e2e` repeats it through the C ABI with
+pinned host buffers, host<->device copies inside the timed region.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "site-frequencies/s for diag(H^-1) at ≤1e-6 rel err vs plain; p50/p99 solve latency"
+UNIT = "site-frequencies/s"
+DEFAULT_WORKLOAD = "square128_K64_p4_k32"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# FP64 peak of GB300: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz (the
+# nominal 1.25 TFLOP/s of the part).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+# ----------------------------------------------------------------- oracle timing
+def _oracle_freq(args):
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+    from oracle import dyson_oracle as O
+    from paper_1102_3137_gb300 import inputs as I
+    name, k = args
+    w = I.WORKLOADS[name]
+    omega, V, sigma, q1 = I.make_inputs(w)
+    t0 = time.perf_counter()
+    O.lowrank_diag(w.L, (False,) * 3, w.t, w.mu, V, sigma[k], omega[k], q1, w.p, w.k)
+    return time.perf_counter() - t0
+
+
+def oracle_rate(name, n_freq, procs):
+    """Time the oracle on n_freq frequencies spread over the grid, `procs` spawned workers."""
+    import multiprocessing as mp
+    from paper_1102_3137_gb300 import inputs as I
+    w = I.WORKLOADS[name]
+    ks = sorted({int(round(x)) for x in
+                 [i * (w.K - 1) / max(1, n_freq - 1) for i in range(n_freq)]})
+    for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(processes=procs) as pool:
+        per = pool.map(_oracle_freq, [(name, k) for k in ks])
+    wall = time.perf_counter() - t0
+    return dict(value=len(ks) * w.N / wall, unit=UNIT, cores=procs, kind="oracle",
+                sample=f"{len(ks)} of {w.K} frequencies (k = {ks[0]}..{ks[-1]}), full "
+                       f"{'x'.join(map(str, w.L))} lattice, wall {wall:.2f} s, "
+                       f"per-frequency CPU {statistics.mean(per):.2f} s",
+                wall_s=wall)
+
+
+# ----------------------------------------------------------------- clocks
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.idx = gpu_index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as f:
+            for line in f:
+                c = [x.strip() for x in line.split(",")]
+                if len(c) >= 9:
+                    rows.append(c)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = max(float(r[2]) for r in rows if r[2].replace(".", "").isdigit())
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return dict(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=mx, reasons=reasons,
+                    samples=len(rows),
+                    power_w_max=max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit()))
+
+
+# ----------------------------------------------------------------- our arm
+def run_ours(a, rank, world, local_rank):
+    import numpy as np
+    import torch
+    from paper_1102_3137_gb300 import build as B
+    from paper_1102_3137_gb300 import dyson as D
+    from paper_1102_3137_gb300 import inputs as I
+
+    if rank == 0:
+        B.build()
+    if world > 1:
+        torch.distributed.barrier()
+    D.load()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = I.WORKLOADS[a.workload]
+    omega, V, sigma, q1 = I.make_inputs(w, seed=w.seed + rank)
+    t = lambda x: torch.from_numpy(x).to(dev)
+    om, Vd, sg, qd = t(omega), t(V), t(sigma), t(q1)
+    prec = D.DYSON_MIXED if a.form == "mixed" else D.DYSON_FP64
+    stream = torch.cuda.current_stream(dev)
+    ss = stream.cuda_stream
+
+    # CPU baseline first (spawned pool, before the first CUDA call of the workload)
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        cpu = oracle_rate(a.workload, a.cpu_freqs, min(a.cpu_freqs, os.cpu_count() or 1))
+
+    plan = D.Plan(w.L, w.t, w.mu, w.p, w.k, prec, max_freqs=w.K)
+    D.dyson_plan_set_profiling(plan.handle, 1)
+    out = torch.zeros((w.K, w.N), dtype=torch.complex128, device=dev)
+    st = torch.zeros(w.K, dtype=torch.int32, device=dev)
+
+    def step():
+        D.dyson_solve(plan.handle, w.K, om, Vd, sg, qd, out, st, ss)
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = Clocks(local_rank) if rank == 0 else None
+    if clocks:
+        clocks.start()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps + 1)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    evs[0].record(stream)
+    for i in range(a.steps):
+        step()
+        evs[i + 1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop() if clocks else None
+    step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(a.steps)]
+    total_ms = evs[0].elapsed_time(evs[-1])
+    if world > 1:
+        tt = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    ms_per_step = total_ms / a.steps
+    value = world * w.K * w.N / (ms_per_step / 1e3)
+
+    # kernel profile of the last timed step (events captured inside the graph)
+    kinds, kms = D.dyson_profile_read(plan.handle)
+    n_launch = len(kinds)
+    sweeps = D.dyson_work_counters(plan.handle, w.K, w.p)
+    info = plan.info(w.K)
+    status = st.cpu().numpy()
+    res = out.cpu().numpy()
+    xm = kms[kinds == 3]
+    heights, _, _ = D.dyson_partition(plan.geom)
+    T = 1 if len(w.L) == 2 else w.L[1]
+    wi = np.array([T * h for h in heights], dtype=np.float64)
+    cs = 8 if prec == D.DYSON_MIXED else 16
+    # algorithmic work of one sweep of subdomain i: g_s read twice (forward, back),
+    # Lx blocks of w_i x w_i complex entries; 8 real flops per complex multiply-add.
+    sw_bytes = float((sweeps.astype(np.float64) * (2 * w.L[0] * wi * wi * cs)[None, :]).sum())
+    sw_flops = float((sweeps.astype(np.float64) * (2 * w.L[0] * wi * wi * 8)[None, :]).sum())
+    n_xm = max(1, len(xm))
+    hbm_peak, peak_src = peaks()
+    xm_avg_ms = float(xm.mean()) if len(xm) else float("nan")
+    if prec == D.DYSON_MIXED:
+        ach = sw_bytes / n_xm / (xm_avg_ms / 1e3) / 1e9
+        roof = dict(bound="hbm", achieved=ach, peak=hbm_peak, unit="GB/s", frac=ach / hbm_peak,
+                    traffic=None, kernel="k_xmatvec<float>", peak_source=peak_src,
+                    per_launch_algorithmic_bytes=sw_bytes / n_xm)
+    else:
+        ach = sw_flops / n_xm / (xm_avg_ms / 1e3) / 1e12
+        roof = dict(bound="alu", achieved=ach, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
+                    frac=ach / FP64_PEAK_TFLOPS, traffic=None, kernel="k_xmatvec<double>",
+                    peak_source="derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
+                    per_launch_algorithmic_flops=sw_flops / n_xm)
+    roof["share_of_step"] = float(xm.sum() / kms.sum()) if len(kms) else None
+    phases = {D.KERNEL_NAMES[int(k)]: round(float(kms[kinds == k].sum()), 3) for k in sorted(set(kinds))}
+
+    extra = {}
+    if rank == 0 and world == 1 and not a.quick:
+        # error vs the plain FP64 GPU method (the metric's condition) and its throughput
+        pf = D.Plan(w.L, w.t, w.mu, w.p, w.k, D.DYSON_FP64, max_freqs=w.K)
+        outf = torch.zeros_like(out)
+        stf = torch.zeros_like(st)
+        D.dyson_solve(pf.handle, w.K, om, Vd, sg, qd, outf, stf, ss)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        nf = 2
+        e0.record(stream)
+        for _ in range(nf):
+            D.dyson_solve(pf.handle, w.K, om, Vd, sg, qd, outf, stf, ss)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_f = e0.elapsed_time(e1) / nf
+        plain = outf.cpu().numpy()
+        rel = np.abs(res - plain) / np.abs(plain)
+        extra["err_vs_plain"] = dict(max=float(rel.max()), median=float(np.median(rel)))
+        extra["fp64_plain"] = dict(value=w.K * w.N / (ms_f / 1e3), ms_per_step=ms_f)
+        pf.close()
+        # one frequency per launch vs all frequencies in one batch (same form)
+        p1 = D.Plan(w.L, w.t, w.mu, w.p, w.k, prec, max_freqs=1)
+        o1 = torch.zeros((1, w.N), dtype=torch.complex128, device=dev)
+        s1 = torch.zeros(1, dtype=torch.int32, device=dev)
+        D.dyson_solve(p1.handle, 1, om[:1], Vd, sg[:1], qd, o1, s1, ss)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for k in range(w.K):
+            D.dyson_solve(p1.handle, 1, om[k:k + 1], Vd, sg[k:k + 1], qd, o1, s1, ss)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms1 = e0.elapsed_time(e1)
+        extra["one_frequency_per_launch"] = dict(value=w.K * w.N / (ms1 / 1e3), ms_all=ms1)
+        p1.close()
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    if True:
+        pin = lambda x: torch.from_numpy(x).pin_memory().numpy()
+        h_om, h_V, h_sg, h_q = pin(omega), pin(V), pin(sigma), pin(q1)
+        h_out = torch.zeros((w.K, w.N), dtype=torch.complex128).pin_memory().numpy()
+        h_st = torch.zeros(w.K, dtype=torch.int32).pin_memory().numpy()
+        D.dyson_solve(plan.handle, w.K, h_om, h_V, h_sg, h_q, h_out, h_st, ss)
+        n_e2e = max(2, a.steps // 2)
+        if world > 1:
+            torch.distributed.barrier()
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            D.dyson_solve(plan.handle, w.K, h_om, h_V, h_sg, h_q, h_out, h_st, ss)
+        e2e_s = (time.perf_counter() - t0) / n_e2e
+        if world > 1:
+            tt = torch.tensor([e2e_s], device=dev)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            e2e_s = float(tt.item())
+        e2e = dict(value=world * w.K * w.N / e2e_s, unit=UNIT,
+                   h2d_bytes_per_step=int(h_om.nbytes + h_V.nbytes + h_sg.nbytes + h_q.nbytes),
+                   d2h_bytes_per_step=int(h_out.nbytes + h_st.nbytes), ms_per_step=e2e_s * 1e3)
+    plan.close()
+    if rank != 0:
+        return None
+    sl = sorted(step_ms)
+    pct = lambda q: sl[min(len(sl) - 1, int(math.ceil(q * len(sl))) - 1)]
+    line = dict(
+        metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=a.steps, warmup=a.warmup,
+        ms_per_step=ms_per_step, higher_is_better=True, scaling="weak", vs_baseline=None,
+        dtype="mixed c64/f64" if prec == D.DYSON_MIXED else "c128 (f64)",
+        data="synthetic",
+        config=dict(workload=a.workload, lattice="x".join(map(str, w.L)), K=w.K, p=w.p, k=w.k,
+                    form=a.form, N=w.N, beta=w.beta,
+                    l2="per-step working set > L2: factors + Lanczos basis ~1 GB, no flush",
+                    parallelism=f"replicas x{world}"),
+        latency_ms=dict(p50=pct(0.50), p99=pct(0.99)),
+        roofline=roof, phases_ms_last_step=phases,
+        inner_iterations_per_solve=float(np.mean(info["iters"]) / max(1, w.k)),
+        status_flags=sorted({int(x) for x in status}),
+        cpu_baseline=({k: v for k, v in cpu.items() if k != "wall_s"} if cpu else None),
+        e2e=e2e, gpu_launches=int(n_launch * a.steps), clocks=clk,
+        **extra)
+    return line
+
+
+# ----------------------------------------------------------------- reference arm
+def run_reference(a, rank, world):
+    if rank != 0:
+        return None
+    from paper_1102_3137_gb300 import inputs as I
+    w = I.WORKLOADS[a.workload]
+    procs = min(a.cpu_freqs, os.cpu_count() or 1)
+    if a.warmup > 0:                      # page in numpy/oracle in the workers once
+        oracle_rate(a.workload, 2, min(2, procs))
+    vals = []
+    for _ in range(a.steps):
+        vals.append(oracle_rate(a.workload, a.cpu_freqs, procs))
+    value = statistics.mean(v["value"] for v in vals)
+    ms = statistics.mean(v["wall_s"] for v in vals) * 1e3
+    c = vals[-1]
+    return dict(
+        impl="reference", metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=a.steps,
+        warmup=a.warmup, ms_per_step=ms, higher_is_better=True, scaling="weak", vs_baseline=None,
+        dtype="c128 (f64)", data="synthetic",
+        config=dict(workload=a.workload, lattice="x".join(map(str, w.L)), K=w.K, p=w.p, k=w.k,
+                    form="fp64 oracle", N=w.N, beta=w.beta,
+                    step=f"{a.cpu_freqs} of {w.K} frequencies per step (bounded CPU sample)"),
+        cpu_baseline=dict(value=value, unit=UNIT, cores=procs, kind="oracle", sample=c["sample"]),
+        e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0),
+        gpu_launches=0)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--form", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--cpu-freqs", type=int, default=16)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="skip the plain-FP64 and per-launch extras")
+    a = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        line = run_reference(a, rank, world)
+    else:
+        if world > 1:
+            import torch
+            torch.cuda.set_device(local_rank)
+            torch.distributed.init_process_group("nccl")
+        line = run_ours(a, rank, world, local_rank)
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

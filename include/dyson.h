@@ -1,0 +1,231 @@
+/*
+ * dyson.h -- C ABI of the GB300 solver for the diagonal of the lattice
+ * Green's function of inhomogeneous DMFT,
+ *
+ *     G_ii(i w_k) = [H(i w_k)^-1]_ii,
+ *     H_ij(i w_k) = t_ij + (i w_k + mu - V_i - Sigma_i(i w_k)) delta_ij,
+ *
+ * (Eq. 1 of Carrier, Tang, Saad, Freericks, "Lanczos-based Low-Rank Correction
+ * Method for Solving the Dyson Equation in Inhomogeneous Dynamical Mean-Field
+ * Theory", and the text after it: t_ij = t on nearest neighbours of a square
+ * or simple-cubic lattice, H complex symmetric with real off-diagonals; only
+ * diag(G) is wanted, Sec. 1 end).  The diagonal is computed by the paper's
+ * Lanczos-based low-rank correction method (Sec. 2.3, Eqs. 5-9):
+ *
+ *     diag(H^-1) = diag(blkdiag(B^-1, 0)) + diag(Q_k T_k Q_k^T),
+ *
+ * B the subdomain blocks of the domain-decomposition ordering (Sec. 2.2,
+ * Eq. 3) and Q_k T_k Q_k^T the rank-k complex-symmetric Lanczos
+ * approximation of X = H^-1 - blkdiag(B^-1, 0) (Eq. 6, Eq. 10).
+ *
+ * Conventions shared by every call
+ *   - Sites are in natural order, x fastest: i = x + Lx*(y + Ly*z).
+ *   - Complex numbers are interleaved (re, im) pairs of double (layout of
+ *     C99 double _Complex); "complex[K][N]" is K*N such pairs, row-major.
+ *   - Boundaries are open on every axis.
+ *   - Domain decomposition: the slowest axis (y in 2D, z in 3D) is cut into
+ *     p strips/slabs separated by p-1 single interface lines/planes; the first
+ *     (L_slow - p + 1) mod p strips are one layer taller.  m = (p-1)*(sites
+ *     per layer) interface sites.  p = 1 means no interface: the result is the
+ *     exact diagonal.
+ *   - mem_kind says where the caller's buffers live: DYSON_MEM_HOST (plain or
+ *     pinned host memory; the call copies in, computes, copies out and returns
+ *     after the stream has finished) or DYSON_MEM_DEVICE (device pointers on
+ *     the plan's device; the call only enqueues work on `stream` and returns).
+ *   - stream is a cudaStream_t (NULL = the legacy default stream).
+ *   - Ownership: the caller owns every buffer it passes and keeps it valid
+ *     until the work on `stream` has finished; the library borrows inputs
+ *     for the duration of the call and never frees them.  A plan owns its
+ *     device workspace (factors, Lanczos vectors, scratch).
+ *   - Errors: every call returns DYSON_OK (0) or a negative DYSON_E_* code and
+ *     sets a thread-local message readable with dyson_last_error().  The
+ *     library never aborts the process and its kernels never trap.
+ */
+#ifndef DYSON_H
+#define DYSON_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define DYSON_OK 0
+#define DYSON_E_BAD_ARG (-1)      /* an argument is out of range or NULL */
+#define DYSON_E_OOM (-2)          /* device allocation failed */
+#define DYSON_E_CUDA (-3)         /* a CUDA runtime call failed */
+#define DYSON_E_UNSUPPORTED (-4)  /* valid input this build does not handle */
+#define DYSON_E_BUDGET (-5)       /* serving: request larger than the memory budget */
+#define DYSON_E_NOT_FOUND (-6)    /* serving: unknown ticket */
+
+/* per-frequency status flags, written to status[K] by dyson_solve */
+#define DYSON_ST_OK 0
+#define DYSON_ST_TERMINATED 1     /* Lanczos reached an invariant subspace before k_max: exact */
+#define DYSON_ST_BREAKDOWN 2      /* (r, r)_C vanished for r != 0 (Sec. 2.1); partial sum kept */
+#define DYSON_ST_NO_CONVERGENCE 4 /* an interface solve hit krylov_maxit */
+
+/* precision forms */
+#define DYSON_FP64 0   /* every step in complex128 */
+#define DYSON_MIXED 1  /* subdomain recursions and sweeps in complex64 with FP32 accumulation;
+                          Lanczos, re-orthogonalisation, the tridiagonal T_k and the
+                          iterative-refinement residuals in FP64 */
+
+#define DYSON_MEM_HOST 0
+#define DYSON_MEM_DEVICE 1
+
+typedef struct dyson_plan_s* dyson_plan;
+
+/* Lattice, physics constants and method sizes of one plan. */
+typedef struct {
+  int dim;            /* 2 (square lattice) or 3 (simple cubic) */
+  int L[3];           /* Lx, Ly, Lz; Lz ignored when dim == 2 */
+  double t;           /* nearest-neighbour hopping t_ij */
+  double mu;          /* chemical potential */
+  int p;              /* subdomains along the slowest axis, 1..16 */
+  int k_max;          /* Lanczos rank cap k, 1..256 (Sec. 2.3 stopping rule) */
+  int precision;      /* DYSON_FP64 or DYSON_MIXED */
+  double krylov_tol;  /* relative residual of each interface solve; 0 = default
+                         (1e-13 FP64, 1e-5 mixed inner solves) */
+  int krylov_maxit;   /* iteration cap of each interface solve; 0 = default (1000) */
+  double refine_tol;  /* mixed form: relative FP64 residual after refinement; 0 = 1e-13 */
+  int refine_max;     /* mixed form: most refinement passes per solve; 0 = default (6) */
+  int max_freqs;      /* most frequencies one dyson_solve call may carry (>= 1) */
+} dyson_geometry;
+
+/* Library version string. */
+const char* dyson_version(void);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* dyson_last_error(void);
+
+/*
+ * Domain-decomposition ordering (Sec. 2.2, Fig. 1 right; Eq. 3), host only,
+ * no GPU needed.  heights[p] receives the strip/slab heights along the slow
+ * axis; *m the number of interface sites; if dd2nat is not NULL it receives
+ * the natural site index of every slot of the internal subdomain-first
+ * vector layout (length *ndd, -1 on padding slots; call once with
+ * dd2nat = NULL to learn *ndd).
+ */
+int dyson_partition(const dyson_geometry* geom, int* heights, int* m, int* ndd, int* dd2nat);
+
+/* Device bytes a plan for `geom` allocates (for admission by memory footprint). */
+int dyson_plan_footprint(const dyson_geometry* geom, size_t* bytes);
+
+/*
+ * Create a plan on the current CUDA device: validates geom, builds the
+ * domain-decomposition maps and allocates all device workspace for up to
+ * geom->max_freqs frequencies.  *out is set on success.
+ */
+int dyson_plan_create(const dyson_geometry* geom, dyson_plan* out);
+
+/* Free a plan and its device memory (waits for its pending work). */
+int dyson_plan_destroy(dyson_plan plan);
+
+/*
+ * diag(G(i w_k)) for K frequencies (Eq. 1 solved by the method of Sec. 2.3):
+ *   omega  [K]         real Matsubara frequencies w_k
+ *   V      [N]         real local potential V_i
+ *   sigma  complex[K][N]  self-energy Sigma_i(i w_k)
+ *   q1     [N]         real Lanczos start vector (normalised internally in the
+ *                      bilinear form); the paper leaves it open
+ *   diagG  complex[K][N]  output G_ii(i w_k)
+ *   status [K]         output DYSON_ST_* flags per frequency (may be NULL)
+ * All frequencies run in one batch: one thread-block cluster per frequency
+ * with one CTA per subdomain, the whole sequence replayed from a CUDA graph.
+ * Frequencies are independent: a frequency's result does not depend on which
+ * other frequencies share the call.
+ */
+int dyson_solve(dyson_plan plan, int K, const double* omega, const double* V,
+                const double* sigma, const double* q1, double* diagG, int* status,
+                int mem_kind, void* stream);
+
+/*
+ * Diagnostics of the last dyson_solve on this plan (host buffers, each may be
+ * NULL; waits for the plan's work): alpha_beta complex[K][k_max][2] holds
+ * (alpha_j, beta_j) with beta_j coupling q_{j-1} and q_j (beta_1 = 0);
+ * steps[K] the Lanczos steps taken; iters[K] the interface Krylov iterations
+ * summed over all solves; refines[K] the refinement passes (mixed form).
+ */
+int dyson_solve_info(dyson_plan plan, int K, double* alpha_beta, int* steps, int* iters,
+                     int* refines);
+
+/*
+ * y = H(i w_k) x for K frequencies by the nearest-neighbour stencil (Eq. 1),
+ * H never stored.  x, y complex[K][N] (complex128).
+ */
+int dyson_apply_H(dyson_plan plan, int K, const double* omega, const double* V,
+                  const double* sigma, const double* x, double* y, int mem_kind, void* stream);
+
+/* The same product in complex64: x, y are interleaved float pairs [K][N]. */
+int dyson_apply_H_c64(dyson_plan plan, int K, const double* omega, const double* V,
+                      const double* sigma, const float* x, float* y, int mem_kind,
+                      void* stream);
+
+/*
+ * diag(blkdiag(B^-1, 0)) per frequency (the first term of Eq. 9; Sec. 2.3:
+ * computed once before the Lanczos steps) by the block-tridiagonal recursion
+ * of each subdomain.  diagB complex[K][N], zero on interface sites.  Runs in
+ * the plan's precision.
+ */
+int dyson_subdomain_diag(dyson_plan plan, int K, const double* omega, const double* V,
+                         const double* sigma, double* diagB, int mem_kind, void* stream);
+
+/* w = blkdiag(B^-1, 0) q (Eq. 7) for complex[K][N] q and w. */
+int dyson_subdomain_solve(dyson_plan plan, int K, const double* omega, const double* V,
+                          const double* sigma, const double* q, double* w, int mem_kind,
+                          void* stream);
+
+/*
+ * u = X q = H^-1 q - blkdiag(B^-1, 0) q, the modified Lanczos "matvec" of
+ * Eqs. 6-8, for complex[K][N] q and u.  FP64 form: u from the elimination
+ * y = S^-1 (E^T B^-1 q_B - q_C), u_B = B^-1 E y, u_C = -y, with S applied
+ * implicitly (never formed).  Mixed form: v = H^-1 q and w refined in FP64,
+ * u = v - w.
+ */
+int dyson_xmatvec(dyson_plan plan, int K, const double* omega, const double* V,
+                  const double* sigma, const double* q, double* u, int mem_kind, void* stream);
+
+/* Kernel kinds reported by dyson_profile_read. */
+#define DYSON_KERNEL_INIT 0      /* start vector, per-frequency state */
+#define DYSON_KERNEL_FACTOR 1    /* subdomain recursions: g_s and diag(B^-1) */
+#define DYSON_KERNEL_PRECOND 2   /* interface preconditioner factors */
+#define DYSON_KERNEL_XMATVEC 3   /* u = X q_j (Eqs. 6-8) */
+#define DYSON_KERNEL_LANCZOS 4   /* Lanczos step, CGS2, assembly (Eq. 9) */
+#define DYSON_KERNEL_FINALIZE 5  /* diag(G) to natural order */
+#define DYSON_KERNEL_STATUS 6    /* per-frequency status */
+
+/*
+ * Kernel timing.  With profiling on, dyson_solve brackets every kernel it
+ * launches with CUDA timing events on the stream the kernel runs on (inside
+ * the captured graph they become event-record nodes).  Switching it on or
+ * off drops the plan's cached graphs.  dyson_profile_read waits for the
+ * device and returns, for the most recent dyson_solve, *n kernels with their
+ * DYSON_KERNEL_* kind and duration in ms (at most max_kernels written).
+ */
+int dyson_plan_set_profiling(dyson_plan plan, int on);
+int dyson_profile_read(dyson_plan plan, int max_kernels, int* kinds, float* ms, int* n);
+
+/*
+ * Work accounting of the last dyson_solve: sweeps[K][p] receives the number
+ * of block forward/back substitutions (each reads the subdomain's stored
+ * g_s twice) that the CTA of subdomain i performed for frequency k.
+ * Waits for the device.
+ */
+int dyson_work_counters(dyson_plan plan, int K, unsigned long long* sweeps);
+
+/*
+ * Lanczos basis of frequency k (0-based) from the last dyson_solve, for
+ * checking the run step by step: Q complex[nvec][N] (host) receives q_1 ..
+ * q_nvec in natural order (bilinear-normalised, Sec. 2.1), nvec <= k_max+1;
+ * vectors past the last step taken are left over from earlier work.  Waits for
+ * the device; allocates a temporary device buffer.
+ */
+int dyson_lanczos_basis(dyson_plan plan, int k, int nvec, double* Q);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DYSON_H */

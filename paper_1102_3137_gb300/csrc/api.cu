@@ -1,0 +1,616 @@
+// Host side of the C ABI declared in include/dyson.h: argument checks, the
+// domain-decomposition maps (Sec. 2.2, Fig. 1 right), the plan's device
+// arena, and the solve sequence replayed from a captured CUDA graph:
+//   init -> factor (diag(B^-1), g_s) -> preconditioner ->
+//   k x [X-matvec -> Lanczos step + assembly] -> diag(G) out.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "dyson.h"
+#include "dyson_common.cuh"
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+#define CK(call)                                                                  \
+  do {                                                                            \
+    cudaError_t e_ = (call);                                                      \
+    if (e_ != cudaSuccess)                                                        \
+      return fail(DYSON_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+struct Part {
+  Geo g;
+  std::vector<int> dd2nat;
+  int m;
+};
+
+// Validate a geometry and build the subdomain-first ordering.
+int build_part(const dyson_geometry* in, Part* out, bool gpu) {
+  if (!in) return fail(DYSON_E_BAD_ARG, "geometry is NULL");
+  Geo g;
+  std::memset(&g, 0, sizeof(g));
+  if (in->dim != 2 && in->dim != 3) return fail(DYSON_E_BAD_ARG, "dim must be 2 or 3");
+  g.dim = in->dim;
+  g.Lx = in->L[0];
+  g.Ly = in->L[1];
+  g.Lz = in->dim == 3 ? in->L[2] : 1;
+  if (g.Lx < 1 || g.Ly < 1 || g.Lz < 1) return fail(DYSON_E_BAD_ARG, "lattice extents must be >= 1");
+  long long N = (long long)g.Lx * g.Ly * g.Lz;
+  if (N > (1LL << 30)) return fail(DYSON_E_UNSUPPORTED, "lattice too large");
+  g.N = (int)N;
+  g.p = in->p;
+  g.T = in->dim == 3 ? g.Ly : 1;
+  g.A = g.Lx * g.T;
+  g.Ls = in->dim == 3 ? g.Lz : g.Ly;
+  if (g.p < 1 || g.p > DY_MAXP) return fail(DYSON_E_BAD_ARG, "p must be in 1..16");
+  if (g.Ls - (g.p - 1) < g.p) return fail(DYSON_E_BAD_ARG, "too many subdomains for the slow axis");
+  const int base = (g.Ls - (g.p - 1)) / g.p, extra = (g.Ls - (g.p - 1)) % g.p;
+  int c = 0, hmax = 0;
+  for (int i = 0; i < g.p; ++i) {
+    g.h[i] = base + (i < extra ? 1 : 0);
+    g.s0[i] = c;
+    c += g.h[i];
+    if (g.h[i] > hmax) hmax = g.h[i];
+    if (i < g.p - 1) g.ylayer[i] = c++;
+  }
+  g.W = (g.T * hmax + 3) & ~3;   // multiple of 4: 16-byte aligned rows and bulk copies
+  if (gpu && g.W > DY_MAXW_SMEM)
+    return fail(DYSON_E_UNSUPPORTED, "slice width " + std::to_string(g.W) +
+                                         " exceeds 64 (shared-memory subdomain factorization)");
+  long long ndd = (long long)g.p * g.Lx * g.W + (long long)(g.p - 1) * g.A;
+  if (ndd > (1LL << 30)) return fail(DYSON_E_UNSUPPORTED, "lattice too large");
+  g.Ndd = (int)ndd;
+  g.ifc_off = g.p * g.Lx * g.W;
+  g.k_max = in->k_max;
+  if (g.k_max < 1 || g.k_max > 256) return fail(DYSON_E_BAD_ARG, "k_max must be in 1..256");
+  if (in->precision != DYSON_FP64 && in->precision != DYSON_MIXED)
+    return fail(DYSON_E_BAD_ARG, "precision must be DYSON_FP64 or DYSON_MIXED");
+  const bool mixed = in->precision == DYSON_MIXED;
+  g.t = in->t;
+  g.mu = in->mu;
+  g.krylov_tol = in->krylov_tol > 0 ? in->krylov_tol : (mixed ? 1e-5 : 1e-13);
+  g.krylov_maxit = in->krylov_maxit > 0 ? in->krylov_maxit : 1000;
+  g.refine_tol = in->refine_tol > 0 ? in->refine_tol : 1e-13;
+  g.refine_max = in->refine_max > 0 ? in->refine_max : 6;
+  if (in->max_freqs < 1 || in->max_freqs > 65535)
+    return fail(DYSON_E_BAD_ARG, "max_freqs must be in 1..65535");
+  out->dd2nat.assign(g.Ndd, -1);
+  for (int i = 0; i < g.p; ++i) {
+    const int w = g.T * g.h[i];
+    for (int s = 0; s < g.Lx; ++s)
+      for (int j = 0; j < w; ++j) {
+        int tr = j % g.T, sl = j / g.T;
+        out->dd2nat[(size_t)i * g.Lx * g.W + (size_t)s * g.W + j] =
+            s + g.Lx * tr + g.A * (g.s0[i] + sl);
+      }
+  }
+  for (int l = 0; l < g.p - 1; ++l)
+    for (int a = 0; a < g.A; ++a) out->dd2nat[(size_t)g.ifc_off + (size_t)l * g.A + a] = a + g.A * g.ylayer[l];
+  out->m = (g.p - 1) * g.A;
+  out->g = g;
+  return DYSON_OK;
+}
+
+enum {
+  B_V, B_OMEGA, B_SIGMA, B_Q1, B_DD2NAT, B_G, B_G64, B_DIAGB, B_Q, B_ACC, B_U, B_V1, B_V2, B_V3,
+  B_YSCR, B_BND, B_IFV, B_PRE, B_LAN, B_MAXT, B_ST, B_OUT, B_STATUS, B_SWEEPS, B_COUNT
+};
+
+size_t layout(const Geo& g, int K, bool mixed, size_t off[B_COUNT]) {
+  const size_t cs = mixed ? sizeof(cxf) : sizeof(cxd);
+  const size_t Kz = (size_t)K, Ndd = g.Ndd, nsub = (size_t)g.Lx * g.W;
+  size_t sz[B_COUNT];
+  sz[B_V] = g.N * sizeof(double);
+  sz[B_OMEGA] = Kz * sizeof(double);
+  sz[B_SIGMA] = Kz * g.N * sizeof(cxd);
+  sz[B_Q1] = g.N * sizeof(double);
+  sz[B_DD2NAT] = Ndd * sizeof(int);
+  sz[B_G] = Kz * g.p * nsub * g.W * cs;
+  sz[B_G64] = mixed ? Kz * g.p * nsub * g.W * sizeof(cxd) : 0;
+  sz[B_DIAGB] = Kz * Ndd * sizeof(cxd);
+  sz[B_Q] = Kz * (g.k_max + 1) * Ndd * sizeof(cxd);
+  sz[B_ACC] = Kz * Ndd * sizeof(cxd);
+  sz[B_U] = Kz * Ndd * sizeof(cxd);
+  sz[B_V1] = mixed ? Kz * Ndd * sizeof(cxd) : 0;
+  sz[B_V2] = sz[B_V1];
+  sz[B_V3] = sz[B_V1];
+  sz[B_YSCR] = Kz * g.p * nsub * cs;
+  sz[B_BND] = Kz * g.p * 2 * g.A * sizeof(cxd);
+  sz[B_IFV] = Kz * IF_N * nifc(g) * sizeof(cxd);
+  sz[B_PRE] = Kz * nifc(g) * 2 * sizeof(cxd);
+  sz[B_LAN] = Kz * (g.k_max + 1) * 2 * sizeof(cxd);
+  sz[B_MAXT] = Kz * sizeof(double);
+  sz[B_ST] = Kz * ST_N * sizeof(int);
+  sz[B_OUT] = Kz * g.N * sizeof(cxd);
+  sz[B_STATUS] = Kz * sizeof(int);
+  sz[B_SWEEPS] = Kz * g.p * sizeof(unsigned long long);
+  size_t o = 0;
+  for (int k = 0; k < B_COUNT; ++k) {
+    off[k] = o;
+    o += (sz[k] + 255) & ~(size_t)255;
+  }
+  return o;
+}
+
+}  // namespace
+
+struct dyson_plan_s {
+  dyson_geometry gi;
+  Geo g;
+  bool mixed;
+  int Kcap;
+  int device;
+  char* arena;
+  size_t bytes;
+  size_t off[B_COUNT];
+  Bufs b;
+  int* status_d;
+  cudaStream_t cap;
+  std::map<int, cudaGraphExec_t> graphs;
+  bool use_graph;
+  bool profile;                    // bracket every kernel with timing events
+  std::vector<cudaEvent_t> evs;    // 2 per profiled kernel
+  std::vector<int> ev_kind;        // DYSON_KERNEL_* of each profiled kernel
+  int n_prof;                      // profiled kernels in the last enqueued sequence
+};
+
+namespace {
+
+template <typename T>
+T* at(dyson_plan p, int k) { return reinterpret_cast<T*>(p->arena + p->off[k]); }
+
+int check_plan(dyson_plan p) {
+  if (!p) return fail(DYSON_E_BAD_ARG, "plan is NULL");
+  cudaError_t e = cudaSetDevice(p->device);
+  if (e != cudaSuccess) return fail(DYSON_E_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+  return DYSON_OK;
+}
+
+int check_K(dyson_plan p, int K) {
+  if (K < 1 || K > p->Kcap)
+    return fail(DYSON_E_BAD_ARG, "K must be in 1..max_freqs (" + std::to_string(p->Kcap) + ")");
+  return DYSON_OK;
+}
+
+int check_mem(int mem_kind) {
+  if (mem_kind != DYSON_MEM_HOST && mem_kind != DYSON_MEM_DEVICE)
+    return fail(DYSON_E_BAD_ARG, "mem_kind must be DYSON_MEM_HOST or DYSON_MEM_DEVICE");
+  return DYSON_OK;
+}
+
+// copy omega, V, sigma (and q1) into the plan's input buffers
+int stage_inputs(dyson_plan p, int K, const double* omega, const double* V, const double* sigma,
+                 const double* q1, cudaStream_t s) {
+  if (!omega || !V || !sigma) return fail(DYSON_E_BAD_ARG, "omega, V and sigma must not be NULL");
+  const Geo& g = p->g;
+  CK(cudaMemcpyAsync(at<double>(p, B_OMEGA), omega, K * sizeof(double), cudaMemcpyDefault, s));
+  CK(cudaMemcpyAsync(at<double>(p, B_V), V, g.N * sizeof(double), cudaMemcpyDefault, s));
+  CK(cudaMemcpyAsync(at<cxd>(p, B_SIGMA), sigma, (size_t)K * g.N * sizeof(cxd), cudaMemcpyDefault, s));
+  if (q1) CK(cudaMemcpyAsync(at<double>(p, B_Q1), q1, g.N * sizeof(double), cudaMemcpyDefault, s));
+  return DYSON_OK;
+}
+
+int finish(int mem_kind, cudaStream_t s) {
+  if (mem_kind == DYSON_MEM_HOST) CK(cudaStreamSynchronize(s));
+  else CK(cudaGetLastError());
+  return DYSON_OK;
+}
+
+#define LK(call)                                                                     \
+  do {                                                                               \
+    cudaError_t e_ = (call);                                                         \
+    if (e_ != cudaSuccess)                                                           \
+      return fail(DYSON_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+int enqueue_factor(dyson_plan p, int K, cudaStream_t s) {
+  if (p->mixed) LK((launch_factor<double, float>(p->g, p->b, K, s)));
+  else LK((launch_factor<double, double>(p->g, p->b, K, s)));
+  return DYSON_OK;
+}
+
+// Record a timing event on s; inside a stream capture it becomes an event-record
+// node of the graph, so replays time every kernel on the stream they run on.
+cudaError_t prof_event(dyson_plan p, int idx, cudaStream_t s, bool capturing) {
+  while ((int)p->evs.size() <= idx) {
+    cudaEvent_t e;
+    cudaError_t r = cudaEventCreate(&e);
+    if (r != cudaSuccess) return r;
+    p->evs.push_back(e);
+  }
+  return capturing ? cudaEventRecordWithFlags(p->evs[idx], s, cudaEventRecordExternal)
+                   : cudaEventRecord(p->evs[idx], s);
+}
+
+template <typename F>
+int run_kernel(dyson_plan p, int kind, cudaStream_t s, bool cap, const char* what, F&& f) {
+  if (p->profile) {
+    const int k = p->n_prof;
+    if ((int)p->ev_kind.size() <= k) p->ev_kind.resize(k + 1);
+    p->ev_kind[k] = kind;
+    LK(prof_event(p, 2 * k, s, cap));
+  }
+  cudaError_t e = f();
+  if (e != cudaSuccess) return fail(DYSON_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  if (p->profile) {
+    LK(prof_event(p, 2 * p->n_prof + 1, s, cap));
+    p->n_prof++;
+  }
+  return DYSON_OK;
+}
+
+#define RUN(kind, what, expr) \
+  do {                       \
+    int rc_ = run_kernel(p, kind, s, cap, what, [&]() { return (expr); }); \
+    if (rc_) return rc_;     \
+  } while (0)
+
+int enqueue_solve(dyson_plan p, int K, cudaStream_t s, bool cap) {
+  const Geo& g = p->g;
+  p->n_prof = 0;
+  RUN(DYSON_KERNEL_INIT, "init", launch_init(g, p->b, K, s));
+  if (p->mixed) RUN(DYSON_KERNEL_FACTOR, "factor", (launch_factor<double, float>(g, p->b, K, s)));
+  else RUN(DYSON_KERNEL_FACTOR, "factor", (launch_factor<double, double>(g, p->b, K, s)));
+  if (g.p > 1) RUN(DYSON_KERNEL_PRECOND, "precond", launch_precond(g, p->b, K, s));
+  if (g.p > 1) {
+    for (int j = 0; j < g.k_max; ++j) {
+      if (p->mixed) RUN(DYSON_KERNEL_XMATVEC, "xmatvec", launch_xmatvec<float>(g, p->b, K, j, 1, s));
+      else RUN(DYSON_KERNEL_XMATVEC, "xmatvec", launch_xmatvec<double>(g, p->b, K, j, 0, s));
+      RUN(DYSON_KERNEL_LANCZOS, "lanczos", launch_lanczos(g, p->b, K, j, s));
+    }
+  }
+  RUN(DYSON_KERNEL_FINALIZE, "finalize", launch_finalize(g, p->b, K, s));
+  RUN(DYSON_KERNEL_STATUS, "status", launch_status(g, p->b, K, p->status_d, s));
+  return DYSON_OK;
+}
+
+int get_graph(dyson_plan p, int K, cudaGraphExec_t* out) {
+  auto it = p->graphs.find(K);
+  if (it != p->graphs.end()) {
+    *out = it->second;
+    return DYSON_OK;
+  }
+  CK(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeRelaxed));
+  int rc = enqueue_solve(p, K, p->cap, true);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(p->cap, &graph);
+  if (rc) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e != cudaSuccess) return fail(DYSON_E_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+  cudaGraphExec_t exec;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return fail(DYSON_E_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+  p->graphs[K] = exec;
+  *out = exec;
+  return DYSON_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* dyson_version(void) { return "paper_1102_3137_gb300 0.1 (sm_103a)"; }
+
+const char* dyson_last_error(void) { return g_err.c_str(); }
+
+int dyson_partition(const dyson_geometry* geom, int* heights, int* m, int* ndd, int* dd2nat) {
+  Part part;
+  int rc = build_part(geom, &part, false);
+  if (rc) return rc;
+  if (heights)
+    for (int i = 0; i < part.g.p; ++i) heights[i] = part.g.h[i];
+  if (m) *m = part.m;
+  if (ndd) *ndd = part.g.Ndd;
+  if (dd2nat) std::memcpy(dd2nat, part.dd2nat.data(), part.dd2nat.size() * sizeof(int));
+  return DYSON_OK;
+}
+
+int dyson_plan_footprint(const dyson_geometry* geom, size_t* bytes) {
+  Part part;
+  int rc = build_part(geom, &part, true);
+  if (rc) return rc;
+  if (!bytes) return fail(DYSON_E_BAD_ARG, "bytes is NULL");
+  size_t off[B_COUNT];
+  *bytes = layout(part.g, geom->max_freqs, geom->precision == DYSON_MIXED, off);
+  return DYSON_OK;
+}
+
+int dyson_plan_create(const dyson_geometry* geom, dyson_plan* out) {
+  if (!out) return fail(DYSON_E_BAD_ARG, "out is NULL");
+  *out = nullptr;
+  Part part;
+  int rc = build_part(geom, &part, true);
+  if (rc) return rc;
+  dyson_plan p = new dyson_plan_s();
+  p->gi = *geom;
+  p->g = part.g;
+  p->mixed = geom->precision == DYSON_MIXED;
+  p->Kcap = geom->max_freqs;
+  p->use_graph = !(getenv("DYSON_NO_GRAPH") && getenv("DYSON_NO_GRAPH")[0] == '1');
+  cudaGetDevice(&p->device);
+  p->bytes = layout(p->g, p->Kcap, p->mixed, p->off);
+  cudaError_t e = cudaMalloc(&p->arena, p->bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    delete p;
+    return fail(DYSON_E_OOM, "cudaMalloc of " + std::to_string(p->bytes) + " bytes failed: " +
+                                 cudaGetErrorString(e));
+  }
+  e = cudaMemset(p->arena, 0, p->bytes);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(at<int>(p, B_DD2NAT), part.dd2nat.data(), part.dd2nat.size() * sizeof(int),
+                   cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    cudaFree(p->arena);
+    delete p;
+    return fail(DYSON_E_CUDA, std::string("plan set-up: ") + cudaGetErrorString(e));
+  }
+  Bufs& b = p->b;
+  b.V = at<double>(p, B_V);
+  b.omega = at<double>(p, B_OMEGA);
+  b.sigma = at<cxd>(p, B_SIGMA);
+  b.q1 = at<double>(p, B_Q1);
+  b.dd2nat = at<int>(p, B_DD2NAT);
+  b.g = at<void>(p, B_G);
+  b.g64 = p->mixed ? at<cxd>(p, B_G64) : nullptr;
+  b.diagB = at<cxd>(p, B_DIAGB);
+  b.Q = at<cxd>(p, B_Q);
+  b.acc = at<cxd>(p, B_ACC);
+  b.u = at<cxd>(p, B_U);
+  b.v1 = p->mixed ? at<cxd>(p, B_V1) : nullptr;
+  b.v2 = p->mixed ? at<cxd>(p, B_V2) : nullptr;
+  b.v3 = p->mixed ? at<cxd>(p, B_V3) : nullptr;
+  b.yscr = at<void>(p, B_YSCR);
+  b.bnd = at<cxd>(p, B_BND);
+  b.ifv = at<cxd>(p, B_IFV);
+  b.pre = at<cxd>(p, B_PRE);
+  b.lan = at<cxd>(p, B_LAN);
+  b.maxT = at<double>(p, B_MAXT);
+  b.st = at<int>(p, B_ST);
+  b.out = at<cxd>(p, B_OUT);
+  b.sweeps = at<unsigned long long>(p, B_SWEEPS);
+  p->status_d = at<int>(p, B_STATUS);
+  p->profile = false;
+  p->n_prof = 0;
+  *out = p;
+  return DYSON_OK;
+}
+
+int dyson_plan_destroy(dyson_plan p) {
+  if (!p) return DYSON_OK;
+  cudaSetDevice(p->device);
+  cudaDeviceSynchronize();
+  for (auto& kv : p->graphs) cudaGraphExecDestroy(kv.second);
+  for (auto e : p->evs) cudaEventDestroy(e);
+  cudaStreamDestroy(p->cap);
+  cudaFree(p->arena);
+  delete p;
+  return DYSON_OK;
+}
+
+int dyson_solve(dyson_plan p, int K, const double* omega, const double* V, const double* sigma,
+                const double* q1, double* diagG, int* status, int mem_kind, void* stream) {
+  int rc;
+  if ((rc = check_plan(p)) || (rc = check_K(p, K)) || (rc = check_mem(mem_kind))) return rc;
+  if (!q1 || !diagG) return fail(DYSON_E_BAD_ARG, "q1 and diagG must not be NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((rc = stage_inputs(p, K, omega, V, sigma, q1, s))) return rc;
+  if (p->use_graph) {
+    cudaGraphExec_t ex;
+    if ((rc = get_graph(p, K, &ex))) return rc;
+    CK(cudaGraphLaunch(ex, s));
+  } else if ((rc = enqueue_solve(p, K, s, false))) {
+    return rc;
+  }
+  CK(cudaMemcpyAsync(diagG, p->b.out, (size_t)K * p->g.N * sizeof(cxd), cudaMemcpyDefault, s));
+  if (status) CK(cudaMemcpyAsync(status, p->status_d, K * sizeof(int), cudaMemcpyDefault, s));
+  return finish(mem_kind, s);
+}
+
+int dyson_solve_info(dyson_plan p, int K, double* alpha_beta, int* steps, int* iters, int* refines) {
+  int rc;
+  if ((rc = check_plan(p)) || (rc = check_K(p, K))) return rc;
+  CK(cudaDeviceSynchronize());
+  const Geo& g = p->g;
+  std::vector<int> st((size_t)K * ST_N);
+  CK(cudaMemcpy(st.data(), p->b.st, st.size() * sizeof(int), cudaMemcpyDeviceToHost));
+  for (int k = 0; k < K; ++k) {
+    if (steps) steps[k] = st[(size_t)k * ST_N + ST_STEPS];
+    if (iters) iters[k] = st[(size_t)k * ST_N + ST_ITERS];
+    if (refines) refines[k] = st[(size_t)k * ST_N + ST_REFINE];
+  }
+  if (alpha_beta) {
+    std::vector<cxd> lan((size_t)K * (g.k_max + 1) * 2);
+    CK(cudaMemcpy(lan.data(), p->b.lan, lan.size() * sizeof(cxd), cudaMemcpyDeviceToHost));
+    for (int k = 0; k < K; ++k)
+      for (int j = 0; j < g.k_max; ++j)
+        for (int c = 0; c < 2; ++c) {
+          cxd v = lan[((size_t)k * (g.k_max + 1) + j) * 2 + c];
+          double* o = alpha_beta + (((size_t)k * g.k_max + j) * 2 + c) * 2;
+          o[0] = v.x;
+          o[1] = v.y;
+        }
+  }
+  return DYSON_OK;
+}
+
+int dyson_plan_set_profiling(dyson_plan p, int on) {
+  int rc;
+  if ((rc = check_plan(p))) return rc;
+  if (p->profile != (on != 0)) {
+    CK(cudaDeviceSynchronize());
+    for (auto& kv : p->graphs) cudaGraphExecDestroy(kv.second);
+    p->graphs.clear();
+    p->profile = on != 0;
+  }
+  return DYSON_OK;
+}
+
+int dyson_profile_read(dyson_plan p, int max_kernels, int* kinds, float* ms, int* n) {
+  int rc;
+  if ((rc = check_plan(p))) return rc;
+  if (!n) return fail(DYSON_E_BAD_ARG, "n is NULL");
+  if (!p->profile) return fail(DYSON_E_BAD_ARG, "profiling is off for this plan");
+  CK(cudaDeviceSynchronize());
+  *n = p->n_prof;
+  for (int k = 0; k < p->n_prof && k < max_kernels; ++k) {
+    if (kinds) kinds[k] = p->ev_kind[k];
+    if (ms) CK(cudaEventElapsedTime(&ms[k], p->evs[2 * k], p->evs[2 * k + 1]));
+  }
+  return DYSON_OK;
+}
+
+int dyson_lanczos_basis(dyson_plan p, int k, int nvec, double* Q) {
+  int rc;
+  if ((rc = check_plan(p))) return rc;
+  const Geo& g = p->g;
+  if (k < 0 || k >= p->Kcap) return fail(DYSON_E_BAD_ARG, "frequency index out of range");
+  if (nvec < 1 || nvec > g.k_max + 1) return fail(DYSON_E_BAD_ARG, "nvec must be in 1..k_max+1");
+  if (!Q) return fail(DYSON_E_BAD_ARG, "Q is NULL");
+  CK(cudaDeviceSynchronize());
+  const size_t bytes = (size_t)nvec * g.N * sizeof(cxd);
+  cxd* tmp = nullptr;
+  CK(cudaMalloc(&tmp, bytes));
+  const cxd* src = p->b.Q + (size_t)k * (g.k_max + 1) * g.Ndd;
+  cudaError_t e = launch_scatter(g, p->b, nvec, src, tmp, g.Ndd, 0);
+  if (e == cudaSuccess) e = cudaMemcpy(Q, tmp, bytes, cudaMemcpyDeviceToHost);
+  cudaFree(tmp);
+  if (e != cudaSuccess) return fail(DYSON_E_CUDA, std::string("basis copy: ") + cudaGetErrorString(e));
+  return DYSON_OK;
+}
+
+int dyson_work_counters(dyson_plan p, int K, unsigned long long* sweeps) {
+  int rc;
+  if ((rc = check_plan(p)) || (rc = check_K(p, K))) return rc;
+  if (!sweeps) return fail(DYSON_E_BAD_ARG, "sweeps is NULL");
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemcpy(sweeps, p->b.sweeps, (size_t)K * p->g.p * sizeof(unsigned long long),
+                cudaMemcpyDeviceToHost));
+  return DYSON_OK;
+}
+
+int dyson_apply_H(dyson_plan p, int K, const double* omega, const double* V, const double* sigma,
+                  const double* x, double* y, int mem_kind, void* stream) {
+  int rc;
+  if ((rc = check_plan(p)) || (rc = check_K(p, K)) || (rc = check_mem(mem_kind))) return rc;
+  if (!x || !y) return fail(DYSON_E_BAD_ARG, "x and y must not be NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((rc = stage_inputs(p, K, omega, V, sigma, nullptr, s))) return rc;
+  const size_t bytes = (size_t)K * p->g.N * sizeof(cxd);
+  const cxd* xd = reinterpret_cast<const cxd*>(x);
+  cxd* yd = reinterpret_cast<cxd*>(y);
+  if (mem_kind == DYSON_MEM_HOST) {
+    CK(cudaMemcpyAsync(p->b.u, x, bytes, cudaMemcpyHostToDevice, s));
+    xd = p->b.u;
+    yd = p->b.out;
+  }
+  LK(launch_spmv<double>(p->g, p->b.V, p->b.omega, p->b.sigma, xd, yd, K, s));
+  if (mem_kind == DYSON_MEM_HOST) CK(cudaMemcpyAsync(y, yd, bytes, cudaMemcpyDeviceToHost, s));
+  return finish(mem_kind, s);
+}
+
+int dyson_apply_H_c64(dyson_plan p, int K, const double* omega, const double* V,
+                      const double* sigma, const float* x, float* y, int mem_kind, void* stream) {
+  int rc;
+  if ((rc = check_plan(p)) || (rc = check_K(p, K)) || (rc = check_mem(mem_kind))) return rc;
+  if (!x || !y) return fail(DYSON_E_BAD_ARG, "x and y must not be NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((rc = stage_inputs(p, K, omega, V, sigma, nullptr, s))) return rc;
+  const size_t bytes = (size_t)K * p->g.N * sizeof(cxf);
+  const cxf* xd = reinterpret_cast<const cxf*>(x);
+  cxf* yd = reinterpret_cast<cxf*>(y);
+  if (mem_kind == DYSON_MEM_HOST) {
+    CK(cudaMemcpyAsync(p->b.u, x, bytes, cudaMemcpyHostToDevice, s));
+    xd = reinterpret_cast<const cxf*>(p->b.u);
+    yd = reinterpret_cast<cxf*>(p->b.out);
+  }
+  LK(launch_spmv<float>(p->g, p->b.V, p->b.omega, p->b.sigma, xd, yd, K, s));
+  if (mem_kind == DYSON_MEM_HOST) CK(cudaMemcpyAsync(y, yd, bytes, cudaMemcpyDeviceToHost, s));
+  return finish(mem_kind, s);
+}
+
+int dyson_subdomain_diag(dyson_plan p, int K, const double* omega, const double* V,
+                         const double* sigma, double* diagB, int mem_kind, void* stream) {
+  int rc;
+  if ((rc = check_plan(p)) || (rc = check_K(p, K)) || (rc = check_mem(mem_kind))) return rc;
+  if (!diagB) return fail(DYSON_E_BAD_ARG, "diagB must not be NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((rc = stage_inputs(p, K, omega, V, sigma, nullptr, s))) return rc;
+  if ((rc = enqueue_factor(p, K, s))) return rc;
+  cxd* dst = mem_kind == DYSON_MEM_HOST ? p->b.out : reinterpret_cast<cxd*>(diagB);
+  LK(launch_scatter(p->g, p->b, K, p->b.diagB, dst, p->g.Ndd, s));
+  if (mem_kind == DYSON_MEM_HOST)
+    CK(cudaMemcpyAsync(diagB, dst, (size_t)K * p->g.N * sizeof(cxd), cudaMemcpyDeviceToHost, s));
+  return finish(mem_kind, s);
+}
+
+int dyson_subdomain_solve(dyson_plan p, int K, const double* omega, const double* V,
+                          const double* sigma, const double* q, double* w, int mem_kind,
+                          void* stream) {
+  int rc;
+  if ((rc = check_plan(p)) || (rc = check_K(p, K)) || (rc = check_mem(mem_kind))) return rc;
+  if (!q || !w) return fail(DYSON_E_BAD_ARG, "q and w must not be NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((rc = stage_inputs(p, K, omega, V, sigma, nullptr, s))) return rc;
+  const size_t bytes = (size_t)K * p->g.N * sizeof(cxd);
+  const cxd* qn = reinterpret_cast<const cxd*>(q);
+  if (mem_kind == DYSON_MEM_HOST) {
+    CK(cudaMemcpyAsync(p->b.out, q, bytes, cudaMemcpyHostToDevice, s));
+    qn = p->b.out;
+  }
+  if ((rc = enqueue_factor(p, K, s))) return rc;
+  LK(launch_gather(p->g, p->b, K, qn, p->b.acc, p->g.Ndd, s));
+  if (p->mixed) LK(launch_bsolve<float>(p->g, p->b, K, p->b.acc, p->b.u, s));
+  else LK(launch_bsolve<double>(p->g, p->b, K, p->b.acc, p->b.u, s));
+  cxd* dst = mem_kind == DYSON_MEM_HOST ? p->b.out : reinterpret_cast<cxd*>(w);
+  LK(launch_scatter(p->g, p->b, K, p->b.u, dst, p->g.Ndd, s));
+  if (mem_kind == DYSON_MEM_HOST) CK(cudaMemcpyAsync(w, dst, bytes, cudaMemcpyDeviceToHost, s));
+  return finish(mem_kind, s);
+}
+
+int dyson_xmatvec(dyson_plan p, int K, const double* omega, const double* V, const double* sigma,
+                  const double* q, double* u, int mem_kind, void* stream) {
+  int rc;
+  if ((rc = check_plan(p)) || (rc = check_K(p, K)) || (rc = check_mem(mem_kind))) return rc;
+  if (!q || !u) return fail(DYSON_E_BAD_ARG, "q and u must not be NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((rc = stage_inputs(p, K, omega, V, sigma, nullptr, s))) return rc;
+  const Geo& g = p->g;
+  const size_t bytes = (size_t)K * g.N * sizeof(cxd);
+  const cxd* qn = reinterpret_cast<const cxd*>(q);
+  if (mem_kind == DYSON_MEM_HOST) {
+    CK(cudaMemcpyAsync(p->b.out, q, bytes, cudaMemcpyHostToDevice, s));
+    qn = p->b.out;
+  }
+  if ((rc = enqueue_factor(p, K, s))) return rc;
+  LK(launch_precond(g, p->b, K, s));
+  LK(launch_gather(g, p->b, K, qn, p->b.Q, (size_t)(g.k_max + 1) * g.Ndd, s));
+  CK(cudaMemsetAsync(p->b.st, 0, (size_t)K * ST_N * sizeof(int), s));
+  if (g.p > 1) {
+    if (p->mixed) LK(launch_xmatvec<float>(g, p->b, K, 0, 1, s));
+    else LK(launch_xmatvec<double>(g, p->b, K, 0, 0, s));
+  } else {
+    CK(cudaMemsetAsync(p->b.u, 0, (size_t)K * g.Ndd * sizeof(cxd), s));
+  }
+  cxd* dst = mem_kind == DYSON_MEM_HOST ? p->b.out : reinterpret_cast<cxd*>(u);
+  LK(launch_scatter(g, p->b, K, p->b.u, dst, g.Ndd, s));
+  if (mem_kind == DYSON_MEM_HOST) CK(cudaMemcpyAsync(u, dst, bytes, cudaMemcpyDeviceToHost, s));
+  return finish(mem_kind, s);
+}
+
+}  // extern "C"

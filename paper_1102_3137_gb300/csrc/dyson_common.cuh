@@ -1,0 +1,179 @@
+// Shared device-side definitions of the GB300 Dyson solver.
+//
+// Notation follows the low-rank correction method (Sec. 2.2-2.3): H is
+// ordered as [B E; E^T C] with p subdomains (strips in 2D, slabs in 3D) cut
+// along the slowest axis by p-1 single interface layers.  Inside a subdomain
+// the sites are sliced along x; slice s holds the w = T*h sites with that x,
+// local index j = tr + T*sl (tr: transverse coordinate, y in 3D, T = 1 in 2D;
+// sl: slow coordinate inside the subdomain).  Consecutive slices couple
+// through t*I, so every subdomain block B_i is block tridiagonal.
+//
+// Internal vector layout ("DD layout", per frequency):
+//   [subdomain 0: Lx slices x W][subdomain 1] ... [subdomain p-1]
+//   [interface layer 0: A = Lx*T sites, index x + Lx*tr] ... [layer p-2]
+// W is the slice width padded to the widest subdomain; padded entries are 0.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#define DY_MAXP 16          // largest cluster (one CTA per subdomain)
+#define DY_THREADS 256      // threads per CTA of every solver kernel
+#define DY_WARPS (DY_THREADS / 32)
+#define DY_MAXW 256         // widest slice the sweep kernels take
+#define DY_MAXW_SMEM 64     // widest slice the shared-memory factor kernel takes
+
+// per-frequency state words
+enum {
+  ST_DONE = 0,       // Lanczos finished for this frequency
+  ST_STATUS = 1,     // DYSON_ST_* flags
+  ST_STEPS = 2,      // Lanczos steps taken
+  ST_ITERS = 3,      // interface Krylov iterations, summed over all solves
+  ST_SOLVES = 4,     // interface solves performed
+  ST_REFINE = 5,     // refinement passes (mixed form)
+  ST_N = 8
+};
+
+// ---------------------------------------------------------------- complex
+template <typename R>
+struct alignas(2 * sizeof(R)) cx {
+  R x, y;
+};
+using cxd = cx<double>;
+using cxf = cx<float>;
+
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> mk(R a, R b) { return cx<R>{a, b}; }
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> operator+(cx<R> a, cx<R> b) { return {a.x + b.x, a.y + b.y}; }
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> operator-(cx<R> a, cx<R> b) { return {a.x - b.x, a.y - b.y}; }
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> operator-(cx<R> a) { return {-a.x, -a.y}; }
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> operator*(cx<R> a, cx<R> b) {
+  return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> operator*(R s, cx<R> a) { return {s * a.x, s * a.y}; }
+// acc + a*b with fused multiply-adds
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> cfma(cx<R> a, cx<R> b, cx<R> acc) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+  return acc;
+}
+template <typename R>
+__host__ __device__ __forceinline__ R cabs2(cx<R> a) { return a.x * a.x + a.y * a.y; }
+// 1/a = conj(a)/|a|^2
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> cinv(cx<R> a) {
+  R d = a.x * a.x + a.y * a.y;
+  return {a.x / d, -a.y / d};
+}
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> cdiv(cx<R> a, cx<R> b) { return a * cinv(b); }
+// principal square root: Re >= 0, branch cut on the negative real axis with the
+// sign of the imaginary part (+0 or -0) selecting the side.
+__host__ __device__ __forceinline__ cxd csqrt_principal(cxd z) {
+  double r = sqrt(z.x * z.x + z.y * z.y);
+  if (r == 0.0) return {0.0, z.y};
+  if (z.x >= 0.0) {
+    double s = sqrt(0.5 * (r + z.x));
+    return {s, z.y / (2.0 * s)};
+  }
+  double s = sqrt(0.5 * (r - z.x));
+  return {fabs(z.y) / (2.0 * s), copysign(s, z.y)};
+}
+template <typename R, typename S>
+__host__ __device__ __forceinline__ cx<R> cconv(cx<S> a) { return {(R)a.x, (R)a.y}; }
+
+// ---------------------------------------------------------------- geometry
+struct Geo {
+  int dim;        // 2 or 3
+  int Lx, Ly, Lz; // lattice extents (Lz = 1 in 2D); x fastest
+  int N;          // sites
+  int p;          // subdomains
+  int T;          // transverse count per slice row (1 in 2D, Ly in 3D)
+  int A;          // sites per slow layer = Lx*T
+  int Ls;         // slow extent (Ly in 2D, Lz in 3D)
+  int W;          // padded slice width
+  int Ndd;        // DD-layout vector length
+  int ifc_off;    // start of the interface part = p*Lx*W
+  int k_max;      // Lanczos rank cap
+  int krylov_maxit;
+  int refine_max; // mixed form: most refinement passes per solve
+  double t, mu;
+  double krylov_tol;   // relative residual target of an interface solve
+  double refine_tol;   // mixed form: relative residual target after refinement
+  int h[DY_MAXP];      // subdomain heights along the slow axis
+  int s0[DY_MAXP];     // subdomain start along the slow axis
+  int ylayer[DY_MAXP]; // slow coordinate of interface layer l
+};
+
+// Device buffers of one plan; every per-frequency array is [K_cap][...].
+struct Bufs {
+  const double* V;      // [N] trap/local potential, natural order
+  const double* omega;  // [K] Matsubara frequencies
+  const cxd* sigma;     // [K][N] self-energy, natural order
+  const double* q1;     // [N] real Lanczos start vector
+  const int* dd2nat;    // [Ndd] natural index of each DD slot, -1 on padding
+  void* g;              // [K][p][Lx][W][W] slice factors g_s read by the sweeps (precision of the form)
+  cxd* g64;             // [K][p][Lx][W][W] FP64 g_s kept for the mixed form's FP64 recursion
+  cxd* diagB;           // [K][Ndd] diag(B^-1), zero on the interface
+  cxd* Q;               // [K][k_max+1][Ndd] Lanczos vectors
+  cxd* acc;             // [K][Ndd] running diag(Q T Q^T)
+  cxd* u;               // [K][Ndd] X q
+  cxd* v1;              // [K][Ndd] work vectors of the mixed form
+  cxd* v2;
+  cxd* v3;
+  void* yscr;           // [K][p][Lx][W] forward-sweep intermediates (precision of the form)
+  cxd* bnd;             // [K][p][2][A] sweep values on the subdomain boundary rows
+  cxd* ifv;             // [K][6][(p-1)*A] interface Krylov vectors
+  cxd* pre;             // [K][p-1][2][A] tridiagonal preconditioner factors
+  cxd* lan;             // [K][k_max+1][2] (alpha_j, beta_j); beta_j couples q_{j-1}, q_j
+  double* maxT;         // [K] running max |T| entry
+  int* st;              // [K][ST_N]
+  cxd* out;             // [K][N] diag(G), natural order
+  unsigned long long* sweeps;  // [K][p] subdomain sweeps performed (work accounting)
+};
+
+// interface Krylov vector slots inside ifv
+enum { IF_X = 0, IF_R = 1, IF_Z = 2, IF_P = 3, IF_SP = 4, IF_B = 5, IF_N = 6 };
+
+__host__ __device__ __forceinline__ size_t nifc(const Geo& g) { return (size_t)(g.p > 1 ? g.p - 1 : 1) * g.A; }
+
+// H_ii(i w) = i w + mu - V_i - Sigma_i(i w)   (Eq. 1)
+__device__ __forceinline__ cxd dyson_diag(const Geo& g, const Bufs& b, int kf, int nat) {
+  cxd s = b.sigma[(size_t)kf * g.N + nat];
+  return {g.mu - b.V[nat] - s.x, b.omega[kf] - s.y};
+}
+
+// natural index of row j of slice s in subdomain i
+__device__ __forceinline__ int sub_nat(const Geo& g, int i, int s, int j) {
+  int tr = j % g.T, sl = j / g.T;
+  return s + g.Lx * tr + g.A * (g.s0[i] + sl);
+}
+
+// ---------------------------------------------------------------- host launchers
+template <typename R, typename S>
+cudaError_t launch_factor(const Geo& g, const Bufs& b, int K, cudaStream_t st);
+cudaError_t launch_precond(const Geo& g, const Bufs& b, int K, cudaStream_t st);
+cudaError_t launch_init(const Geo& g, const Bufs& b, int K, cudaStream_t st);
+template <typename R>
+cudaError_t launch_xmatvec(const Geo& g, const Bufs& b, int K, int j, int mixed, cudaStream_t st);
+cudaError_t launch_lanczos(const Geo& g, const Bufs& b, int K, int j, cudaStream_t st);
+cudaError_t launch_finalize(const Geo& g, const Bufs& b, int K, cudaStream_t st);
+template <typename R>
+cudaError_t launch_spmv(const Geo& g, const double* V, const double* omega, const cxd* sigma,
+                        const cx<R>* x, cx<R>* y, int K, cudaStream_t st);
+template <typename R>
+cudaError_t launch_bsolve(const Geo& g, const Bufs& b, int K, const cxd* q_dd, cxd* w_dd,
+                          cudaStream_t st);
+cudaError_t launch_gather(const Geo& g, const Bufs& b, int K, const cxd* nat, cxd* dd,
+                          size_t dd_stride, cudaStream_t st);
+cudaError_t launch_scatter(const Geo& g, const Bufs& b, int K, const cxd* dd, cxd* nat,
+                           size_t dd_stride, cudaStream_t st);
+cudaError_t launch_status(const Geo& g, const Bufs& b, int K, int* status, cudaStream_t st);

@@ -1,0 +1,198 @@
+// Subdomain factorization: diag(B^-1) and the slice factors used by every
+// subdomain solve (Sec. 2.3: "the diagonal of B^-1 ... needs to be
+// calculated only once at the very beginning of the Lanczos steps"; Eq. 7).
+//
+// One CTA per (subdomain, frequency).  B_i is block tridiagonal along x with
+// slice blocks D_s (diag(H_jj) + t * in-slice hopping) and couplings t*I:
+//   forward   g_s  = (D_s - t^2 g_{s-1})^-1          (left-connected inverse)
+//   backward  G_ss = g_s + t^2 g_s G_{s+1,s+1} g_s
+// The g_s are stored for the block forward/back substitutions; diag(G_ss) is
+// diag(B^-1) on that slice.  Matrices live in shared memory (W <= 64);
+// inversion is in-place Gauss-Jordan without pivoting, which is safe here
+// because every pivot block has a positive-definite imaginary part
+// (Im H_jj >= w_0 > 0 and -t^2 Im g_{s-1} is positive semi-definite), so
+// all Schur complements stay non-singular.
+#include "dyson_common.cuh"
+
+namespace {
+
+template <typename R>
+__device__ __forceinline__ bool slice_adjacent(int r, int c, int T) {
+  int tr_r = r % T, sl_r = r / T, tr_c = c % T, sl_c = c / T;
+  if (sl_r == sl_c) return abs(tr_r - tr_c) == 1;
+  return tr_r == tr_c && abs(sl_r - sl_c) == 1;
+}
+
+// In-place Gauss-Jordan inverse of the W x W matrix A (row-major, shared).
+template <typename R>
+__device__ void gj_invert(cx<R>* A, int W) {
+  constexpr int MAXE = DY_MAXW_SMEM * DY_MAXW_SMEM / DY_THREADS;
+  cx<R> nv[MAXE];
+  const int n = W * W;
+  for (int k = 0; k < W; ++k) {
+    __syncthreads();
+    const cx<R> piv = cinv(A[k * W + k]);
+    int q = 0;
+    for (int e = threadIdx.x; e < n; e += DY_THREADS, ++q) {
+      int r = e / W, c = e - r * W;
+      cx<R> v;
+      if (r == k && c == k) {
+        v = piv;
+      } else if (r == k) {
+        v = A[k * W + c] * piv;
+      } else if (c == k) {
+        v = -(A[r * W + k] * piv);
+      } else {
+        cx<R> f = A[r * W + k] * piv;
+        v = A[e] - f * A[k * W + c];
+      }
+      nv[q] = v;
+    }
+    __syncthreads();
+    q = 0;
+    for (int e = threadIdx.x; e < n; e += DY_THREADS, ++q) A[e] = nv[q];
+  }
+  __syncthreads();
+}
+
+// C = X * Y for W x W shared matrices
+template <typename R>
+__device__ __forceinline__ void smem_matmul(cx<R>* C, const cx<R>* X, const cx<R>* Y, int W) {
+  const int n = W * W;
+  for (int e = threadIdx.x; e < n; e += DY_THREADS) {
+    int r = e / W, c = e - r * W;
+    cx<R> acc = {0, 0};
+    const cx<R>* xr = X + r * W;
+    for (int k = 0; k < W; ++k) acc = cfma(xr[k], Y[k * W + c], acc);
+    C[e] = acc;
+  }
+}
+
+// R: arithmetic of the recursion; S: storage of the g_s handed to the sweeps.
+// With S != R (mixed form) the g_s are kept in R in b.g64 for the backward
+// pass and rounded to S only for the sweeps.
+template <typename R, typename S>
+__global__ void __launch_bounds__(DY_THREADS) k_factor(Geo g, Bufs b) {
+  using C = cx<R>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int i = blockIdx.x, kf = blockIdx.y;
+  const int W = g.W, Lx = g.Lx, T = g.T, w = T * g.h[i];
+  const int n = W * W;
+  C* A = reinterpret_cast<C*>(smem_raw);
+  C* Bm = A + n;
+  C* Cm = Bm + n;
+  constexpr bool two = sizeof(S) != sizeof(R);
+  const size_t uoff = ((size_t)kf * g.p + i) * (size_t)Lx * n;
+  C* gout = reinterpret_cast<C*>(two ? b.g64 : b.g) + uoff;
+  cx<S>* gsw = reinterpret_cast<cx<S>*>(b.g) + uoff;
+  cxd* dB = b.diagB + (size_t)kf * g.Ndd + (size_t)i * Lx * W;
+  const R t = (R)g.t, t2 = (R)(g.t * g.t);
+
+  // forward: g_s = (D_s - t^2 g_{s-1})^-1, A holds g_{s-1} on entry
+  for (int s = 0; s < Lx; ++s) {
+    for (int e = threadIdx.x; e < n; e += DY_THREADS) {
+      int r = e / W, c = e - r * W;
+      C v = (s > 0) ? (-t2) * A[e] : C{0, 0};
+      if (r < w && c < w) {
+        if (r == c) {
+          cxd d = dyson_diag(g, b, kf, sub_nat(g, i, s, r));
+          v = v + cconv<R>(d);
+        } else if (slice_adjacent<R>(r, c, T)) {
+          v.x += t;
+        }
+      } else {
+        v = (r == c) ? C{1, 0} : C{0, 0};
+      }
+      A[e] = v;
+    }
+    gj_invert<R>(A, W);
+    for (int e = threadIdx.x; e < n; e += DY_THREADS) {
+      int r = e / W, c = e - r * W;
+      C v = A[e];
+      if (r >= w || c >= w) v = C{0, 0};
+      A[e] = v;
+      gout[(size_t)s * n + e] = v;
+      if (two) gsw[(size_t)s * n + e] = cconv<S>(v);
+    }
+    __syncthreads();
+  }
+  // backward: A holds G_{s+1,s+1}
+  for (int r = threadIdx.x; r < W; r += DY_THREADS)
+    dB[(size_t)(Lx - 1) * W + r] = (r < w) ? cconv<double>(A[r * W + r]) : cxd{0, 0};
+  for (int s = Lx - 2; s >= 0; --s) {
+    for (int e = threadIdx.x; e < n; e += DY_THREADS) Bm[e] = gout[(size_t)s * n + e];
+    __syncthreads();
+    smem_matmul<R>(Cm, Bm, A, W);            // g_s G_{s+1}
+    __syncthreads();
+    for (int e = threadIdx.x; e < n; e += DY_THREADS) {
+      int r = e / W, c = e - r * W;
+      C acc = {0, 0};
+      const C* xr = Cm + r * W;
+      for (int k = 0; k < W; ++k) acc = cfma(xr[k], Bm[k * W + c], acc);
+      A[e] = Bm[e] + t2 * acc;               // g_s + t^2 g_s G_{s+1} g_s
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < W; r += DY_THREADS)
+      dB[(size_t)s * W + r] = (r < w) ? cconv<double>(A[r * W + r]) : cxd{0, 0};
+  }
+  // interface part of diag(B^-1) is zero (blkdiag(B^-1, 0), Eq. 9)
+  if (i == g.p - 1) {
+    cxd* dI = b.diagB + (size_t)kf * g.Ndd + g.ifc_off;
+    size_t m = (size_t)(g.p - 1) * g.A;
+    for (size_t e = threadIdx.x; e < m; e += DY_THREADS) dI[e] = cxd{0, 0};
+  }
+}
+
+// Tridiagonal preconditioner of the interface Schur system.  The Schur
+// complement S = C - E^T B^-1 E (Eq. 4) is never formed; its cheap
+// approximation keeps C and the diagonal of B^-1 next to the interface:
+//   M = C_x - t^2 (diag B^-1 below + diag B^-1 above),
+// with C_x the hopping along x only (in-plane y hopping dropped in 3D).
+// Thomas factors per x-line: inv_den[x] and c'[x].
+__global__ void __launch_bounds__(DY_THREADS) k_precond(Geo g, Bufs b) {
+  const int l = blockIdx.x, kf = blockIdx.y;
+  const int Lx = g.Lx, T = g.T, A = g.A, W = g.W;
+  const cxd* dB = b.diagB + (size_t)kf * g.Ndd;
+  cxd* pre = b.pre + ((size_t)kf * nifc(g) + (size_t)l * A) * 2;
+  const double t = g.t;
+  for (int tr = threadIdx.x; tr < T; tr += DY_THREADS) {
+    cxd cprev = {0, 0};
+    for (int x = 0; x < Lx; ++x) {
+      int a = x + Lx * tr;
+      int nat = a + A * g.ylayer[l];
+      cxd d = dyson_diag(g, b, kf, nat);
+      // row just below the layer: top row of subdomain l; just above: bottom row of l+1
+      cxd gb = dB[(size_t)l * Lx * W + (size_t)x * W + tr + T * (g.h[l] - 1)];
+      cxd ga = dB[(size_t)(l + 1) * Lx * W + (size_t)x * W + tr];
+      cxd m = d - (t * t) * (gb + ga);
+      cxd den = (x == 0) ? m : m - t * cprev;
+      cxd inv = cinv(den);
+      cxd cp = t * inv;
+      pre[a] = inv;
+      pre[A + a] = cp;
+      cprev = cp;
+    }
+  }
+}
+
+}  // namespace
+
+template <typename R, typename S>
+cudaError_t launch_factor(const Geo& g, const Bufs& b, int K, cudaStream_t st) {
+  if (g.W > DY_MAXW_SMEM) return cudaErrorInvalidValue;
+  size_t smem = 3 * (size_t)g.W * g.W * sizeof(cx<R>);
+  cudaError_t e = cudaFuncSetAttribute(k_factor<R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  k_factor<R, S><<<dim3(g.p, K), DY_THREADS, smem, st>>>(g, b);
+  return cudaGetLastError();
+}
+template cudaError_t launch_factor<double, double>(const Geo&, const Bufs&, int, cudaStream_t);
+template cudaError_t launch_factor<double, float>(const Geo&, const Bufs&, int, cudaStream_t);
+template cudaError_t launch_factor<float, float>(const Geo&, const Bufs&, int, cudaStream_t);
+
+cudaError_t launch_precond(const Geo& g, const Bufs& b, int K, cudaStream_t st) {
+  if (g.p < 2) return cudaSuccess;
+  k_precond<<<dim3(g.p - 1, K), DY_THREADS, 0, st>>>(g, b);
+  return cudaGetLastError();
+}

@@ -1,0 +1,1053 @@
+// Lanczos-based low-rank correction: the per-step kernels.
+//
+// Every kernel here runs one thread-block cluster per frequency with one CTA
+// per subdomain (cluster = p CTAs, grid = p x K).  CTA i owns subdomain i's
+// slice block of every DD-layout vector and interface layer i (i < p-1).
+// Reductions over a frequency's lattice are two-level: a fixed-order
+// block reduction, then every CTA reads the p partials from distributed
+// shared memory in rank order, so all CTAs of a cluster hold bit-identical
+// scalars and take identical branch decisions (no CTA can leave a cluster
+// barrier behind).
+//
+// X-"matvec" (Sec. 2.3, Eqs. 6-8).  The paper defines u = v - w with
+// H v = q and w = blkdiag(B^-1, 0) q.  Eliminating the subdomain unknowns
+// of H v = q gives, without ever forming S = C - E^T B^-1 E (Eq. 4),
+//     y   = S^-1 (E^T B^-1 q_B - q_C),
+//     u_B = B^-1 E y,   u_C = -y,
+// which is exactly v - w with no cancellation.  S y = r is solved by COCG
+// (conjugate orthogonal CG: CG in the bilinear form, valid for complex
+// symmetric S) whose S-products are subdomain solves with boundary-only
+// right-hand sides.
+#include <cooperative_groups.h>
+
+#include "dyson_common.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace {
+
+constexpr double TERM_TOL = 1e-12;    // |beta_{j+1}| <= TERM_TOL * max|T|: invariant subspace
+constexpr double BRK_TOL = 1e-14;     // |r^T r| <= BRK_TOL * ||r||^2: breakdown
+constexpr int KMAX_SMEM = 256;        // largest Lanczos rank cap
+
+__device__ __forceinline__ size_t own_idx(const Geo& g, int i, int e, int nsub) {
+  return e < nsub ? (size_t)i * nsub + e : (size_t)g.ifc_off + (size_t)i * g.A + (e - nsub);
+}
+__device__ __forceinline__ int own_count(const Geo& g, int i) {
+  return g.Lx * g.W + (i < g.p - 1 ? g.A : 0);
+}
+
+// ---------------------------------------------------------------- reductions
+struct RedSmem {
+  cxd wred[DY_WARPS * 8];
+  cxd slot[2 * 8];
+  cxd res[8];
+};
+
+__device__ __forceinline__ cxd warp_sum(cxd v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, off);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, off);
+  }
+  return v;
+}
+
+// Sum NV complex partials over the whole cluster; every thread gets the totals.
+template <int NV>
+__device__ void cluster_sum(cg::cluster_group& cl, RedSmem& rs, int& phase, int p, cxd (&v)[NV]) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) rs.wred[wid * 8 + k] = v[k];
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    cxd s = {0, 0};
+    for (int w = 0; w < DY_WARPS; ++w) s = s + rs.wred[w * 8 + threadIdx.x];
+    rs.slot[phase * 8 + threadIdx.x] = s;
+  }
+  cl.sync();
+  if (threadIdx.x < NV) {
+    cxd s = {0, 0};
+    for (int r = 0; r < p; ++r) {
+      const cxd* rem = cl.map_shared_rank(rs.slot, r);
+      s = s + rem[phase * 8 + threadIdx.x];
+    }
+    rs.res[threadIdx.x] = s;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = rs.res[k];
+  phase ^= 1;
+}
+
+// CTA-local sum (no cluster exchange)
+template <int NV>
+__device__ void block_sum(RedSmem& rs, cxd (&v)[NV]) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) rs.wred[wid * 8 + k] = v[k];
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    cxd s = {0, 0};
+    for (int w = 0; w < DY_WARPS; ++w) s = s + rs.wred[w * 8 + threadIdx.x];
+    rs.res[threadIdx.x] = s;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = rs.res[k];
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------- async copies
+// g_s blocks stream from HBM into a ring of shared-memory slots with 1D bulk
+// copies (cp.async.bulk, completion counted on an mbarrier per slot).  Every
+// wait is bounded by the global timer: on time-out the kernel records
+// DYSON_ST_WAIT_TIMEOUT and goes on (no CTA may leave its cluster's barriers).
+constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;   // 2 s
+constexpr int ST_WAIT_TIMEOUT = 16;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes) : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}" : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (!mbar_try_wait(bar, parity))
+    if (global_ns() - t0 > WAIT_LIMIT_NS) return false;
+  return true;
+}
+
+// Per-CTA copy pipeline: S slots of one W x W block each, one mbarrier per slot.
+struct Pipe {
+  uint64_t* bar;   // [S] in static shared memory
+  void* ring;      // S slots in dynamic shared memory
+  int S;
+  unsigned seq;    // blocks issued (= consumed) so far by this CTA
+  int* err;        // shared flag: a bounded wait ran out
+};
+
+constexpr int MAX_STAGES = 8;
+
+__device__ void pipe_init(Pipe& pp) {
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < pp.S; ++k) mbar_init(pp.bar + k, 1);
+    *pp.err = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------- block sweep
+// Solve B_i x = rhs by block forward/back substitution with the stored
+// left-connected inverses g_s (Eq. 7 and the S-products):
+//   forward  y_s = g_s (rhs_s - t y_{s-1})
+//   backward x_s = y_s - t g_s x_{s+1}
+// The right-hand side is either a full DD block (src) or boundary-only,
+// t times an interface-layer vector on the first/last slow rows (E y).
+// The 2 Lx - 1 blocks the two passes read stream through the copy ring.
+template <typename R>
+struct SweepArgs {
+  const cx<R>* g;      // [Lx][W][W] this subdomain's factors
+  cx<R>* y;            // [Lx][W] scratch for the forward intermediates
+  const cxd* src;      // full right-hand side (subdomain block) or null
+  const cxd* lay_lo;   // interface layer below (i-1), boundary mode
+  const cxd* lay_hi;   // interface layer above (i), boundary mode
+  cxd* dst;            // full solution out (subdomain block) or null
+  int dst_op;          // 0 store, 1 add, 2 subtract, 3 store negated
+  cxd* bnd_lo;         // solution on the lowest slow row, layer layout (or null)
+  cxd* bnd_hi;         // solution on the highest slow row
+};
+
+// Thread layout of the block products y = g_s z (g_s complex symmetric, so its
+// row r is also its column r and rows are read contiguously): warp w owns rows
+// [w*RPW, (w+1)*RPW); inside the warp lane = rr*G + cg, row group rr, column
+// class cg (columns cg, cg+G, ...: CPG of them); the G partial sums of a row
+// are added with log2(G) butterfly shuffles and lane rr*G finishes the row.
+struct SweepLayout {
+  int RPW, G, CPG;
+};
+__host__ __device__ inline SweepLayout sweep_layout(int W) {
+  int rpw = (W + DY_WARPS - 1) / DY_WARPS, p2 = 1;
+  while (p2 < rpw) p2 <<= 1;
+  SweepLayout L;
+  L.RPW = p2;
+  L.G = 32 / p2;
+  L.CPG = (W + L.G - 1) / L.G;
+  return L;
+}
+
+template <typename R>
+__device__ void sweep(const Geo& g, int i, const SweepArgs<R>& a, cx<R>* sm, Pipe& pp,
+                      unsigned long long* cnt) {
+  const int W = g.W, Lx = g.Lx, T = g.T, w = T * g.h[i];
+  const SweepLayout L = sweep_layout(W);
+  cx<R>* zbuf = sm;                      // [2][W]: z of the current and of the next slice
+  cx<R>* ring = reinterpret_cast<cx<R>*>(pp.ring);
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int rr = lane / L.G, cg = lane - rr * L.G;
+  const int row = wid * L.RPW + rr;      // the row this lane works on
+  const bool rvalid = row < W;
+  const bool owner = rvalid && cg == 0;  // finishes the row
+  // rows of one warp are W entries apart, i.e. in the same banks; starting each
+  // row group at a different multiple of G spreads a warp's accesses over all banks
+  const int rot = (W % L.G == 0) ? (rr * L.G) % W : 0;
+  const R t = (R)g.t;
+  const int WW = W * W;
+  const uint32_t bytes = (uint32_t)(WW * sizeof(cx<R>));
+  const int NL = 2 * Lx - 1;
+  const int S = pp.S;
+  auto slice_of = [&](int n) { return n < Lx ? n : 2 * Lx - 2 - n; };
+  auto issue = [&](int n) {
+    const unsigned q = pp.seq + n;
+    const int slot = (int)(q % S);
+    bulk_load(ring + (size_t)slot * WW, a.g + (size_t)slice_of(n) * WW, bytes, pp.bar + slot);
+  };
+  auto rhs = [&](int s, int j) -> cx<R> {
+    if (a.src) return cconv<R>(a.src[(size_t)s * W + j]);
+    cxd v = {0, 0};
+    if (j < w) {
+      if (a.lay_lo && j < T) v = v + g.t * a.lay_lo[s + Lx * j];
+      if (a.lay_hi && j >= w - T) v = v + g.t * a.lay_hi[s + Lx * (j - (w - T))];
+    }
+    return cconv<R>(v);
+  };
+  // old value of the destination row for the add/subtract forms (0 otherwise)
+  auto dst_old = [&](int s, int j) -> cxd {
+    if (a.dst && (a.dst_op == 1 || a.dst_op == 2) && j < w) return a.dst[(size_t)s * W + j];
+    return cxd{0, 0};
+  };
+  auto out = [&](int s, int j, cx<R> x, cxd old) {
+    if (j >= w) return;
+    cxd xd = cconv<double>(x);
+    if (a.dst) {
+      cxd* d = a.dst + (size_t)s * W + j;
+      if (a.dst_op == 0) *d = xd;
+      else if (a.dst_op == 1) *d = old + xd;
+      else if (a.dst_op == 2) *d = old - xd;
+      else *d = -xd;
+    }
+    if (a.bnd_lo && j < T) a.bnd_lo[s + Lx * j] = xd;
+    if (a.bnd_hi && j >= w - T) a.bnd_hi[s + Lx * (j - (w - T))] = xd;
+  };
+
+  __syncthreads();                       // previous users of ring and zbuf are done
+  if (tid == 0) {
+    fence_proxy_async();
+    for (int n = 0; n < S && n < NL; ++n) issue(n);
+  }
+  // Per-row values the critical path needs are loaded two slices ahead:
+  // forward f1, f2 = rhs(s+1), rhs(s+2); backward y1, y2 = y_s, y_{s-1} and
+  // o1, o2 = old destination values of the same rows.
+  cx<R> f1 = {0, 0}, f2 = {0, 0}, y1 = {0, 0}, y2 = {0, 0};
+  cxd o1 = {0, 0}, o2 = {0, 0};
+  if (owner) {
+    zbuf[row] = rhs(0, row);
+    if (Lx > 1) f1 = rhs(1, row);
+    if (Lx > 2) f2 = rhs(2, row);
+  }
+  __syncthreads();
+  for (int n = 0; n < NL; ++n) {
+    const unsigned q = pp.seq + n;
+    const int slot = (int)(q % S);
+    if (!mbar_wait(pp.bar + slot, (q / S) & 1u)) *pp.err = 1;
+    const cx<R>* grow = ring + (size_t)slot * WW + (size_t)row * W;
+    const cx<R>* zc = zbuf + (n & 1) * W;
+    cx<R> acc = {0, 0};
+    if (rvalid) {
+#pragma unroll 4
+      for (int k = 0; k < L.CPG; ++k) {
+        const int base = cg + L.G * k;   // columns interleaved over the group's lanes
+        if (base < W) {
+          int col = base + rot;          // rotated per row group: no bank conflicts
+          if (col >= W) col -= W;
+          acc = cfma(grow[col], zc[col], acc);
+        }
+      }
+    }
+    for (int off = L.G >> 1; off > 0; off >>= 1) {
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+    }
+    if (owner) {
+      const cx<R> m = acc;
+      cx<R>* zn = zbuf + ((n + 1) & 1) * W;
+      const int s = slice_of(n);
+      if (n < Lx) {                      // forward pass
+        a.y[(size_t)s * W + row] = m;
+        if (s + 1 < Lx) {
+          zn[row] = f1 - t * m;
+          f1 = f2;
+          if (s + 3 < Lx) f2 = rhs(s + 3, row);
+        } else {
+          zn[row] = m;                   // x_{Lx-1} = y_{Lx-1}
+          out(s, row, m, dst_old(s, row));
+        }
+        if (s == Lx - 1 && Lx > 1) {     // start the backward prefetch
+          y1 = a.y[(size_t)(Lx - 2) * W + row];
+          o1 = dst_old(Lx - 2, row);
+          if (Lx > 2) {
+            y2 = a.y[(size_t)(Lx - 3) * W + row];
+            o2 = dst_old(Lx - 3, row);
+          }
+        }
+      } else {                           // backward pass
+        cx<R> xv = y1 - t * m;
+        out(s, row, xv, o1);
+        zn[row] = xv;
+        y1 = y2;
+        o1 = o2;
+        if (s >= 2) {
+          y2 = a.y[(size_t)(s - 2) * W + row];
+          o2 = dst_old(s - 2, row);
+        }
+      }
+    }
+    __syncthreads();                     // slot n and z of slice n fully read; z of n+1 written
+    if (tid == 0 && n + S < NL) {
+      fence_proxy_async();
+      issue(n + S);
+    }
+  }
+  pp.seq += NL;
+  if (tid == 0 && cnt) *cnt += 1;
+}
+
+template <typename R>
+__device__ __forceinline__ SweepArgs<R> sweep_base(const Geo& g, const Bufs& b, int kf, int i) {
+  SweepArgs<R> a;
+  const size_t nsub = (size_t)g.Lx * g.W;
+  a.g = reinterpret_cast<const cx<R>*>(b.g) + ((size_t)kf * g.p + i) * nsub * g.W;
+  a.y = reinterpret_cast<cx<R>*>(b.yscr) + ((size_t)kf * g.p + i) * nsub;
+  a.src = nullptr;
+  a.lay_lo = a.lay_hi = nullptr;
+  a.dst = nullptr;
+  a.dst_op = 0;
+  a.bnd_lo = a.bnd_hi = nullptr;
+  return a;
+}
+
+__device__ __forceinline__ unsigned long long* sweep_cnt(const Geo& g, const Bufs& b, int kf, int i) {
+  return b.sweeps ? b.sweeps + (size_t)kf * g.p + i : nullptr;
+}
+__device__ __forceinline__ cxd* bnd_ptr(const Geo& g, const Bufs& b, int kf, int i, int hi) {
+  return b.bnd + (((size_t)kf * g.p + i) * 2 + hi) * g.A;
+}
+__device__ __forceinline__ cxd* ifv_ptr(const Geo& g, const Bufs& b, int kf, int slot) {
+  return b.ifv + ((size_t)kf * IF_N + slot) * nifc(g);
+}
+
+// ---------------------------------------------------------------- interface pieces
+// Apply the tridiagonal preconditioner along x lines of layer i: z = M^-1 r.
+__device__ void precond_apply(const Geo& g, const Bufs& b, int kf, int i, const cxd* r, cxd* z) {
+  const int Lx = g.Lx, A = g.A;
+  const cxd* pre = b.pre + ((size_t)kf * nifc(g) + (size_t)i * A) * 2;
+  const double t = g.t;
+  for (int tr = threadIdx.x; tr < g.T; tr += DY_THREADS) {
+    const int o = Lx * tr;
+    cxd prev = r[o] * pre[o];
+    z[o] = prev;
+    for (int x = 1; x < Lx; ++x) {
+      prev = (r[o + x] - t * prev) * pre[o + x];
+      z[o + x] = prev;
+    }
+    cxd nxt = z[o + Lx - 1];
+    for (int x = Lx - 2; x >= 0; --x) {
+      nxt = z[o + x] - pre[A + o + x] * nxt;
+      z[o + x] = nxt;
+    }
+  }
+}
+
+// (C p)[a] on layer l: the Dyson matrix restricted to the interface layer.
+__device__ __forceinline__ cxd layer_C_apply(const Geo& g, const Bufs& b, int kf, int l,
+                                             const cxd* pv, int a) {
+  const int Lx = g.Lx, x = a % Lx, tr = a / Lx;
+  cxd d = dyson_diag(g, b, kf, a + g.A * g.ylayer[l]);
+  cxd v = d * pv[a];
+  cxd nb = {0, 0};
+  if (x > 0) nb = nb + pv[a - 1];
+  if (x < Lx - 1) nb = nb + pv[a + 1];
+  if (tr > 0) nb = nb + pv[a - Lx];
+  if (tr < g.T - 1) nb = nb + pv[a + Lx];
+  return v + g.t * nb;
+}
+
+// COCG for S y = b on the interface (S = C - E^T B^-1 E never formed).
+// Right-hand side in IF_B, solution in IF_X.  Sweeps run in precision R.
+// Returns the iteration count; *conv is set to 0 if the cap was hit.
+template <typename R>
+__device__ int schur_cocg(cg::cluster_group& cl, RedSmem& rs, int& phase, const Geo& g,
+                          const Bufs& b, int kf, int i, double tol, cx<R>* sm, Pipe& pp,
+                          int* conv) {
+  const int p = g.p, A = g.A;
+  const bool has = i < p - 1;
+  cxd* X = ifv_ptr(g, b, kf, IF_X);
+  cxd* Rv = ifv_ptr(g, b, kf, IF_R);
+  cxd* Z = ifv_ptr(g, b, kf, IF_Z);
+  cxd* P = ifv_ptr(g, b, kf, IF_P);
+  cxd* SP = ifv_ptr(g, b, kf, IF_SP);
+  const cxd* Bv = ifv_ptr(g, b, kf, IF_B);
+  const size_t o = (size_t)i * A;
+  cxd* bl_i = bnd_ptr(g, b, kf, i, 1);
+  const cxd* bl_n = has ? bnd_ptr(g, b, kf, i + 1, 0) : nullptr;
+
+  if (has) {
+    for (int a = threadIdx.x; a < A; a += DY_THREADS) {
+      X[o + a] = cxd{0, 0};
+      Rv[o + a] = Bv[o + a];
+    }
+  }
+  __syncthreads();
+  if (has) precond_apply(g, b, kf, i, Rv + o, Z + o);
+  __syncthreads();
+  cxd v2[2] = {{0, 0}, {0, 0}};
+  if (has) {
+    for (int a = threadIdx.x; a < A; a += DY_THREADS) {
+      cxd z = Z[o + a], r = Rv[o + a];
+      P[o + a] = z;
+      v2[0] = cfma(r, z, v2[0]);
+      v2[1].x += cabs2(r);
+    }
+  }
+  cluster_sum<2>(cl, rs, phase, p, v2);
+  cxd rho = v2[0];
+  const double bn = v2[1].x;
+  *conv = 1;
+  if (bn == 0.0) return 0;
+  SweepArgs<R> sa = sweep_base<R>(g, b, kf, i);
+  sa.lay_lo = (i > 0) ? P + (size_t)(i - 1) * A : nullptr;
+  sa.lay_hi = has ? P + o : nullptr;
+  sa.bnd_lo = bnd_ptr(g, b, kf, i, 0);
+  sa.bnd_hi = bnd_ptr(g, b, kf, i, 1);
+  int it = 0;
+  for (;;) {
+    if (it >= g.krylov_maxit) {
+      *conv = 0;
+      break;
+    }
+    ++it;
+    cl.sync();                                  // P of both neighbour layers is final
+    sweep<R>(g, i, sa, sm, pp, sweep_cnt(g, b, kf, i));   // B^-1 E p on this subdomain
+    cl.sync();                                  // boundary values of every subdomain written
+    cxd v1[1] = {{0, 0}};
+    if (has) {
+      for (int a = threadIdx.x; a < A; a += DY_THREADS) {
+        cxd sp = layer_C_apply(g, b, kf, i, P + o, a) - g.t * (bl_i[a] + bl_n[a]);
+        SP[o + a] = sp;
+        v1[0] = cfma(P[o + a], sp, v1[0]);
+      }
+    }
+    cluster_sum<1>(cl, rs, phase, p, v1);
+    const cxd alpha = cdiv(rho, v1[0]);
+    if (has) {
+      for (int a = threadIdx.x; a < A; a += DY_THREADS) {
+        X[o + a] = X[o + a] + alpha * P[o + a];
+        Rv[o + a] = Rv[o + a] - alpha * SP[o + a];
+      }
+    }
+    __syncthreads();
+    if (has) precond_apply(g, b, kf, i, Rv + o, Z + o);
+    __syncthreads();
+    v2[0] = v2[1] = cxd{0, 0};
+    if (has) {
+      for (int a = threadIdx.x; a < A; a += DY_THREADS) {
+        cxd z = Z[o + a], r = Rv[o + a];
+        v2[0] = cfma(r, z, v2[0]);
+        v2[1].x += cabs2(r);
+      }
+    }
+    cluster_sum<2>(cl, rs, phase, p, v2);
+    if (v2[1].x <= tol * tol * bn) break;
+    const cxd beta = cdiv(v2[0], rho);
+    rho = v2[0];
+    if (has) {
+      for (int a = threadIdx.x; a < A; a += DY_THREADS) P[o + a] = Z[o + a] + beta * P[o + a];
+    }
+  }
+  return it;
+}
+
+// res = rhs - H x (mode 0: full H; mode 1: B only, no interface coupling),
+// FP64, on this CTA's entries.  Returns partials (||res||^2, ||rhs||^2).
+__device__ void residual_H(const Geo& g, const Bufs& b, int kf, int i, const cxd* rhs,
+                           const cxd* x, cxd* res, int mode, double* rn, double* qn) {
+  const int W = g.W, Lx = g.Lx, T = g.T, h = g.h[i], w = T * h, A = g.A;
+  const size_t nsub = (size_t)Lx * W;
+  const cxd* xs = x + i * nsub;
+  const double t = g.t;
+  double sr = 0, sq = 0;
+  for (int e = threadIdx.x; e < (int)nsub; e += DY_THREADS) {
+    const int s = e / W, j = e - s * W;
+    if (j >= w) continue;
+    const int tr = j % T, sl = j / T;
+    cxd d = dyson_diag(g, b, kf, sub_nat(g, i, s, j));
+    cxd nb = {0, 0};
+    if (s > 0) nb = nb + xs[e - W];
+    if (s < Lx - 1) nb = nb + xs[e + W];
+    if (tr > 0) nb = nb + xs[e - 1];
+    if (tr < T - 1) nb = nb + xs[e + 1];
+    if (sl > 0) nb = nb + xs[e - T];
+    if (sl < h - 1) nb = nb + xs[e + T];
+    if (mode == 0) {
+      if (sl == 0 && i > 0) nb = nb + x[g.ifc_off + (size_t)(i - 1) * A + s + Lx * tr];
+      if (sl == h - 1 && i < g.p - 1) nb = nb + x[g.ifc_off + (size_t)i * A + s + Lx * tr];
+    }
+    cxd hv = d * xs[e] + t * nb;
+    cxd q = rhs[i * nsub + e];
+    cxd rr = q - hv;
+    res[i * nsub + e] = rr;
+    sr += cabs2(rr);
+    sq += cabs2(q);
+  }
+  if (mode == 0 && i < g.p - 1) {
+    const size_t o = g.ifc_off + (size_t)i * A;
+    const cxd* xl = x + o;
+    const cxd* xb = x + i * nsub;           // subdomain i: its top row touches layer i
+    const cxd* xa = x + (i + 1) * nsub;     // subdomain i+1: its bottom row touches layer i
+    const int hi = T * (g.h[i] - 1);
+    for (int a = threadIdx.x; a < A; a += DY_THREADS) {
+      const int xx = a % Lx, tr = a / Lx;
+      cxd hv = layer_C_apply(g, b, kf, i, xl, a);
+      hv = hv + t * (xb[(size_t)xx * W + hi + tr] + xa[(size_t)xx * W + tr]);
+      cxd q = rhs[o + a];
+      cxd rr = q - hv;
+      res[o + a] = rr;
+      sr += cabs2(rr);
+      sq += cabs2(q);
+    }
+  }
+  *rn = sr;
+  *qn = sq;
+}
+
+// x = H^-1 rhs by elimination of the subdomain unknowns, sweeps in precision R:
+//   z = B^-1 rhs_B;  y = S^-1 (rhs_C - E^T z);  x_B = z - B^-1 E y;  x_C = y.
+// zero_B: rhs_B = 0 is known, so z = 0 and its sweep is skipped.
+template <typename R>
+__device__ int solve_H(cg::cluster_group& cl, RedSmem& rs, int& phase, const Geo& g,
+                       const Bufs& b, int kf, int i, const cxd* rhs, cxd* xout, bool zero_B,
+                       double tol, cx<R>* sm, Pipe& pp, int* conv) {
+  const int A = g.A;
+  const bool has = i < g.p - 1;
+  const size_t nsub = (size_t)g.Lx * g.W;
+  cxd* Bv = ifv_ptr(g, b, kf, IF_B);
+  const cxd* rc = rhs + g.ifc_off + (size_t)i * A;
+  if (!zero_B) {
+    SweepArgs<R> sa = sweep_base<R>(g, b, kf, i);
+    sa.src = rhs + i * nsub;
+    sa.dst = xout + i * nsub;
+    sa.dst_op = 0;
+    sa.bnd_lo = bnd_ptr(g, b, kf, i, 0);
+    sa.bnd_hi = bnd_ptr(g, b, kf, i, 1);
+    sweep<R>(g, i, sa, sm, pp, sweep_cnt(g, b, kf, i));
+    cl.sync();
+    if (has) {
+      const cxd* bl_i = bnd_ptr(g, b, kf, i, 1);
+      const cxd* bl_n = bnd_ptr(g, b, kf, i + 1, 0);
+      for (int a = threadIdx.x; a < A; a += DY_THREADS)
+        Bv[(size_t)i * A + a] = rc[a] - g.t * (bl_i[a] + bl_n[a]);
+    }
+  } else if (has) {
+    for (int a = threadIdx.x; a < A; a += DY_THREADS) Bv[(size_t)i * A + a] = rc[a];
+  }
+  __syncthreads();
+  int it = schur_cocg<R>(cl, rs, phase, g, b, kf, i, tol, sm, pp, conv);
+  cl.sync();
+  const cxd* X = ifv_ptr(g, b, kf, IF_X);
+  SweepArgs<R> sb = sweep_base<R>(g, b, kf, i);
+  sb.lay_lo = (i > 0) ? X + (size_t)(i - 1) * A : nullptr;
+  sb.lay_hi = has ? X + (size_t)i * A : nullptr;
+  sb.dst = xout + i * nsub;
+  sb.dst_op = zero_B ? 3 : 2;
+  sweep<R>(g, i, sb, sm, pp, sweep_cnt(g, b, kf, i));
+  if (has) {
+    cxd* xc = xout + g.ifc_off + (size_t)i * A;
+    for (int a = threadIdx.x; a < A; a += DY_THREADS) xc[a] = X[(size_t)i * A + a];
+  }
+  return it;
+}
+
+// shared-memory plan of the solver kernels: copy ring, then partials and z
+template <typename R>
+__host__ __device__ inline int ring_stages(int W) {
+  const int slot = W * W * (int)sizeof(cx<R>);
+  int S = (96 * 1024) / slot;
+  if (S > MAX_STAGES) S = MAX_STAGES;
+  if (S < 2) S = 2;
+  return S;
+}
+template <typename R>
+__host__ __device__ inline size_t solver_smem(int W) {
+  return (size_t)ring_stages<R>(W) * W * W * sizeof(cx<R>) + (size_t)2 * W * sizeof(cx<R>);
+}
+
+// ---------------------------------------------------------------- kernels
+// u = X q_j  (Sec. 2.3 Eqs. 6-8), with u = v - w computed as the solution of
+// H u = q - H w = [0; q_C - E^T w_B]  (w = blkdiag(B^-1, 0) q, so B w_B = q_B),
+// i.e. y = S^-1 (E^T w_B - q_C), u_B = B^-1 E y, u_C = -y: no cancellation.
+//   mixed = 0: every sweep in R (= double), the interface solve to krylov_tol.
+//   mixed = 1: sweeps in complex64 (R = float).  w_B is refined against FP64
+//              residuals of B, u against FP64 residuals of H, each until the
+//              relative residual is below refine_tol.
+template <typename R>
+__global__ void __launch_bounds__(DY_THREADS, 2) k_xmatvec(Geo g, Bufs b, int j, int mixed) {
+  cg::cluster_group cl = cg::this_cluster();
+  __shared__ RedSmem rs;
+  __shared__ __align__(8) uint64_t bars[MAX_STAGES];
+  __shared__ int err;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int i = blockIdx.x, kf = blockIdx.y, p = g.p, A = g.A;
+  int* st = b.st + (size_t)kf * ST_N;
+  if (st[ST_DONE]) return;                 // same value in every CTA of the cluster
+  Pipe pp;
+  pp.bar = bars;
+  pp.S = ring_stages<R>(g.W);
+  pp.ring = smem_raw;
+  pp.seq = 0;
+  pp.err = &err;
+  pipe_init(pp);
+  cx<R>* sm = reinterpret_cast<cx<R>*>(smem_raw + (size_t)pp.S * g.W * g.W * sizeof(cx<R>));
+  int phase = 0;
+  const bool has = i < p - 1;
+  const size_t Ndd = g.Ndd, nsub = (size_t)g.Lx * g.W;
+  const cxd* q = b.Q + ((size_t)kf * (g.k_max + 1) + j) * Ndd;
+  cxd* u = b.u + (size_t)kf * Ndd;
+  int iters = 0, solves = 0, refines = 0, conv_all = 1, conv = 1;
+
+  if (!mixed) {
+    // w = B^-1 q_B, only its boundary rows are needed: E^T w
+    SweepArgs<R> sa = sweep_base<R>(g, b, kf, i);
+    sa.src = q + i * nsub;
+    sa.bnd_lo = bnd_ptr(g, b, kf, i, 0);
+    sa.bnd_hi = bnd_ptr(g, b, kf, i, 1);
+    sweep<R>(g, i, sa, sm, pp, sweep_cnt(g, b, kf, i));
+    cl.sync();
+    cxd* Bv = ifv_ptr(g, b, kf, IF_B);
+    if (has) {
+      const cxd* bl_i = bnd_ptr(g, b, kf, i, 1);
+      const cxd* bl_n = bnd_ptr(g, b, kf, i + 1, 0);
+      const cxd* qc = q + g.ifc_off + (size_t)i * A;
+      for (int a = threadIdx.x; a < A; a += DY_THREADS)
+        Bv[(size_t)i * A + a] = g.t * (bl_i[a] + bl_n[a]) - qc[a];
+    }
+    __syncthreads();
+    iters += schur_cocg<R>(cl, rs, phase, g, b, kf, i, g.krylov_tol, sm, pp, &conv);
+    conv_all &= conv;
+    solves = 1;
+    cl.sync();
+    const cxd* X = ifv_ptr(g, b, kf, IF_X);
+    SweepArgs<R> sb = sweep_base<R>(g, b, kf, i);
+    sb.lay_lo = (i > 0) ? X + (size_t)(i - 1) * A : nullptr;
+    sb.lay_hi = has ? X + (size_t)i * A : nullptr;
+    sb.dst = u + i * nsub;
+    sb.dst_op = 0;
+    sweep<R>(g, i, sb, sm, pp, sweep_cnt(g, b, kf, i));
+    if (has) {
+      cxd* uc = u + g.ifc_off + (size_t)i * A;
+      for (int a = threadIdx.x; a < A; a += DY_THREADS) uc[a] = -X[(size_t)i * A + a];
+    }
+  } else {
+    cxd* wv = b.v1 + (size_t)kf * Ndd;   // w_B, later the refinement corrections
+    cxd* rv = b.v2 + (size_t)kf * Ndd;   // FP64 residuals
+    cxd* hr = b.v3 + (size_t)kf * Ndd;   // right-hand side [0; q_C - E^T w_B]
+    // ---- w_B = B^-1 q_B, refined against FP64 residuals of B (subdomain-local)
+    {
+      SweepArgs<R> sa = sweep_base<R>(g, b, kf, i);
+      sa.src = q + i * nsub;
+      sa.dst = wv + i * nsub;
+      sa.dst_op = 0;
+      sweep<R>(g, i, sa, sm, pp, sweep_cnt(g, b, kf, i));
+      for (int r = 0; r < g.refine_max; ++r) {
+        __syncthreads();
+        double rn, qn;
+        residual_H(g, b, kf, i, q, wv, rv, 1, &rn, &qn);
+        cxd v2[2] = {{rn, 0}, {qn, 0}};
+        block_sum<2>(rs, v2);
+        if (v2[0].x <= g.refine_tol * g.refine_tol * v2[1].x) break;
+        SweepArgs<R> sc = sweep_base<R>(g, b, kf, i);
+        sc.src = rv + i * nsub;
+        sc.dst = wv + i * nsub;
+        sc.dst_op = 1;
+        sweep<R>(g, i, sc, sm, pp, sweep_cnt(g, b, kf, i));
+      }
+    }
+    cl.sync();                             // w_B of the neighbour subdomains is final
+    {
+      const int n = own_count(g, i);
+      const int hi = g.T * (g.h[i] - 1);
+      for (int e = threadIdx.x; e < n; e += DY_THREADS) {
+        size_t k = own_idx(g, i, e, (int)nsub);
+        cxd v = {0, 0};
+        if (e >= (int)nsub) {
+          const int a = e - (int)nsub, xx = a % g.Lx, tr = a / g.Lx;
+          const cxd ew = wv[i * nsub + (size_t)xx * g.W + hi + tr] +
+                         wv[(i + 1) * nsub + (size_t)xx * g.W + tr];
+          v = q[k] - g.t * ew;
+        }
+        hr[k] = v;
+      }
+    }
+    cl.sync();                             // every CTA has read w_B before it is reused
+    iters += solve_H<R>(cl, rs, phase, g, b, kf, i, hr, u, true, g.krylov_tol, sm, pp, &conv);
+    conv_all &= conv;
+    ++solves;
+    for (int r = 0; r < g.refine_max; ++r) {
+      cl.sync();
+      double rn, qn;
+      residual_H(g, b, kf, i, hr, u, rv, 0, &rn, &qn);
+      cxd v2[2] = {{rn, 0}, {qn, 0}};
+      cluster_sum<2>(cl, rs, phase, p, v2);
+      if (v2[0].x <= g.refine_tol * g.refine_tol * v2[1].x) break;
+      ++refines;
+      iters += solve_H<R>(cl, rs, phase, g, b, kf, i, rv, wv, false, g.krylov_tol, sm, pp, &conv);
+      conv_all &= conv;
+      ++solves;
+      __syncthreads();
+      const int n = own_count(g, i);
+      for (int e = threadIdx.x; e < n; e += DY_THREADS) {
+        size_t k = own_idx(g, i, e, (int)nsub);
+        u[k] = u[k] + wv[k];
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && err) atomicOr(st + ST_STATUS, ST_WAIT_TIMEOUT);
+  if (i == 0 && threadIdx.x == 0) {
+    st[ST_ITERS] += iters;
+    st[ST_SOLVES] += solves;
+    st[ST_REFINE] += refines;
+    if (!conv_all) st[ST_STATUS] |= 4;
+  }
+}
+
+// One step of complex-symmetric Lanczos on X with the bilinear form
+// (Sec. 2.1, Freund et al.), full CGS2 re-orthogonalisation in the same form,
+// and the three-vector update of diag(Q T Q^T) (Sec. 2.3 after Eq. 9).
+__global__ void __launch_bounds__(DY_THREADS) k_lanczos(Geo g, Bufs b, int j) {
+  cg::cluster_group cl = cg::this_cluster();
+  __shared__ RedSmem rs;
+  __shared__ cxd hs[KMAX_SMEM];
+  const int i = blockIdx.x, kf = blockIdx.y, p = g.p;
+  int* st = b.st + (size_t)kf * ST_N;
+  if (st[ST_DONE]) return;
+  int phase = 0;
+  const size_t Ndd = g.Ndd;
+  const int nsub = g.Lx * g.W, n = own_count(g, i);
+  cxd* Q = b.Q + (size_t)kf * (g.k_max + 1) * Ndd;
+  const cxd* qj = Q + (size_t)j * Ndd;
+  const cxd* qm = (j > 0) ? Q + (size_t)(j - 1) * Ndd : nullptr;
+  cxd* r = Q + (size_t)(j + 1) * Ndd;
+  const cxd* u = b.u + (size_t)kf * Ndd;
+  cxd* acc = b.acc + (size_t)kf * Ndd;
+  cxd* lan = b.lan + (size_t)kf * (g.k_max + 1) * 2;
+  const cxd beta_j = (j > 0) ? lan[2 * j + 1] : cxd{0, 0};
+
+  cxd v1[1] = {{0, 0}};
+  for (int e = threadIdx.x; e < n; e += DY_THREADS) {
+    size_t k = own_idx(g, i, e, nsub);
+    v1[0] = cfma(qj[k], u[k], v1[0]);
+  }
+  cluster_sum<1>(cl, rs, phase, p, v1);
+  const cxd alpha = v1[0];
+  for (int e = threadIdx.x; e < n; e += DY_THREADS) {
+    size_t k = own_idx(g, i, e, nsub);
+    cxd rv = u[k] - alpha * qj[k];
+    if (qm) rv = rv - beta_j * qm[k];
+    r[k] = rv;
+  }
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int c0 = 0; c0 <= j; c0 += 8) {
+      cxd h8[8];
+#pragma unroll
+      for (int m = 0; m < 8; ++m) h8[m] = cxd{0, 0};
+      for (int e = threadIdx.x; e < n; e += DY_THREADS) {
+        size_t k = own_idx(g, i, e, nsub);
+        cxd rv = r[k];
+#pragma unroll
+        for (int m = 0; m < 8; ++m)
+          if (c0 + m <= j) h8[m] = cfma(Q[(size_t)(c0 + m) * Ndd + k], rv, h8[m]);
+      }
+      cluster_sum<8>(cl, rs, phase, p, h8);
+      if (threadIdx.x < 8 && c0 + threadIdx.x <= j) hs[c0 + threadIdx.x] = h8[threadIdx.x];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n; e += DY_THREADS) {
+      size_t k = own_idx(g, i, e, nsub);
+      cxd rv = r[k];
+      for (int m = 0; m <= j; ++m) rv = rv - hs[m] * Q[(size_t)m * Ndd + k];
+      r[k] = rv;
+    }
+    __syncthreads();
+  }
+  cxd v2[2] = {{0, 0}, {0, 0}};
+  for (int e = threadIdx.x; e < n; e += DY_THREADS) {
+    size_t k = own_idx(g, i, e, nsub);
+    cxd rv = r[k];
+    v2[0] = cfma(rv, rv, v2[0]);
+    v2[1].x += cabs2(rv);
+    cxd a = acc[k] + alpha * (qj[k] * qj[k]);
+    if (qm) a = a + (2.0 * beta_j) * (qm[k] * qj[k]);
+    acc[k] = a;
+  }
+  cluster_sum<2>(cl, rs, phase, p, v2);
+  const cxd rr = v2[0];
+  const cxd beta = csqrt_principal(rr);
+  const double maxT = fmax(b.maxT[kf], sqrt(cabs2(alpha)));
+  const double babs = sqrt(cabs2(beta));
+  int done = 0, flag = 0;
+  if (j == g.k_max - 1) {
+    done = 1;
+  } else if (babs <= TERM_TOL * maxT) {
+    done = 1;
+    flag = 1;
+  } else if (sqrt(cabs2(rr)) <= BRK_TOL * v2[1].x) {
+    done = 1;
+    flag = 2;
+  }
+  if (!done) {
+    const cxd ib = cinv(beta);
+    for (int e = threadIdx.x; e < n; e += DY_THREADS) {
+      size_t k = own_idx(g, i, e, nsub);
+      r[k] = r[k] * ib;
+    }
+  }
+  if (i == 0 && threadIdx.x == 0) {
+    lan[2 * j] = alpha;
+    st[ST_STEPS] = j + 1;
+    if (done) {
+      st[ST_DONE] = 1;
+      st[ST_STATUS] |= flag;
+    } else {
+      lan[2 * (j + 1) + 1] = beta;
+      b.maxT[kf] = fmax(maxT, babs);
+    }
+  }
+}
+
+// Gather the real start vector into DD layout and normalise it in the
+// bilinear form: q_1 = q / sqrt(q^T q).  Clears the per-frequency state.
+__global__ void __launch_bounds__(DY_THREADS) k_init(Geo g, Bufs b) {
+  cg::cluster_group cl = cg::this_cluster();
+  __shared__ RedSmem rs;
+  const int i = blockIdx.x, kf = blockIdx.y;
+  int phase = 0;
+  const int nsub = g.Lx * g.W, n = own_count(g, i);
+  cxd* q = b.Q + (size_t)kf * (g.k_max + 1) * g.Ndd;
+  cxd* acc = b.acc + (size_t)kf * g.Ndd;
+  cxd v1[1] = {{0, 0}};
+  for (int e = threadIdx.x; e < n; e += DY_THREADS) {
+    size_t k = own_idx(g, i, e, nsub);
+    int nat = b.dd2nat[k];
+    double v = nat >= 0 ? b.q1[nat] : 0.0;
+    q[k] = cxd{v, 0};
+    acc[k] = cxd{0, 0};
+    v1[0].x += v * v;
+  }
+  cluster_sum<1>(cl, rs, phase, g.p, v1);
+  const cxd inv = cinv(csqrt_principal(v1[0]));
+  for (int e = threadIdx.x; e < n; e += DY_THREADS) {
+    size_t k = own_idx(g, i, e, nsub);
+    q[k] = q[k] * inv;
+  }
+  if (threadIdx.x == 0 && b.sweeps) b.sweeps[(size_t)kf * g.p + i] = 0;
+  if (i == 0 && threadIdx.x == 0) {
+    int* st = b.st + (size_t)kf * ST_N;
+    for (int k = 0; k < ST_N; ++k) st[k] = 0;
+    if (g.p < 2) st[ST_DONE] = 1;        // one subdomain: X = 0, no Lanczos steps
+    cxd* lan = b.lan + (size_t)kf * (g.k_max + 1) * 2;
+    lan[0] = lan[1] = cxd{0, 0};
+    b.maxT[kf] = 0.0;
+  }
+}
+
+// diag(G) = diag(blkdiag(B^-1, 0)) + diag(Q T Q^T)  (Eq. 9), natural order.
+__global__ void k_finalize(Geo g, Bufs b) {
+  const int kf = blockIdx.y;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < (size_t)g.Ndd;
+       k += (size_t)gridDim.x * blockDim.x) {
+    int nat = b.dd2nat[k];
+    if (nat < 0) continue;
+    size_t o = (size_t)kf * g.Ndd + k;
+    b.out[(size_t)kf * g.N + nat] = b.diagB[o] + b.acc[o];
+  }
+}
+
+__global__ void k_gather(Geo g, const int* dd2nat, const cxd* nat, cxd* dd, size_t ds) {
+  const int kf = blockIdx.y;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < (size_t)g.Ndd;
+       k += (size_t)gridDim.x * blockDim.x) {
+    int n = dd2nat[k];
+    dd[(size_t)kf * ds + k] = n >= 0 ? nat[(size_t)kf * g.N + n] : cxd{0, 0};
+  }
+}
+
+__global__ void k_scatter(Geo g, const int* dd2nat, const cxd* dd, cxd* nat, size_t ds) {
+  const int kf = blockIdx.y;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < (size_t)g.Ndd;
+       k += (size_t)gridDim.x * blockDim.x) {
+    int n = dd2nat[k];
+    if (n >= 0) nat[(size_t)kf * g.N + n] = dd[(size_t)kf * ds + k];
+  }
+}
+
+__global__ void k_status(const int* st, int K, int* status) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x)
+    status[k] = st[(size_t)k * ST_N + ST_STATUS];
+}
+
+// w = blkdiag(B^-1, 0) q for DD-layout vectors (Eq. 7), one CTA per subdomain.
+template <typename R>
+__global__ void __launch_bounds__(DY_THREADS, 2) k_bsolve(Geo g, Bufs b, const cxd* q, cxd* w) {
+  __shared__ __align__(8) uint64_t bars[MAX_STAGES];
+  __shared__ int err;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int i = blockIdx.x, kf = blockIdx.y;
+  const size_t nsub = (size_t)g.Lx * g.W;
+  Pipe pp;
+  pp.bar = bars;
+  pp.S = ring_stages<R>(g.W);
+  pp.ring = smem_raw;
+  pp.seq = 0;
+  pp.err = &err;
+  pipe_init(pp);
+  cx<R>* sm = reinterpret_cast<cx<R>*>(smem_raw + (size_t)pp.S * g.W * g.W * sizeof(cx<R>));
+  SweepArgs<R> sa = sweep_base<R>(g, b, kf, i);
+  sa.src = q + (size_t)kf * g.Ndd + i * nsub;
+  sa.dst = w + (size_t)kf * g.Ndd + i * nsub;
+  sa.dst_op = 0;
+  sweep<R>(g, i, sa, sm, pp, sweep_cnt(g, b, kf, i));
+  if (i < g.p - 1)
+    for (int a = threadIdx.x; a < g.A; a += DY_THREADS)
+      w[(size_t)kf * g.Ndd + g.ifc_off + (size_t)i * g.A + a] = cxd{0, 0};
+  __syncthreads();
+  if (threadIdx.x == 0 && err) atomicOr(b.st + (size_t)kf * ST_N + ST_STATUS, ST_WAIT_TIMEOUT);
+}
+
+template <typename Kern, typename... Args>
+cudaError_t launch_cluster(Kern kern, dim3 grid, int cx_, size_t smem, cudaStream_t st,
+                           Args... args) {
+  cudaError_t e;
+  if (smem > 48 * 1024) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  if (cx_ > 8) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(DY_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cx_;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+template <typename R>
+size_t sweep_smem(const Geo& g) { return solver_smem<R>(g.W); }
+
+}  // namespace
+
+template <typename R>
+cudaError_t launch_xmatvec(const Geo& g, const Bufs& b, int K, int j, int mixed, cudaStream_t st) {
+  return launch_cluster(k_xmatvec<R>, dim3(g.p, K), g.p, sweep_smem<R>(g), st, g, b, j, mixed);
+}
+template cudaError_t launch_xmatvec<double>(const Geo&, const Bufs&, int, int, int, cudaStream_t);
+template cudaError_t launch_xmatvec<float>(const Geo&, const Bufs&, int, int, int, cudaStream_t);
+
+cudaError_t launch_lanczos(const Geo& g, const Bufs& b, int K, int j, cudaStream_t st) {
+  if (g.k_max > KMAX_SMEM) return cudaErrorInvalidValue;
+  return launch_cluster(k_lanczos, dim3(g.p, K), g.p, 0, st, g, b, j);
+}
+
+cudaError_t launch_init(const Geo& g, const Bufs& b, int K, cudaStream_t st) {
+  return launch_cluster(k_init, dim3(g.p, K), g.p, 0, st, g, b);
+}
+
+static dim3 flat_grid(const Geo& g, int K) {
+  int bx = (g.Ndd + DY_THREADS - 1) / DY_THREADS;
+  if (bx > 1024) bx = 1024;
+  return dim3(bx, K);
+}
+
+cudaError_t launch_finalize(const Geo& g, const Bufs& b, int K, cudaStream_t st) {
+  k_finalize<<<flat_grid(g, K), DY_THREADS, 0, st>>>(g, b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather(const Geo& g, const Bufs& b, int K, const cxd* nat, cxd* dd,
+                          size_t dd_stride, cudaStream_t st) {
+  k_gather<<<flat_grid(g, K), DY_THREADS, 0, st>>>(g, b.dd2nat, nat, dd, dd_stride);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(const Geo& g, const Bufs& b, int K, const cxd* dd, cxd* nat,
+                           size_t dd_stride, cudaStream_t st) {
+  k_scatter<<<flat_grid(g, K), DY_THREADS, 0, st>>>(g, b.dd2nat, dd, nat, dd_stride);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_status(const Geo&, const Bufs& b, int K, int* status, cudaStream_t st) {
+  k_status<<<(K + 255) / 256, 256, 0, st>>>(b.st, K, status);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_bsolve(const Geo& g, const Bufs& b, int K, const cxd* q_dd, cxd* w_dd,
+                          cudaStream_t st) {
+  size_t smem = sweep_smem<R>(g);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_bsolve<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_bsolve<R><<<dim3(g.p, K), DY_THREADS, smem, st>>>(g, b, q_dd, w_dd);
+  return cudaGetLastError();
+}
+template cudaError_t launch_bsolve<double>(const Geo&, const Bufs&, int, const cxd*, cxd*, cudaStream_t);
+template cudaError_t launch_bsolve<float>(const Geo&, const Bufs&, int, const cxd*, cxd*, cudaStream_t);

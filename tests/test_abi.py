@@ -1,0 +1,92 @@
+"""C-ABI checks that need no GPU: the library loads, exports every symbol that
+include/dyson.h declares, validates arguments, and builds the
+domain-decomposition ordering (Sec. 2.2, Fig. 1) identical to the oracle's."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import dyson_oracle as O
+from paper_1102_3137_gb300 import dyson as D
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1102_3137_gb300 import build
+    build.build()
+    return D.load()
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "dyson.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(dyson_[A-Za-z0-9_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_symbols()
+    assert len(names) >= 12
+    for n in names:
+        assert hasattr(lib, n), n
+    out = os.popen(f"nm -D --defined-only {D.LIB_PATH}").read()
+    for n in names:
+        assert re.search(rf"\bT {n}\b", out), n
+
+
+@pytest.mark.parametrize("L,p", [((16, 16), 2), ((128, 128), 4), ((9, 13), 3), ((4, 5, 9), 3),
+                                 ((32, 32, 32), 8), ((7, 5), 3), ((6, 1), 1)])
+def test_partition_matches_oracle(lib, L, p):
+    g = D.make_geometry(L, p=p, k_max=4, max_freqs=2)
+    h, m, dd = D.dyson_partition(g)
+    _, hh, _ = O.dd_partition(L, p)
+    assert list(h) == hh
+    sub, iface = O.dd_sites(L, p)
+    W = (max(s.shape[1] for s in sub) + 3) // 4 * 4     # slice width padded to a multiple of 4
+    ref = []
+    for s in sub:
+        blk = -np.ones((L[0], W), dtype=np.int64)
+        blk[:, :s.shape[1]] = s
+        ref.append(blk.ravel())
+    ref = np.concatenate(ref + [np.asarray(x) for x in iface])
+    assert np.array_equal(ref, dd)
+    assert m == sum(len(x) for x in iface)
+
+
+@pytest.mark.parametrize("bad", [
+    dict(L=(16, 16), p=17), dict(L=(16, 16), p=0), dict(L=(4, 4), p=3), dict(L=(16, 16), k_max=0),
+    dict(L=(16, 16), k_max=300), dict(L=(16, 16), max_freqs=0), dict(L=(16, 16), precision=5),
+])
+def test_bad_geometry_rejected_without_gpu(lib, bad):
+    kw = dict(L=(16, 16), p=2, k_max=4, max_freqs=2)
+    kw.update(bad)
+    g = D.make_geometry(**kw)
+    with pytest.raises(D.DysonError) as e:
+        D.dyson_plan_create(g)
+    assert e.value.code == -1
+    assert D.dyson_last_error()
+
+
+def test_wide_slices_reported_unsupported(lib):
+    g = D.make_geometry((32, 32, 32), p=2, k_max=4, max_freqs=1)
+    with pytest.raises(D.DysonError) as e:
+        D.dyson_plan_footprint(g)
+    assert e.value.code == -4
+
+
+def test_footprint(lib):
+    g = D.make_geometry((128, 128), p=4, k_max=32, max_freqs=64)
+    b = D.dyson_plan_footprint(g)
+    # Lanczos basis alone: 64 freqs x 33 vectors x 16768 slots x 16 B
+    assert b > 64 * 33 * 16768 * 16
+    g.precision = D.DYSON_MIXED
+    assert D.dyson_plan_footprint(g) < b * 1.5     # + complex64 copy of g_s, refinement vectors
+
+
+def test_null_plan_is_an_error(lib):
+    z = np.zeros(4)
+    with pytest.raises(D.DysonError):
+        D.dyson_solve(None, 1, z[:1], z, np.zeros(4, complex), z, np.zeros(4, complex))
