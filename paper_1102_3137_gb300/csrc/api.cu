@@ -262,7 +262,10 @@ int enqueue_solve(dyson_plan p, int K, cudaStream_t s, bool cap) {
   RUN(DYSON_KERNEL_INIT, "init", launch_init(g, p->b, K, s));
   if (p->mixed) RUN(DYSON_KERNEL_FACTOR, "factor", (launch_factor<double, float>(g, p->b, K, s)));
   else RUN(DYSON_KERNEL_FACTOR, "factor", (launch_factor<double, double>(g, p->b, K, s)));
-  if (g.p > 1) RUN(DYSON_KERNEL_PRECOND, "precond", launch_precond(g, p->b, K, s));
+  if (g.p > 1) {
+    if (p->mixed) RUN(DYSON_KERNEL_PRECOND, "precond", launch_precond<float>(g, p->b, K, s));
+    else RUN(DYSON_KERNEL_PRECOND, "precond", launch_precond<double>(g, p->b, K, s));
+  }
   if (g.p > 1) {
     for (int j = 0; j < g.k_max; ++j) {
       if (p->mixed) RUN(DYSON_KERNEL_XMATVEC, "xmatvec", launch_xmatvec<float>(g, p->b, K, j, 1, s));
@@ -598,7 +601,8 @@ int dyson_xmatvec(dyson_plan p, int K, const double* omega, const double* V, con
     qn = p->b.out;
   }
   if ((rc = enqueue_factor(p, K, s))) return rc;
-  LK(launch_precond(g, p->b, K, s));
+  if (p->mixed) LK(launch_precond<float>(g, p->b, K, s));
+  else LK(launch_precond<double>(g, p->b, K, s));
   LK(launch_gather(g, p->b, K, qn, p->b.Q, (size_t)(g.k_max + 1) * g.Ndd, s));
   CK(cudaMemsetAsync(p->b.st, 0, (size_t)K * ST_N * sizeof(int), s));
   if (g.p > 1) {

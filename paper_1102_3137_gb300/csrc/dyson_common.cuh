@@ -141,7 +141,7 @@ struct Bufs {
 };
 
 // interface Krylov vector slots inside ifv
-enum { IF_X = 0, IF_R = 1, IF_Z = 2, IF_P = 3, IF_SP = 4, IF_B = 5, IF_N = 6 };
+enum { IF_X = 0, IF_R = 1, IF_Z = 2, IF_P = 3, IF_SP = 4, IF_B = 5, IF_D = 6, IF_N = 7 };
 
 __host__ __device__ __forceinline__ size_t nifc(const Geo& g) { return (size_t)(g.p > 1 ? g.p - 1 : 1) * g.A; }
 
@@ -160,6 +160,7 @@ __device__ __forceinline__ int sub_nat(const Geo& g, int i, int s, int j) {
 // ---------------------------------------------------------------- host launchers
 template <typename R, typename S>
 cudaError_t launch_factor(const Geo& g, const Bufs& b, int K, cudaStream_t st);
+template <typename R>
 cudaError_t launch_precond(const Geo& g, const Bufs& b, int K, cudaStream_t st);
 cudaError_t launch_init(const Geo& g, const Bufs& b, int K, cudaStream_t st);
 template <typename R>

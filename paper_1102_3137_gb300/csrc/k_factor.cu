@@ -148,12 +148,14 @@ __global__ void __launch_bounds__(DY_THREADS) k_factor(Geo g, Bufs b) {
 // approximation keeps C and the diagonal of B^-1 next to the interface:
 //   M = C_x - t^2 (diag B^-1 below + diag B^-1 above),
 // with C_x the hopping along x only (in-plane y hopping dropped in 3D).
-// Thomas factors per x-line: inv_den[x] and c'[x].
+// Thomas factors per x-line, computed in FP64 and stored in precision R (the
+// precision the interface solve runs in): inv_den[x] and c'[x].
+template <typename R>
 __global__ void __launch_bounds__(DY_THREADS) k_precond(Geo g, Bufs b) {
   const int l = blockIdx.x, kf = blockIdx.y;
   const int Lx = g.Lx, T = g.T, A = g.A, W = g.W;
   const cxd* dB = b.diagB + (size_t)kf * g.Ndd;
-  cxd* pre = b.pre + ((size_t)kf * nifc(g) + (size_t)l * A) * 2;
+  cx<R>* pre = reinterpret_cast<cx<R>*>(b.pre) + ((size_t)kf * nifc(g) + (size_t)l * A) * 2;
   const double t = g.t;
   for (int tr = threadIdx.x; tr < T; tr += DY_THREADS) {
     cxd cprev = {0, 0};
@@ -168,8 +170,8 @@ __global__ void __launch_bounds__(DY_THREADS) k_precond(Geo g, Bufs b) {
       cxd den = (x == 0) ? m : m - t * cprev;
       cxd inv = cinv(den);
       cxd cp = t * inv;
-      pre[a] = inv;
-      pre[A + a] = cp;
+      pre[a] = cconv<R>(inv);
+      pre[A + a] = cconv<R>(cp);
       cprev = cp;
     }
   }
@@ -191,8 +193,11 @@ template cudaError_t launch_factor<double, double>(const Geo&, const Bufs&, int,
 template cudaError_t launch_factor<double, float>(const Geo&, const Bufs&, int, cudaStream_t);
 template cudaError_t launch_factor<float, float>(const Geo&, const Bufs&, int, cudaStream_t);
 
+template <typename R>
 cudaError_t launch_precond(const Geo& g, const Bufs& b, int K, cudaStream_t st) {
   if (g.p < 2) return cudaSuccess;
-  k_precond<<<dim3(g.p - 1, K), DY_THREADS, 0, st>>>(g, b);
+  k_precond<R><<<dim3(g.p - 1, K), DY_THREADS, 0, st>>>(g, b);
   return cudaGetLastError();
 }
+template cudaError_t launch_precond<double>(const Geo&, const Bufs&, int, cudaStream_t);
+template cudaError_t launch_precond<float>(const Geo&, const Bufs&, int, cudaStream_t);

@@ -159,6 +159,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
 struct Pipe {
   uint64_t* bar;   // [S] in static shared memory
   void* ring;      // S slots in dynamic shared memory
+  void* ybuf;      // forward intermediates in shared memory, or null (global scratch)
   int S;
   unsigned seq;    // blocks issued (= consumed) so far by this CTA
   int* err;        // shared flag: a bounded wait ran out
@@ -188,12 +189,14 @@ struct SweepArgs {
   const cx<R>* g;      // [Lx][W][W] this subdomain's factors
   cx<R>* y;            // [Lx][W] scratch for the forward intermediates
   const cxd* src;      // full right-hand side (subdomain block) or null
-  const cxd* lay_lo;   // interface layer below (i-1), boundary mode
-  const cxd* lay_hi;   // interface layer above (i), boundary mode
+  const cx<R>* lay_lo; // interface layer below (i-1), boundary mode
+  const cx<R>* lay_hi; // interface layer above (i), boundary mode
   cxd* dst;            // full solution out (subdomain block) or null
   int dst_op;          // 0 store, 1 add, 2 subtract, 3 store negated
-  cxd* bnd_lo;         // solution on the lowest slow row, layer layout (or null)
-  cxd* bnd_hi;         // solution on the highest slow row
+  double in_scale;     // src is multiplied by this when rounded to R
+  double out_scale;    // x is multiplied by this when written to dst
+  cx<R>* bnd_lo;       // solution on the lowest slow row, layer layout (or null)
+  cx<R>* bnd_hi;       // solution on the highest slow row
 };
 
 // Thread layout of the block products y = g_s z (g_s complex symmetric, so its
@@ -214,6 +217,13 @@ __host__ __device__ inline SweepLayout sweep_layout(int W) {
   return L;
 }
 
+// The sequential slice loop touches only shared memory (or the per-unit
+// scratch) and R-precision registers: a parallel pre-pass converts the
+// right-hand side into the row buffer yb (rhs_s in row s), the forward pass
+// overwrites row s with y_s, the backward pass with x_s, and a parallel
+// post-pass converts the rows to FP64 and writes the requested outputs.  On
+// GB300 FP64 issue is ~1/64 of FP32, so keeping conversions out of the
+// dependent chain matters as much as keeping global loads out of it.
 template <typename R>
 __device__ void sweep(const Geo& g, int i, const SweepArgs<R>& a, cx<R>* sm, Pipe& pp,
                       unsigned long long* cnt) {
@@ -221,6 +231,7 @@ __device__ void sweep(const Geo& g, int i, const SweepArgs<R>& a, cx<R>* sm, Pip
   const SweepLayout L = sweep_layout(W);
   cx<R>* zbuf = sm;                      // [2][W]: z of the current and of the next slice
   cx<R>* ring = reinterpret_cast<cx<R>*>(pp.ring);
+  cx<R>* yb = pp.ybuf ? reinterpret_cast<cx<R>*>(pp.ybuf) : a.y;   // [Lx][W] row buffer
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int rr = lane / L.G, cg = lane - rr * L.G;
   const int row = wid * L.RPW + rr;      // the row this lane works on
@@ -234,57 +245,49 @@ __device__ void sweep(const Geo& g, int i, const SweepArgs<R>& a, cx<R>* sm, Pip
   const uint32_t bytes = (uint32_t)(WW * sizeof(cx<R>));
   const int NL = 2 * Lx - 1;
   const int S = pp.S;
+  const int nrow = Lx * W;
   auto slice_of = [&](int n) { return n < Lx ? n : 2 * Lx - 2 - n; };
   auto issue = [&](int n) {
     const unsigned q = pp.seq + n;
     const int slot = (int)(q % S);
     bulk_load(ring + (size_t)slot * WW, a.g + (size_t)slice_of(n) * WW, bytes, pp.bar + slot);
   };
-  auto rhs = [&](int s, int j) -> cx<R> {
-    if (a.src) return cconv<R>(a.src[(size_t)s * W + j]);
-    cxd v = {0, 0};
-    if (j < w) {
-      if (a.lay_lo && j < T) v = v + g.t * a.lay_lo[s + Lx * j];
-      if (a.lay_hi && j >= w - T) v = v + g.t * a.lay_hi[s + Lx * (j - (w - T))];
-    }
-    return cconv<R>(v);
-  };
-  // old value of the destination row for the add/subtract forms (0 otherwise)
-  auto dst_old = [&](int s, int j) -> cxd {
-    if (a.dst && (a.dst_op == 1 || a.dst_op == 2) && j < w) return a.dst[(size_t)s * W + j];
-    return cxd{0, 0};
-  };
-  auto out = [&](int s, int j, cx<R> x, cxd old) {
-    if (j >= w) return;
-    cxd xd = cconv<double>(x);
-    if (a.dst) {
-      cxd* d = a.dst + (size_t)s * W + j;
-      if (a.dst_op == 0) *d = xd;
-      else if (a.dst_op == 1) *d = old + xd;
-      else if (a.dst_op == 2) *d = old - xd;
-      else *d = -xd;
-    }
-    if (a.bnd_lo && j < T) a.bnd_lo[s + Lx * j] = xd;
-    if (a.bnd_hi && j >= w - T) a.bnd_hi[s + Lx * (j - (w - T))] = xd;
-  };
 
-  __syncthreads();                       // previous users of ring and zbuf are done
+  __syncthreads();                       // previous users of ring, zbuf and yb are done
   if (tid == 0) {
     fence_proxy_async();
     for (int n = 0; n < S && n < NL; ++n) issue(n);
   }
-  // Per-row values the critical path needs are loaded two slices ahead:
-  // forward f1, f2 = rhs(s+1), rhs(s+2); backward y1, y2 = y_s, y_{s-1} and
-  // o1, o2 = old destination values of the same rows.
-  cx<R> f1 = {0, 0}, f2 = {0, 0}, y1 = {0, 0}, y2 = {0, 0};
-  cxd o1 = {0, 0}, o2 = {0, 0};
-  if (owner) {
-    zbuf[row] = rhs(0, row);
-    if (Lx > 1) f1 = rhs(1, row);
-    if (Lx > 2) f2 = rhs(2, row);
+  // ---- pre-pass: right-hand side rows in R precision
+  for (int e = tid; e < nrow; e += DY_THREADS) {
+    const int s = e / W, j = e - s * W;
+    cxd v = {0, 0};
+    if (j < w) {
+      if (a.src) {
+        v = a.in_scale * a.src[e];
+      } else {
+        cx<R> u = {0, 0};
+        if (a.lay_lo && j < T) u = u + t * a.lay_lo[s + Lx * j];
+        if (a.lay_hi && j >= w - T) u = u + t * a.lay_hi[s + Lx * (j - (w - T))];
+        yb[e] = u;
+        continue;
+      }
+    }
+    yb[e] = cconv<R>(v);
   }
   __syncthreads();
-  for (int n = 0; n < NL; ++n) {
+  if (owner) zbuf[row] = yb[row];
+  // Rows are read two slices ahead into ping-pong registers: with yb in shared
+  // memory this costs nothing, with the global scratch it hides the latency.
+  cx<R> fA = {0, 0}, fB = {0, 0};
+  if (owner) {
+    if (Lx > 1) fA = yb[W + row];
+    if (Lx > 2) fB = yb[2 * W + row];
+  }
+  __syncthreads();
+
+  // one slice of either pass: wait for g_s, row products, butterfly
+  auto product = [&](int n) -> cx<R> {
     const unsigned q = pp.seq + n;
     const int slot = (int)(q % S);
     if (!mbar_wait(pp.bar + slot, (q / S) & 1u)) *pp.err = 1;
@@ -306,45 +309,67 @@ __device__ void sweep(const Geo& g, int i, const SweepArgs<R>& a, cx<R>* sm, Pip
       acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
       acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
     }
-    if (owner) {
-      const cx<R> m = acc;
-      cx<R>* zn = zbuf + ((n + 1) & 1) * W;
-      const int s = slice_of(n);
-      if (n < Lx) {                      // forward pass
-        a.y[(size_t)s * W + row] = m;
-        if (s + 1 < Lx) {
-          zn[row] = f1 - t * m;
-          f1 = f2;
-          if (s + 3 < Lx) f2 = rhs(s + 3, row);
-        } else {
-          zn[row] = m;                   // x_{Lx-1} = y_{Lx-1}
-          out(s, row, m, dst_old(s, row));
-        }
-        if (s == Lx - 1 && Lx > 1) {     // start the backward prefetch
-          y1 = a.y[(size_t)(Lx - 2) * W + row];
-          o1 = dst_old(Lx - 2, row);
-          if (Lx > 2) {
-            y2 = a.y[(size_t)(Lx - 3) * W + row];
-            o2 = dst_old(Lx - 3, row);
-          }
-        }
-      } else {                           // backward pass
-        cx<R> xv = y1 - t * m;
-        out(s, row, xv, o1);
-        zn[row] = xv;
-        y1 = y2;
-        o1 = o2;
-        if (s >= 2) {
-          y2 = a.y[(size_t)(s - 2) * W + row];
-          o2 = dst_old(s - 2, row);
-        }
-      }
-    }
+    return acc;
+  };
+  auto finish = [&](int n) {
     __syncthreads();                     // slot n and z of slice n fully read; z of n+1 written
     if (tid == 0 && n + S < NL) {
       fence_proxy_async();
       issue(n + S);
     }
+  };
+  // forward: y_s = g_s (rhs_s - t y_{s-1}); row s of yb becomes y_s
+  auto fwd = [&](int s, cx<R>& f) {
+    const cx<R> m = product(s);
+    if (owner) {
+      cx<R>* zn = zbuf + ((s + 1) & 1) * W;
+      yb[(size_t)s * W + row] = m;
+      zn[row] = (s + 1 < Lx) ? f - t * m : m;   // x_{Lx-1} = y_{Lx-1}
+      if (s + 3 < Lx) f = yb[(size_t)(s + 3) * W + row];
+    }
+    finish(s);
+  };
+  for (int s = 0; s < Lx; s += 2) {
+    fwd(s, fA);
+    if (s + 1 < Lx) fwd(s + 1, fB);
+  }
+  // backward: x_s = y_s - t g_s x_{s+1}; row s of yb becomes x_s
+  cx<R> yA = {0, 0}, yB = {0, 0};
+  if (owner && Lx > 1) {
+    yA = yb[(size_t)(Lx - 2) * W + row];
+    if (Lx > 2) yB = yb[(size_t)(Lx - 3) * W + row];
+  }
+  auto bwd = [&](int s, cx<R>& yv) {
+    const int n = 2 * Lx - 2 - s;
+    const cx<R> m = product(n);
+    if (owner) {
+      cx<R>* zn = zbuf + ((n + 1) & 1) * W;
+      const cx<R> xv = yv - t * m;
+      yb[(size_t)s * W + row] = xv;
+      zn[row] = xv;
+      if (s >= 2) yv = yb[(size_t)(s - 2) * W + row];
+    }
+    finish(n);
+  };
+  for (int s = Lx - 2; s >= 0; s -= 2) {
+    bwd(s, yA);
+    if (s - 1 >= 0) bwd(s - 1, yB);
+  }
+  // ---- post-pass: x rows to FP64 outputs
+  for (int e = tid; e < nrow; e += DY_THREADS) {
+    const int s = e / W, j = e - s * W;
+    if (j >= w) continue;
+    const cx<R> xr = yb[e];
+    if (a.dst) {
+      const cxd xd = a.out_scale * cconv<double>(xr);
+      cxd* d = a.dst + e;
+      if (a.dst_op == 0) *d = xd;
+      else if (a.dst_op == 1) *d = *d + xd;
+      else if (a.dst_op == 2) *d = *d - xd;
+      else *d = -xd;
+    }
+    if (a.bnd_lo && j < T) a.bnd_lo[s + Lx * j] = xr;
+    if (a.bnd_hi && j >= w - T) a.bnd_hi[s + Lx * (j - (w - T))] = xr;
   }
   pp.seq += NL;
   if (tid == 0 && cnt) *cnt += 1;
@@ -360,6 +385,7 @@ __device__ __forceinline__ SweepArgs<R> sweep_base(const Geo& g, const Bufs& b, 
   a.lay_lo = a.lay_hi = nullptr;
   a.dst = nullptr;
   a.dst_op = 0;
+  a.in_scale = a.out_scale = 1.0;
   a.bnd_lo = a.bnd_hi = nullptr;
   return a;
 }
@@ -367,96 +393,228 @@ __device__ __forceinline__ SweepArgs<R> sweep_base(const Geo& g, const Bufs& b, 
 __device__ __forceinline__ unsigned long long* sweep_cnt(const Geo& g, const Bufs& b, int kf, int i) {
   return b.sweeps ? b.sweeps + (size_t)kf * g.p + i : nullptr;
 }
-__device__ __forceinline__ cxd* bnd_ptr(const Geo& g, const Bufs& b, int kf, int i, int hi) {
-  return b.bnd + (((size_t)kf * g.p + i) * 2 + hi) * g.A;
+// boundary-row values and interface vectors are kept in the sweep precision R
+// (their buffers are sized for complex128, so either precision fits)
+template <typename R>
+__device__ __forceinline__ cx<R>* bnd_ptr(const Geo& g, const Bufs& b, int kf, int i, int hi) {
+  return reinterpret_cast<cx<R>*>(b.bnd) + (((size_t)kf * g.p + i) * 2 + hi) * g.A;
 }
-__device__ __forceinline__ cxd* ifv_ptr(const Geo& g, const Bufs& b, int kf, int slot) {
-  return b.ifv + ((size_t)kf * IF_N + slot) * nifc(g);
+template <typename R>
+__device__ __forceinline__ cx<R>* ifv_ptr(const Geo& g, const Bufs& b, int kf, int slot) {
+  return reinterpret_cast<cx<R>*>(b.ifv) + ((size_t)kf * IF_N + slot) * nifc(g);
 }
 
 // ---------------------------------------------------------------- interface pieces
-// Apply the tridiagonal preconditioner along x lines of layer i: z = M^-1 r.
-__device__ void precond_apply(const Geo& g, const Bufs& b, int kf, int i, const cxd* r, cxd* z) {
+template <typename R>
+__device__ __forceinline__ cx<R> shfl_up_c(cx<R> v, int d) {
+  return {__shfl_up_sync(0xffffffffu, v.x, d), __shfl_up_sync(0xffffffffu, v.y, d)};
+}
+template <typename R>
+__device__ __forceinline__ cx<R> shfl_down_c(cx<R> v, int d) {
+  return {__shfl_down_sync(0xffffffffu, v.x, d), __shfl_down_sync(0xffffffffu, v.y, d)};
+}
+
+// Apply the tridiagonal preconditioner along the x lines of layer i: z = M^-1 r.
+// Thomas substitution written as compositions of affine maps, one warp per
+// line, 128 sites (4 per lane) per pass with the boundary value carried from
+// pass to pass: forward d'_x = a_x d'_{x-1} + b_x (a_x = -t inv_x,
+// b_x = r_x inv_x), stored in z; backward z_x = -c'_x z_{x+1} + d'_x.  Each
+// lane composes the maps of its 4 sites, a 5-step warp scan composes across
+// lanes, then the lanes finish their sites: ~9 dependent steps per 128 sites.
+template <typename R>
+__device__ void precond_apply(const Geo& g, const Bufs& b, int kf, int i,
+                              const cx<R>* __restrict__ r, cx<R>* __restrict__ z) {
+  constexpr int E = 4, CH = 32 * E;
   const int Lx = g.Lx, A = g.A;
-  const cxd* pre = b.pre + ((size_t)kf * nifc(g) + (size_t)i * A) * 2;
-  const double t = g.t;
-  for (int tr = threadIdx.x; tr < g.T; tr += DY_THREADS) {
+  const cx<R>* __restrict__ pre = reinterpret_cast<const cx<R>*>(b.pre) + ((size_t)kf * nifc(g) + (size_t)i * A) * 2;
+  const R t = (R)g.t;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int tr = wid; tr < g.T; tr += DY_WARPS) {
     const int o = Lx * tr;
-    cxd prev = r[o] * pre[o];
-    z[o] = prev;
-    for (int x = 1; x < Lx; ++x) {
-      prev = (r[o + x] - t * prev) * pre[o + x];
-      z[o + x] = prev;
+    cx<R> carry = {0, 0};                  // d'_{c0-1}
+    for (int c0 = 0; c0 < Lx; c0 += CH) {
+      const int x0 = c0 + lane * E;
+      cx<R> av[E], bv[E];
+      cx<R> FA = {1, 0}, FB = {0, 0};
+#pragma unroll
+      for (int k = 0; k < E; ++k) {
+        av[k] = cx<R>{1, 0};
+        bv[k] = cx<R>{0, 0};
+        if (x0 + k < Lx) {
+          const cx<R> inv = pre[o + x0 + k];
+          av[k] = (x0 + k == 0) ? cx<R>{0, 0} : (-t) * inv;
+          bv[k] = r[o + x0 + k] * inv;
+        }
+        FB = av[k] * FB + bv[k];
+        FA = av[k] * FA;
+      }
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {   // inclusive scan: F_l o F_{l-d}
+        const cx<R> pa = shfl_up_c(FA, d), pb = shfl_up_c(FB, d);
+        if (lane >= d) {
+          FB = FA * pb + FB;
+          FA = FA * pa;
+        }
+      }
+      cx<R> v = shfl_up_c(FA * carry + FB, 1);   // d' before this lane's sites
+      if (lane == 0) v = carry;
+      else {
+        // shfl_up_c moved F_{l-1}(carry) of the previous lane
+      }
+#pragma unroll
+      for (int k = 0; k < E; ++k) {
+        v = av[k] * v + bv[k];
+        if (x0 + k < Lx) z[o + x0 + k] = v;
+      }
+      carry = cx<R>{__shfl_sync(0xffffffffu, v.x, 31), __shfl_sync(0xffffffffu, v.y, 31)};
     }
-    cxd nxt = z[o + Lx - 1];
-    for (int x = Lx - 2; x >= 0; --x) {
-      nxt = z[o + x] - pre[A + o + x] * nxt;
-      z[o + x] = nxt;
+    __syncwarp();
+    cx<R> cz = {0, 0};                     // z_{c1+1}
+    const int nch = (Lx + CH - 1) / CH;
+    for (int c = nch - 1; c >= 0; --c) {
+      const int x0 = c * CH + lane * E;
+      cx<R> av[E], dv[E];
+      cx<R> HA = {1, 0}, HB = {0, 0};
+#pragma unroll
+      for (int k = E - 1; k >= 0; --k) {
+        const int x = x0 + k;
+        av[k] = cx<R>{1, 0};
+        dv[k] = cx<R>{0, 0};
+        if (x < Lx) {
+          av[k] = (x == Lx - 1) ? cx<R>{0, 0} : -pre[A + o + x];
+          dv[k] = z[o + x];
+        }
+        HB = av[k] * HB + dv[k];
+        HA = av[k] * HA;
+      }
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {   // inclusive suffix scan: H_l o H_{l+d}
+        const cx<R> na = shfl_down_c(HA, d), nb = shfl_down_c(HB, d);
+        if (lane + d < 32) {
+          HB = HA * nb + HB;
+          HA = HA * na;
+        }
+      }
+      cx<R> v = shfl_down_c(HA * cz + HB, 1);     // z after this lane's sites
+      if (lane == 31) v = cz;
+#pragma unroll
+      for (int k = E - 1; k >= 0; --k) {
+        v = av[k] * v + dv[k];
+        if (x0 + k < Lx) z[o + x0 + k] = v;
+      }
+      cz = cx<R>{__shfl_sync(0xffffffffu, v.x, 0), __shfl_sync(0xffffffffu, v.y, 0)};
     }
   }
 }
 
-// (C p)[a] on layer l: the Dyson matrix restricted to the interface layer.
-__device__ __forceinline__ cxd layer_C_apply(const Geo& g, const Bufs& b, int kf, int l,
-                                             const cxd* pv, int a) {
+// (C p)[a] on layer l: the Dyson matrix restricted to the interface layer,
+// with its diagonal d_C precomputed in R precision.
+template <typename R>
+__device__ __forceinline__ cx<R> layer_C_apply(const Geo& g, const cx<R>* dC, const cx<R>* pv, int a) {
   const int Lx = g.Lx, x = a % Lx, tr = a / Lx;
-  cxd d = dyson_diag(g, b, kf, a + g.A * g.ylayer[l]);
-  cxd v = d * pv[a];
-  cxd nb = {0, 0};
+  cx<R> nb = {0, 0};
   if (x > 0) nb = nb + pv[a - 1];
   if (x < Lx - 1) nb = nb + pv[a + 1];
   if (tr > 0) nb = nb + pv[a - Lx];
   if (tr < g.T - 1) nb = nb + pv[a + Lx];
-  return v + g.t * nb;
+  return dC[a] * pv[a] + (R)g.t * nb;
 }
 
-// COCG for S y = b on the interface (S = C - E^T B^-1 E never formed).
-// Right-hand side in IF_B, solution in IF_X.  Sweeps run in precision R.
-// Returns the iteration count; *conv is set to 0 if the cap was hit.
+// ---------------------------------------------------------------- reductions in R
+template <typename R>
+__device__ __forceinline__ cx<R> warp_sum_r(cx<R> v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, off);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, off);
+  }
+  return v;
+}
+// Cluster-wide sums in R precision (partials exchanged through the same
+// shared slots as cluster_sum, widened to double there).
+template <typename R, int NV>
+__device__ void cluster_sum_r(cg::cluster_group& cl, RedSmem& rs, int& phase, int p, cx<R> (&v)[NV]) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = warp_sum_r(v[k]);
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) rs.wred[wid * 8 + k] = cconv<double>(v[k]);
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    cxd s = {0, 0};
+    for (int w = 0; w < DY_WARPS; ++w) s = s + rs.wred[w * 8 + threadIdx.x];
+    rs.slot[phase * 8 + threadIdx.x] = s;
+  }
+  cl.sync();
+  if (threadIdx.x < NV) {
+    cxd s = {0, 0};
+    for (int r = 0; r < p; ++r) {
+      const cxd* rem = cl.map_shared_rank(rs.slot, r);
+      s = s + rem[phase * 8 + threadIdx.x];
+    }
+    rs.res[threadIdx.x] = s;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = cconv<R>(rs.res[k]);
+  phase ^= 1;
+}
+
+// COCG for S y = b on the interface (S = C - E^T B^-1 E never formed), all in
+// precision R: the FP64 form solves to krylov_tol in FP64; the mixed form's
+// inner solves (refined in FP64 one level up) run entirely in complex64.
+// Right-hand side in IF_B, solution in IF_X.  Returns the iteration count;
+// *conv is set to 0 if the cap was hit.
 template <typename R>
 __device__ int schur_cocg(cg::cluster_group& cl, RedSmem& rs, int& phase, const Geo& g,
                           const Bufs& b, int kf, int i, double tol, cx<R>* sm, Pipe& pp,
                           int* conv) {
+  using C = cx<R>;
   const int p = g.p, A = g.A;
   const bool has = i < p - 1;
-  cxd* X = ifv_ptr(g, b, kf, IF_X);
-  cxd* Rv = ifv_ptr(g, b, kf, IF_R);
-  cxd* Z = ifv_ptr(g, b, kf, IF_Z);
-  cxd* P = ifv_ptr(g, b, kf, IF_P);
-  cxd* SP = ifv_ptr(g, b, kf, IF_SP);
-  const cxd* Bv = ifv_ptr(g, b, kf, IF_B);
+  C* X = ifv_ptr<R>(g, b, kf, IF_X);
+  C* Rv = ifv_ptr<R>(g, b, kf, IF_R);
+  C* Z = ifv_ptr<R>(g, b, kf, IF_Z);
+  C* P = ifv_ptr<R>(g, b, kf, IF_P);
+  C* SP = ifv_ptr<R>(g, b, kf, IF_SP);
+  const C* Bv = ifv_ptr<R>(g, b, kf, IF_B);
+  const C* dC = ifv_ptr<R>(g, b, kf, IF_D) + (size_t)i * A;
   const size_t o = (size_t)i * A;
-  cxd* bl_i = bnd_ptr(g, b, kf, i, 1);
-  const cxd* bl_n = has ? bnd_ptr(g, b, kf, i + 1, 0) : nullptr;
+  const C* bl_i = bnd_ptr<R>(g, b, kf, i, 1);
+  const C* bl_n = has ? bnd_ptr<R>(g, b, kf, i + 1, 0) : nullptr;
+  const R tr = (R)g.t;
 
   if (has) {
     for (int a = threadIdx.x; a < A; a += DY_THREADS) {
-      X[o + a] = cxd{0, 0};
+      X[o + a] = C{0, 0};
       Rv[o + a] = Bv[o + a];
     }
   }
   __syncthreads();
-  if (has) precond_apply(g, b, kf, i, Rv + o, Z + o);
+  if (has) precond_apply<R>(g, b, kf, i, Rv + o, Z + o);
   __syncthreads();
-  cxd v2[2] = {{0, 0}, {0, 0}};
+  C v2[2] = {{0, 0}, {0, 0}};
   if (has) {
     for (int a = threadIdx.x; a < A; a += DY_THREADS) {
-      cxd z = Z[o + a], r = Rv[o + a];
-      P[o + a] = z;
-      v2[0] = cfma(r, z, v2[0]);
+      C zz = Z[o + a], r = Rv[o + a];
+      P[o + a] = zz;
+      v2[0] = cfma(r, zz, v2[0]);
       v2[1].x += cabs2(r);
     }
   }
-  cluster_sum<2>(cl, rs, phase, p, v2);
-  cxd rho = v2[0];
-  const double bn = v2[1].x;
+  cluster_sum_r<R, 2>(cl, rs, phase, p, v2);
+  C rho = v2[0];
+  const R bn = v2[1].x;
   *conv = 1;
-  if (bn == 0.0) return 0;
+  if (bn == (R)0) return 0;
   SweepArgs<R> sa = sweep_base<R>(g, b, kf, i);
   sa.lay_lo = (i > 0) ? P + (size_t)(i - 1) * A : nullptr;
   sa.lay_hi = has ? P + o : nullptr;
-  sa.bnd_lo = bnd_ptr(g, b, kf, i, 0);
-  sa.bnd_hi = bnd_ptr(g, b, kf, i, 1);
+  sa.bnd_lo = bnd_ptr<R>(g, b, kf, i, 0);
+  sa.bnd_hi = bnd_ptr<R>(g, b, kf, i, 1);
+  const R tol2 = (R)(tol * tol);
   int it = 0;
   for (;;) {
     if (it >= g.krylov_maxit) {
@@ -467,16 +625,16 @@ __device__ int schur_cocg(cg::cluster_group& cl, RedSmem& rs, int& phase, const 
     cl.sync();                                  // P of both neighbour layers is final
     sweep<R>(g, i, sa, sm, pp, sweep_cnt(g, b, kf, i));   // B^-1 E p on this subdomain
     cl.sync();                                  // boundary values of every subdomain written
-    cxd v1[1] = {{0, 0}};
+    C v1[1] = {{0, 0}};
     if (has) {
       for (int a = threadIdx.x; a < A; a += DY_THREADS) {
-        cxd sp = layer_C_apply(g, b, kf, i, P + o, a) - g.t * (bl_i[a] + bl_n[a]);
+        C sp = layer_C_apply<R>(g, dC, P + o, a) - tr * (bl_i[a] + bl_n[a]);
         SP[o + a] = sp;
         v1[0] = cfma(P[o + a], sp, v1[0]);
       }
     }
-    cluster_sum<1>(cl, rs, phase, p, v1);
-    const cxd alpha = cdiv(rho, v1[0]);
+    cluster_sum_r<R, 1>(cl, rs, phase, p, v1);
+    const C alpha = cdiv(rho, v1[0]);
     if (has) {
       for (int a = threadIdx.x; a < A; a += DY_THREADS) {
         X[o + a] = X[o + a] + alpha * P[o + a];
@@ -484,25 +642,35 @@ __device__ int schur_cocg(cg::cluster_group& cl, RedSmem& rs, int& phase, const 
       }
     }
     __syncthreads();
-    if (has) precond_apply(g, b, kf, i, Rv + o, Z + o);
+    if (has) precond_apply<R>(g, b, kf, i, Rv + o, Z + o);
     __syncthreads();
-    v2[0] = v2[1] = cxd{0, 0};
+    v2[0] = v2[1] = C{0, 0};
     if (has) {
       for (int a = threadIdx.x; a < A; a += DY_THREADS) {
-        cxd z = Z[o + a], r = Rv[o + a];
-        v2[0] = cfma(r, z, v2[0]);
+        C zz = Z[o + a], r = Rv[o + a];
+        v2[0] = cfma(r, zz, v2[0]);
         v2[1].x += cabs2(r);
       }
     }
-    cluster_sum<2>(cl, rs, phase, p, v2);
-    if (v2[1].x <= tol * tol * bn) break;
-    const cxd beta = cdiv(v2[0], rho);
+    cluster_sum_r<R, 2>(cl, rs, phase, p, v2);
+    if (v2[1].x <= tol2 * bn) break;
+    const C beta = cdiv(v2[0], rho);
     rho = v2[0];
     if (has) {
       for (int a = threadIdx.x; a < A; a += DY_THREADS) P[o + a] = Z[o + a] + beta * P[o + a];
     }
   }
   return it;
+}
+
+// Layer diagonal d_C = i w + mu - V - Sigma on this CTA's interface layer, in
+// precision R, computed once per launch for the interface products.
+template <typename R>
+__device__ void layer_diag(const Geo& g, const Bufs& b, int kf, int i) {
+  if (i >= g.p - 1) return;
+  cx<R>* dC = ifv_ptr<R>(g, b, kf, IF_D) + (size_t)i * g.A;
+  for (int a = threadIdx.x; a < g.A; a += DY_THREADS)
+    dC[a] = cconv<R>(dyson_diag(g, b, kf, a + g.A * g.ylayer[i]));
 }
 
 // res = rhs - H x (mode 0: full H; mode 1: B only, no interface coupling),
@@ -545,7 +713,12 @@ __device__ void residual_H(const Geo& g, const Bufs& b, int kf, int i, const cxd
     const int hi = T * (g.h[i] - 1);
     for (int a = threadIdx.x; a < A; a += DY_THREADS) {
       const int xx = a % Lx, tr = a / Lx;
-      cxd hv = layer_C_apply(g, b, kf, i, xl, a);
+      cxd nb = {0, 0};
+      if (xx > 0) nb = nb + xl[a - 1];
+      if (xx < Lx - 1) nb = nb + xl[a + 1];
+      if (tr > 0) nb = nb + xl[a - Lx];
+      if (tr < T - 1) nb = nb + xl[a + Lx];
+      cxd hv = dyson_diag(g, b, kf, a + A * g.ylayer[i]) * xl[a] + t * nb;
       hv = hv + t * (xb[(size_t)xx * W + hi + tr] + xa[(size_t)xx * W + tr]);
       cxd q = rhs[o + a];
       cxd rr = q - hv;
@@ -558,65 +731,81 @@ __device__ void residual_H(const Geo& g, const Bufs& b, int kf, int i, const cxd
   *qn = sq;
 }
 
-// x = H^-1 rhs by elimination of the subdomain unknowns, sweeps in precision R:
+// x = H^-1 rhs by elimination of the subdomain unknowns, sweeps and the
+// interface solve in precision R:
 //   z = B^-1 rhs_B;  y = S^-1 (rhs_C - E^T z);  x_B = z - B^-1 E y;  x_C = y.
 // zero_B: rhs_B = 0 is known, so z = 0 and its sweep is skipped.
+// sc: the solve runs on rhs / sc and its result is scaled back by sc, so the
+// R-precision recurrences work on O(1) numbers (the squared norms of the
+// shrinking refinement residuals would leave float range otherwise).
 template <typename R>
 __device__ int solve_H(cg::cluster_group& cl, RedSmem& rs, int& phase, const Geo& g,
                        const Bufs& b, int kf, int i, const cxd* rhs, cxd* xout, bool zero_B,
-                       double tol, cx<R>* sm, Pipe& pp, int* conv) {
+                       double sc, double tol, cx<R>* sm, Pipe& pp, int* conv) {
   const int A = g.A;
   const bool has = i < g.p - 1;
   const size_t nsub = (size_t)g.Lx * g.W;
-  cxd* Bv = ifv_ptr(g, b, kf, IF_B);
+  cx<R>* Bv = ifv_ptr<R>(g, b, kf, IF_B);
   const cxd* rc = rhs + g.ifc_off + (size_t)i * A;
+  const R tr = (R)g.t;
+  const double isc = 1.0 / sc;
   if (!zero_B) {
     SweepArgs<R> sa = sweep_base<R>(g, b, kf, i);
     sa.src = rhs + i * nsub;
+    sa.in_scale = isc;
     sa.dst = xout + i * nsub;
+    sa.out_scale = sc;
     sa.dst_op = 0;
-    sa.bnd_lo = bnd_ptr(g, b, kf, i, 0);
-    sa.bnd_hi = bnd_ptr(g, b, kf, i, 1);
+    sa.bnd_lo = bnd_ptr<R>(g, b, kf, i, 0);
+    sa.bnd_hi = bnd_ptr<R>(g, b, kf, i, 1);
     sweep<R>(g, i, sa, sm, pp, sweep_cnt(g, b, kf, i));
     cl.sync();
     if (has) {
-      const cxd* bl_i = bnd_ptr(g, b, kf, i, 1);
-      const cxd* bl_n = bnd_ptr(g, b, kf, i + 1, 0);
+      const cx<R>* bl_i = bnd_ptr<R>(g, b, kf, i, 1);
+      const cx<R>* bl_n = bnd_ptr<R>(g, b, kf, i + 1, 0);
       for (int a = threadIdx.x; a < A; a += DY_THREADS)
-        Bv[(size_t)i * A + a] = rc[a] - g.t * (bl_i[a] + bl_n[a]);
+        Bv[(size_t)i * A + a] = cconv<R>(isc * rc[a]) - tr * (bl_i[a] + bl_n[a]);
     }
   } else if (has) {
-    for (int a = threadIdx.x; a < A; a += DY_THREADS) Bv[(size_t)i * A + a] = rc[a];
+    for (int a = threadIdx.x; a < A; a += DY_THREADS) Bv[(size_t)i * A + a] = cconv<R>(isc * rc[a]);
   }
   __syncthreads();
   int it = schur_cocg<R>(cl, rs, phase, g, b, kf, i, tol, sm, pp, conv);
   cl.sync();
-  const cxd* X = ifv_ptr(g, b, kf, IF_X);
+  const cx<R>* X = ifv_ptr<R>(g, b, kf, IF_X);
   SweepArgs<R> sb = sweep_base<R>(g, b, kf, i);
   sb.lay_lo = (i > 0) ? X + (size_t)(i - 1) * A : nullptr;
   sb.lay_hi = has ? X + (size_t)i * A : nullptr;
   sb.dst = xout + i * nsub;
+  sb.out_scale = sc;
   sb.dst_op = zero_B ? 3 : 2;
   sweep<R>(g, i, sb, sm, pp, sweep_cnt(g, b, kf, i));
   if (has) {
     cxd* xc = xout + g.ifc_off + (size_t)i * A;
-    for (int a = threadIdx.x; a < A; a += DY_THREADS) xc[a] = X[(size_t)i * A + a];
+    for (int a = threadIdx.x; a < A; a += DY_THREADS) xc[a] = sc * cconv<double>(X[(size_t)i * A + a]);
   }
   return it;
 }
 
-// shared-memory plan of the solver kernels: copy ring, then partials and z
+constexpr size_t YBUF_MAX = 64 * 1024;   // forward intermediates kept on chip up to this size
 template <typename R>
-__host__ __device__ inline int ring_stages(int W) {
-  const int slot = W * W * (int)sizeof(cx<R>);
-  int S = (96 * 1024) / slot;
+__host__ __device__ inline size_t ybuf_bytes(int W, int Lx) {
+  const size_t b = (size_t)Lx * W * sizeof(cx<R>);
+  return b <= YBUF_MAX ? b : 0;
+}
+// copy-ring depth: what is left of a ~100 KB per-CTA budget (two CTAs per SM)
+template <typename R>
+__host__ __device__ inline int ring_stages(int W, int Lx) {
+  const long slot = (long)W * W * (long)sizeof(cx<R>);
+  long S = ((long)100 * 1024 - (long)ybuf_bytes<R>(W, Lx)) / slot;
   if (S > MAX_STAGES) S = MAX_STAGES;
   if (S < 2) S = 2;
-  return S;
+  return (int)S;
 }
 template <typename R>
-__host__ __device__ inline size_t solver_smem(int W) {
-  return (size_t)ring_stages<R>(W) * W * W * sizeof(cx<R>) + (size_t)2 * W * sizeof(cx<R>);
+__host__ __device__ inline size_t solver_smem(int W, int Lx) {
+  return (size_t)ring_stages<R>(W, Lx) * W * W * sizeof(cx<R>) + (size_t)2 * W * sizeof(cx<R>) +
+         ybuf_bytes<R>(W, Lx);
 }
 
 // ---------------------------------------------------------------- kernels
@@ -639,12 +828,14 @@ __global__ void __launch_bounds__(DY_THREADS, 2) k_xmatvec(Geo g, Bufs b, int j,
   if (st[ST_DONE]) return;                 // same value in every CTA of the cluster
   Pipe pp;
   pp.bar = bars;
-  pp.S = ring_stages<R>(g.W);
+  pp.S = ring_stages<R>(g.W, g.Lx);
   pp.ring = smem_raw;
   pp.seq = 0;
   pp.err = &err;
   pipe_init(pp);
   cx<R>* sm = reinterpret_cast<cx<R>*>(smem_raw + (size_t)pp.S * g.W * g.W * sizeof(cx<R>));
+  pp.ybuf = ybuf_bytes<R>(g.W, g.Lx) ? (void*)(sm + 2 * g.W) : nullptr;
+  layer_diag<R>(g, b, kf, i);
   int phase = 0;
   const bool has = i < p - 1;
   const size_t Ndd = g.Ndd, nsub = (size_t)g.Lx * g.W;
@@ -656,24 +847,24 @@ __global__ void __launch_bounds__(DY_THREADS, 2) k_xmatvec(Geo g, Bufs b, int j,
     // w = B^-1 q_B, only its boundary rows are needed: E^T w
     SweepArgs<R> sa = sweep_base<R>(g, b, kf, i);
     sa.src = q + i * nsub;
-    sa.bnd_lo = bnd_ptr(g, b, kf, i, 0);
-    sa.bnd_hi = bnd_ptr(g, b, kf, i, 1);
+    sa.bnd_lo = bnd_ptr<R>(g, b, kf, i, 0);
+    sa.bnd_hi = bnd_ptr<R>(g, b, kf, i, 1);
     sweep<R>(g, i, sa, sm, pp, sweep_cnt(g, b, kf, i));
     cl.sync();
-    cxd* Bv = ifv_ptr(g, b, kf, IF_B);
+    cx<R>* Bv = ifv_ptr<R>(g, b, kf, IF_B);
     if (has) {
-      const cxd* bl_i = bnd_ptr(g, b, kf, i, 1);
-      const cxd* bl_n = bnd_ptr(g, b, kf, i + 1, 0);
+      const cx<R>* bl_i = bnd_ptr<R>(g, b, kf, i, 1);
+      const cx<R>* bl_n = bnd_ptr<R>(g, b, kf, i + 1, 0);
       const cxd* qc = q + g.ifc_off + (size_t)i * A;
       for (int a = threadIdx.x; a < A; a += DY_THREADS)
-        Bv[(size_t)i * A + a] = g.t * (bl_i[a] + bl_n[a]) - qc[a];
+        Bv[(size_t)i * A + a] = (R)g.t * (bl_i[a] + bl_n[a]) - cconv<R>(qc[a]);
     }
     __syncthreads();
     iters += schur_cocg<R>(cl, rs, phase, g, b, kf, i, g.krylov_tol, sm, pp, &conv);
     conv_all &= conv;
     solves = 1;
     cl.sync();
-    const cxd* X = ifv_ptr(g, b, kf, IF_X);
+    const cx<R>* X = ifv_ptr<R>(g, b, kf, IF_X);
     SweepArgs<R> sb = sweep_base<R>(g, b, kf, i);
     sb.lay_lo = (i > 0) ? X + (size_t)(i - 1) * A : nullptr;
     sb.lay_hi = has ? X + (size_t)i * A : nullptr;
@@ -682,7 +873,7 @@ __global__ void __launch_bounds__(DY_THREADS, 2) k_xmatvec(Geo g, Bufs b, int j,
     sweep<R>(g, i, sb, sm, pp, sweep_cnt(g, b, kf, i));
     if (has) {
       cxd* uc = u + g.ifc_off + (size_t)i * A;
-      for (int a = threadIdx.x; a < A; a += DY_THREADS) uc[a] = -X[(size_t)i * A + a];
+      for (int a = threadIdx.x; a < A; a += DY_THREADS) uc[a] = -cconv<double>(X[(size_t)i * A + a]);
     }
   } else {
     cxd* wv = b.v1 + (size_t)kf * Ndd;   // w_B, later the refinement corrections
@@ -725,11 +916,24 @@ __global__ void __launch_bounds__(DY_THREADS, 2) k_xmatvec(Geo g, Bufs b, int j,
         hr[k] = v;
       }
     }
-    cl.sync();                             // every CTA has read w_B before it is reused
-    iters += solve_H<R>(cl, rs, phase, g, b, kf, i, hr, u, true, g.krylov_tol, sm, pp, &conv);
-    conv_all &= conv;
-    ++solves;
-    for (int r = 0; r < g.refine_max; ++r) {
+    double hn;
+    {
+      cxd v1[1] = {{0, 0}};
+      if (has)
+        for (int a = threadIdx.x; a < A; a += DY_THREADS)
+          v1[0].x += cabs2(hr[g.ifc_off + (size_t)i * A + a]);
+      cluster_sum<1>(cl, rs, phase, p, v1);   // also: every CTA has read w_B before it is reused
+      hn = sqrt(v1[0].x);
+    }
+    if (hn > 0.0) {
+      iters += solve_H<R>(cl, rs, phase, g, b, kf, i, hr, u, true, hn, g.krylov_tol, sm, pp, &conv);
+      conv_all &= conv;
+      ++solves;
+    } else {
+      const int n = own_count(g, i);
+      for (int e = threadIdx.x; e < n; e += DY_THREADS) u[own_idx(g, i, e, (int)nsub)] = cxd{0, 0};
+    }
+    for (int r = 0; r < g.refine_max && hn > 0.0; ++r) {
       cl.sync();
       double rn, qn;
       residual_H(g, b, kf, i, hr, u, rv, 0, &rn, &qn);
@@ -737,7 +941,8 @@ __global__ void __launch_bounds__(DY_THREADS, 2) k_xmatvec(Geo g, Bufs b, int j,
       cluster_sum<2>(cl, rs, phase, p, v2);
       if (v2[0].x <= g.refine_tol * g.refine_tol * v2[1].x) break;
       ++refines;
-      iters += solve_H<R>(cl, rs, phase, g, b, kf, i, rv, wv, false, g.krylov_tol, sm, pp, &conv);
+      iters += solve_H<R>(cl, rs, phase, g, b, kf, i, rv, wv, false, sqrt(v2[0].x), g.krylov_tol, sm,
+                          pp, &conv);
       conv_all &= conv;
       ++solves;
       __syncthreads();
@@ -943,12 +1148,13 @@ __global__ void __launch_bounds__(DY_THREADS, 2) k_bsolve(Geo g, Bufs b, const c
   const size_t nsub = (size_t)g.Lx * g.W;
   Pipe pp;
   pp.bar = bars;
-  pp.S = ring_stages<R>(g.W);
+  pp.S = ring_stages<R>(g.W, g.Lx);
   pp.ring = smem_raw;
   pp.seq = 0;
   pp.err = &err;
   pipe_init(pp);
   cx<R>* sm = reinterpret_cast<cx<R>*>(smem_raw + (size_t)pp.S * g.W * g.W * sizeof(cx<R>));
+  pp.ybuf = ybuf_bytes<R>(g.W, g.Lx) ? (void*)(sm + 2 * g.W) : nullptr;
   SweepArgs<R> sa = sweep_base<R>(g, b, kf, i);
   sa.src = q + (size_t)kf * g.Ndd + i * nsub;
   sa.dst = w + (size_t)kf * g.Ndd + i * nsub;
@@ -989,7 +1195,7 @@ cudaError_t launch_cluster(Kern kern, dim3 grid, int cx_, size_t smem, cudaStrea
 }
 
 template <typename R>
-size_t sweep_smem(const Geo& g) { return solver_smem<R>(g.W); }
+size_t sweep_smem(const Geo& g) { return solver_smem<R>(g.W, g.Lx); }
 
 }  // namespace
 
