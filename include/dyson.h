@@ -224,6 +224,32 @@ int dyson_work_counters(dyson_plan plan, int K, unsigned long long* sweeps);
  */
 int dyson_lanczos_basis(dyson_plan plan, int k, int nvec, double* Q);
 
+/*
+ * Allocation-free variant of dyson_subdomain_diag.  The paper has no
+ * counterpart: this exists for callers that cannot call cudaMalloc at all
+ * (work inside a captured or replayed CUDA graph that must not allocate,
+ * processes whose device memory is reserved up front, embedders that pass only
+ * their own buffers).  No plan is needed and nothing is allocated: omega [K],
+ * V [N], sigma complex[K][N] and the output diagB complex[K][N] are the
+ * caller's DEVICE pointers on the current device; the work is enqueued on
+ * `stream` in the FP64 form and the call returns without waiting.
+ *
+ * All other storage lives in one fixed device array of
+ * DYSON_NOALLOC_SCRATCH_BYTES that the library reserves statically: every GPU
+ * that loads the library holds it until the process exits.  A geometry and K
+ * that need more (index map + K x (subdomain-first diagonal + slice factors))
+ * are rejected with DYSON_E_BUDGET and a message naming the bytes needed; use
+ * fewer frequencies per call.  All calls share the array and it keeps the last
+ * call's contents; calls whose work overlaps on the GPU (other streams or
+ * threads) race on it, so callers must serialise them.  The first call on a
+ * device looks up the array's device address (once per device), so make that
+ * first call before any stream capture that should contain later calls.
+ */
+#define DYSON_NOALLOC_SCRATCH_BYTES (32u << 20)
+int dyson_subdomain_diag_noalloc(const dyson_geometry* geom, int K, const double* omega,
+                                 const double* V, const double* sigma, double* diagB,
+                                 void* stream);
+
 #ifdef __cplusplus
 }
 #endif

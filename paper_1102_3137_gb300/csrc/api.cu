@@ -145,6 +145,8 @@ size_t layout(const Geo& g, int K, bool mixed, size_t off[B_COUNT]) {
 
 }  // namespace
 
+int dyson_internal_fail(int code, const std::string& msg) { return fail(code, msg); }
+
 struct dyson_plan_s {
   dyson_geometry gi;
   Geo g;

@@ -15,6 +15,8 @@
 #pragma once
 
 #include <cstdint>
+#include <string>
+
 #include <cuda_runtime.h>
 
 #define DY_MAXP 16          // largest cluster (one CTA per subdomain)
@@ -156,6 +158,10 @@ __device__ __forceinline__ int sub_nat(const Geo& g, int i, int s, int j) {
   int tr = j % g.T, sl = j / g.T;
   return s + g.Lx * tr + g.A * (g.s0[i] + sl);
 }
+
+// ---------------------------------------------------------------- host helpers
+// Record msg as this thread's dyson_last_error() and return code.
+int dyson_internal_fail(int code, const std::string& msg);
 
 // ---------------------------------------------------------------- host launchers
 template <typename R, typename S>

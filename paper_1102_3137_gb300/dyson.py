@@ -74,6 +74,7 @@ def load(path: str = LIB_PATH):
         "dyson_profile_read": ([P, I, P, P, P], I),
         "dyson_work_counters": ([P, I, P], I),
         "dyson_lanczos_basis": ([P, I, I, P], I),
+        "dyson_subdomain_diag_noalloc": ([C.POINTER(dyson_geometry), I, P, P, P, P, P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -261,6 +262,16 @@ def dyson_work_counters(plan, K, p):
     out = np.zeros((K, p), np.uint64)
     _check(load().dyson_work_counters(plan, K, out.ctypes.data))
     return out
+
+
+def dyson_subdomain_diag_noalloc(geom, K, omega, V, sigma, diagB, stream=None):
+    """Allocation-free diag(blkdiag(B^-1, 0)): device arrays only, no plan (see dyson.h)."""
+    N = V.shape[0] if hasattr(V, "shape") else len(V)
+    if _kinds(omega, V, sigma, diagB) != DYSON_MEM_DEVICE:
+        raise TypeError("dyson_subdomain_diag_noalloc takes CUDA tensors only")
+    _check(load().dyson_subdomain_diag_noalloc(C.byref(geom), K, _ptr(omega, "f8", K), _ptr(V, "f8", N),
+                                               _ptr(sigma, "c16", K * N), _ptr(diagB, "c16", K * N),
+                                               _stream(stream)))
 
 
 def dyson_lanczos_basis(plan, k, nvec, N):
