@@ -359,6 +359,81 @@ def run_reference(a, rank, world):
         gpu_launches=0)
 
 
+# ----------------------------------------------------------------- serving stream
+SERVE_SIZES = [((64, 64), 4, 32), ((128, 128), 4, 32)]
+
+
+def run_serving(a):
+    """Open-loop Poisson arrivals of Dyson solves from simulated IDMFT loops.
+
+    Lattices drawn from 64^2 (p=4, k=32) and 128^2 (p=4, k=32), K uniform in
+    [8, 32], a fresh seeded self-energy per request.  The plain-FP64 capacity
+    is measured first by solving every request alone, one after the other;
+    the stream then arrives at rate_frac x that capacity and is served by the
+    continuous-batching server (mixed form, plans resident and reused).
+    """
+    import numpy as np
+    import torch
+    from paper_1102_3137_gb300 import build as B
+    from paper_1102_3137_gb300 import dyson as D
+    from paper_1102_3137_gb300 import inputs as I
+    B.build()
+    D.load()
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(5)
+    reqs = []
+    for n in range(a.requests):
+        L, p, k = SERVE_SIZES[int(rng.integers(len(SERVE_SIZES)))]
+        K = int(rng.integers(8, 33))
+        w = I.Workload("serve", L, -1.0, 0.0, 0.01, 0.5, 20.0, K, p, k, 1000 + n)
+        omega, V, sigma, q1 = I.make_inputs(w)
+        pin = lambda x: torch.from_numpy(x).pin_memory().numpy()
+        reqs.append(dict(w=w, omega=pin(omega), V=pin(V), sigma=pin(sigma), q1=pin(q1),
+                         out=torch.zeros((K, w.N), dtype=torch.complex128).pin_memory().numpy()))
+    work = sum(r["w"].N * r["w"].K for r in reqs)
+
+    def serve(prec, arrivals, inflight):
+        srv = D.dyson_server_create(64 << 30, max_inflight=inflight)
+        t0 = time.perf_counter()
+        tickets = []
+        for r, ta in zip(reqs, arrivals):
+            dt = ta - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            w = r["w"]
+            geom = D.make_geometry(w.L, w.t, w.mu, w.p, w.k, prec, max_freqs=32)
+            tickets.append(D.dyson_submit(srv, geom, w.K, r["omega"], r["V"], r["sigma"], r["q1"], r["out"]))
+        lat = [D.dyson_wait(srv, t)[0] for t in tickets]
+        wall = time.perf_counter() - t0
+        st = D.dyson_server_stats(srv)
+        D.dyson_server_destroy(srv)
+        return wall, lat, st
+
+    # warm plans and graphs for both forms, then the plain-FP64 one-at-a-time capacity
+    serve(D.DYSON_FP64, [0.0] * len(reqs), 1)
+    wall_plain, lat_plain, _ = serve(D.DYSON_FP64, [0.0] * len(reqs), 1)
+    capacity = work / wall_plain
+    mean_work = work / len(reqs)
+    out = dict(metric="serving: site-frequencies/s and p50/p99 request latency (continuous batching)",
+               unit="site-frequencies/s", requests=len(reqs),
+               config=dict(lattices="64x64 p=4 k=32 | 128x128 p=4 k=32", K="uniform 8..32",
+                           arrivals="open-loop Poisson, seed 5", served_form="mixed",
+                           max_inflight=a.inflight),
+               plain_fp64_capacity=capacity, plain_fp64_sequential_wall_s=wall_plain, rates=[])
+    serve(D.DYSON_MIXED, [0.0] * len(reqs), a.inflight)            # warm mixed plans
+    for frac in a.rate_fracs:
+        lam = frac * capacity / mean_work                          # requests per second
+        gaps = np.random.default_rng(int(frac * 1000)).exponential(1.0 / lam, len(reqs))
+        arrivals = np.cumsum(gaps) - gaps[0]
+        wall, lat, st = serve(D.DYSON_MIXED, list(arrivals), a.inflight)
+        sl = sorted(lat)
+        out["rates"].append(dict(rate_frac=frac, offered=frac * capacity, value=work / wall,
+                                 p50_ms=sl[len(sl) // 2], p99_ms=sl[min(len(sl) - 1, int(0.99 * len(sl)))],
+                                 peak_running=st["peak_running"], plans_created=st["plans_created"],
+                                 plans_evicted=st["plans_evicted"]))
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -370,7 +445,14 @@ def main():
     ap.add_argument("--cpu-freqs", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip the plain-FP64 and per-launch extras")
+    ap.add_argument("--serving", action="store_true", help="run the continuous-batching serving stream")
+    ap.add_argument("--requests", type=int, default=48)
+    ap.add_argument("--inflight", type=int, default=8)
+    ap.add_argument("--rate-fracs", type=float, nargs="+", default=[0.5, 0.8, 0.95, 2.0, 4.0])
     a = ap.parse_args()
+    if a.serving:
+        print(json.dumps(run_serving(a)), flush=True)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -187,6 +187,52 @@ int dyson_subdomain_solve(dyson_plan plan, int K, const double* omega, const dou
 int dyson_xmatvec(dyson_plan plan, int K, const double* omega, const double* V,
                   const double* sigma, const double* q, double* u, int mem_kind, void* stream);
 
+/*
+ * Serving: continuous batching of Dyson solves from many IDMFT clients (each
+ * self-consistency iteration needs all frequencies again with a new
+ * self-energy, Sec. 3).  Requests are admitted in arrival order as soon as the
+ * device-memory budget (bytes of resident plans) and a stream slot allow;
+ * admitted requests run concurrently, each as one batched, graph-replayed
+ * solve on its own stream.  Plans (factors, Lanczos bases, workspace) stay
+ * resident and are reused by later requests with the same geometry; idle
+ * plans are evicted least recently used first when memory is needed.  A
+ * request's result is the same alone and in any mix.  Thread-safe: any
+ * thread may submit, poll and wait.
+ */
+typedef struct dyson_server_s* dyson_server;
+
+typedef struct {
+  dyson_geometry geom;   /* geometry and sizes; geom.max_freqs is the plan's capacity */
+  int K;                 /* frequencies in this request, 1..geom.max_freqs */
+  const double* omega;   /* [K] host (pinned host memory lets the copies overlap) */
+  const double* V;       /* [N] host */
+  const double* sigma;   /* complex[K][N] host */
+  const double* q1;      /* [N] host, real Lanczos start vector */
+  double* diagG;         /* complex[K][N] host, written before the request completes */
+  int* status;           /* [K] host, DYSON_ST_* flags, or NULL */
+} dyson_request;
+
+typedef struct {
+  int queued, running, resident_plans, peak_running;
+  size_t bytes_in_use, peak_bytes;
+  uint64_t admitted, completed, plans_created, plans_evicted;
+} dyson_server_stats_t;
+
+/* hbm_budget: most device bytes of resident plans; max_inflight: concurrent requests (1..64).
+ * The server works on the device that is current at creation. */
+int dyson_server_create(size_t hbm_budget, int max_inflight, dyson_server* out);
+/* Finishes queued and running requests, then frees every plan and stream. */
+int dyson_server_destroy(dyson_server server);
+/* Queue a request; the caller keeps its buffers alive until dyson_wait returns.
+ * DYSON_E_BUDGET if the request alone needs more than the budget. */
+int dyson_submit(dyson_server server, const dyson_request* request, uint64_t* ticket);
+/* *done = 1 once the request has finished (outputs written), else 0. */
+int dyson_poll(dyson_server server, uint64_t ticket, int* done);
+/* Block until the request finishes and forget the ticket.  latency_ms: submission to
+ * completion; run_ms: admission to completion (each may be NULL). */
+int dyson_wait(dyson_server server, uint64_t ticket, double* latency_ms, double* run_ms);
+int dyson_server_stats(dyson_server server, dyson_server_stats_t* out);
+
 /* Kernel kinds reported by dyson_profile_read. */
 #define DYSON_KERNEL_INIT 0      /* start vector, per-frequency state */
 #define DYSON_KERNEL_FACTOR 1    /* subdomain recursions: g_s and diag(B^-1) */

@@ -7,6 +7,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -146,6 +147,19 @@ size_t layout(const Geo& g, int K, bool mixed, size_t off[B_COUNT]) {
 }  // namespace
 
 int dyson_internal_fail(int code, const std::string& msg) { return fail(code, msg); }
+
+cudaError_t raise_smem_limit(const void* func, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> cur;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& have = cur[{dev, func}];
+  if (bytes <= have || bytes <= 48 * 1024) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) have = bytes;
+  return e;
+}
 
 struct dyson_plan_s {
   dyson_geometry gi;
@@ -408,8 +422,13 @@ int dyson_plan_destroy(dyson_plan p) {
   return DYSON_OK;
 }
 
-int dyson_solve(dyson_plan p, int K, const double* omega, const double* V, const double* sigma,
-                const double* q1, double* diagG, int* status, int mem_kind, void* stream) {
+}  // extern "C"
+
+// Enqueue a whole solve on `stream` (inputs in, graph, outputs out) without
+// waiting for it; the serving loop uses this directly.
+int dyson_internal_solve_enqueue(dyson_plan p, int K, const double* omega, const double* V,
+                                 const double* sigma, const double* q1, double* diagG, int* status,
+                                 int mem_kind, void* stream) {
   int rc;
   if ((rc = check_plan(p)) || (rc = check_K(p, K)) || (rc = check_mem(mem_kind))) return rc;
   if (!q1 || !diagG) return fail(DYSON_E_BAD_ARG, "q1 and diagG must not be NULL");
@@ -424,7 +443,18 @@ int dyson_solve(dyson_plan p, int K, const double* omega, const double* V, const
   }
   CK(cudaMemcpyAsync(diagG, p->b.out, (size_t)K * p->g.N * sizeof(cxd), cudaMemcpyDefault, s));
   if (status) CK(cudaMemcpyAsync(status, p->status_d, K * sizeof(int), cudaMemcpyDefault, s));
-  return finish(mem_kind, s);
+  return DYSON_OK;
+}
+
+size_t dyson_internal_plan_bytes(dyson_plan p) { return p ? p->bytes : 0; }
+
+extern "C" {
+
+int dyson_solve(dyson_plan p, int K, const double* omega, const double* V, const double* sigma,
+                const double* q1, double* diagG, int* status, int mem_kind, void* stream) {
+  int rc = dyson_internal_solve_enqueue(p, K, omega, V, sigma, q1, diagG, status, mem_kind, stream);
+  if (rc) return rc;
+  return finish(mem_kind, (cudaStream_t)stream);
 }
 
 int dyson_solve_info(dyson_plan p, int K, double* alpha_beta, int* steps, int* iters, int* refines) {

@@ -160,8 +160,19 @@ __device__ __forceinline__ int sub_nat(const Geo& g, int i, int s, int j) {
 }
 
 // ---------------------------------------------------------------- host helpers
+// Raise (never lower) a kernel's dynamic shared-memory limit to at least
+// `bytes`.  Plans of different sizes share the kernels, and a graph captured
+// for a large plan may be replayed after a small plan ran, so the limit only grows.
+cudaError_t raise_smem_limit(const void* func, size_t bytes);
+
 // Record msg as this thread's dyson_last_error() and return code.
 int dyson_internal_fail(int code, const std::string& msg);
+struct dyson_plan_s;
+// dyson_solve without the final wait (all copies and the graph launch enqueued on stream)
+int dyson_internal_solve_enqueue(dyson_plan_s* p, int K, const double* omega, const double* V,
+                                 const double* sigma, const double* q1, double* diagG, int* status,
+                                 int mem_kind, void* stream);
+size_t dyson_internal_plan_bytes(dyson_plan_s* p);
 
 // ---------------------------------------------------------------- host launchers
 template <typename R, typename S>

@@ -183,8 +183,7 @@ template <typename R, typename S>
 cudaError_t launch_factor(const Geo& g, const Bufs& b, int K, cudaStream_t st) {
   if (g.W > DY_MAXW_SMEM) return cudaErrorInvalidValue;
   size_t smem = 3 * (size_t)g.W * g.W * sizeof(cx<R>);
-  cudaError_t e = cudaFuncSetAttribute(k_factor<R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = raise_smem_limit((const void*)k_factor<R, S>, smem);
   if (e != cudaSuccess) return e;
   k_factor<R, S><<<dim3(g.p, K), DY_THREADS, smem, st>>>(g, b);
   return cudaGetLastError();

@@ -7,7 +7,8 @@
 // block reduction, then every CTA reads the p partials from distributed
 // shared memory in rank order, so all CTAs of a cluster hold bit-identical
 // scalars and take identical branch decisions (no CTA can leave a cluster
-// barrier behind).
+// barrier behind).  Every kernel that reads peers' shared memory ends with a
+// cluster barrier, so no CTA exits while a peer may still be reading it.
 //
 // X-"matvec" (Sec. 2.3, Eqs. 6-8).  The paper defines u = v - w with
 // H v = q and w = blkdiag(B^-1, 0) q.  Eliminating the subdomain unknowns
@@ -961,6 +962,7 @@ __global__ void __launch_bounds__(DY_THREADS, 2) k_xmatvec(Geo g, Bufs b, int j,
     st[ST_REFINE] += refines;
     if (!conv_all) st[ST_STATUS] |= 4;
   }
+  cl.sync();          // no CTA exits while a peer may still read its shared memory
 }
 
 // One step of complex-symmetric Lanczos on X with the bilinear form
@@ -1065,6 +1067,7 @@ __global__ void __launch_bounds__(DY_THREADS) k_lanczos(Geo g, Bufs b, int j) {
       b.maxT[kf] = fmax(maxT, babs);
     }
   }
+  cl.sync();          // no CTA exits while a peer may still read its shared memory
 }
 
 // Gather the real start vector into DD layout and normalise it in the
@@ -1101,6 +1104,7 @@ __global__ void __launch_bounds__(DY_THREADS) k_init(Geo g, Bufs b) {
     lan[0] = lan[1] = cxd{0, 0};
     b.maxT[kf] = 0.0;
   }
+  cl.sync();          // no CTA exits while a peer may still read its shared memory
 }
 
 // diag(G) = diag(blkdiag(B^-1, 0)) + diag(Q T Q^T)  (Eq. 9), natural order.
@@ -1170,11 +1174,8 @@ __global__ void __launch_bounds__(DY_THREADS, 2) k_bsolve(Geo g, Bufs b, const c
 template <typename Kern, typename... Args>
 cudaError_t launch_cluster(Kern kern, dim3 grid, int cx_, size_t smem, cudaStream_t st,
                            Args... args) {
-  cudaError_t e;
-  if (smem > 48 * 1024) {
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
+  cudaError_t e = raise_smem_limit((const void*)kern, smem);
+  if (e != cudaSuccess) return e;
   if (cx_ > 8) {
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
@@ -1247,11 +1248,8 @@ template <typename R>
 cudaError_t launch_bsolve(const Geo& g, const Bufs& b, int K, const cxd* q_dd, cxd* w_dd,
                           cudaStream_t st) {
   size_t smem = sweep_smem<R>(g);
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_bsolve<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-  }
+  cudaError_t e = raise_smem_limit((const void*)k_bsolve<R>, smem);
+  if (e != cudaSuccess) return e;
   k_bsolve<R><<<dim3(g.p, K), DY_THREADS, smem, st>>>(g, b, q_dd, w_dd);
   return cudaGetLastError();
 }

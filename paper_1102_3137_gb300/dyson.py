@@ -36,6 +36,19 @@ class dyson_geometry(C.Structure):
                 ("refine_tol", C.c_double), ("refine_max", C.c_int), ("max_freqs", C.c_int)]
 
 
+class dyson_request(C.Structure):
+    _fields_ = [("geom", dyson_geometry), ("K", C.c_int), ("omega", C.c_void_p), ("V", C.c_void_p),
+                ("sigma", C.c_void_p), ("q1", C.c_void_p), ("diagG", C.c_void_p),
+                ("status", C.c_void_p)]
+
+
+class dyson_server_stats_t(C.Structure):
+    _fields_ = [("queued", C.c_int), ("running", C.c_int), ("resident_plans", C.c_int),
+                ("peak_running", C.c_int), ("bytes_in_use", C.c_size_t), ("peak_bytes", C.c_size_t),
+                ("admitted", C.c_uint64), ("completed", C.c_uint64),
+                ("plans_created", C.c_uint64), ("plans_evicted", C.c_uint64)]
+
+
 class DysonError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"dyson error {code}: {msg}")
@@ -75,6 +88,12 @@ def load(path: str = LIB_PATH):
         "dyson_work_counters": ([P, I, P], I),
         "dyson_lanczos_basis": ([P, I, I, P], I),
         "dyson_subdomain_diag_noalloc": ([C.POINTER(dyson_geometry), I, P, P, P, P, P], I),
+        "dyson_server_create": ([C.c_size_t, I, C.POINTER(P)], I),
+        "dyson_server_destroy": ([P], I),
+        "dyson_submit": ([P, C.POINTER(dyson_request), C.POINTER(C.c_uint64)], I),
+        "dyson_poll": ([P, C.c_uint64, C.POINTER(I)], I),
+        "dyson_wait": ([P, C.c_uint64, C.POINTER(C.c_double), C.POINTER(C.c_double)], I),
+        "dyson_server_stats": ([P, C.POINTER(dyson_server_stats_t)], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -278,6 +297,49 @@ def dyson_lanczos_basis(plan, k, nvec, N):
     Q = np.zeros((nvec, N), np.complex128)
     _check(load().dyson_lanczos_basis(plan, int(k), int(nvec), Q.ctypes.data))
     return Q
+
+
+def dyson_server_create(hbm_budget, max_inflight=8):
+    h = C.c_void_p()
+    _check(load().dyson_server_create(int(hbm_budget), int(max_inflight), C.byref(h)))
+    return h
+
+
+def dyson_server_destroy(server):
+    _check(load().dyson_server_destroy(server))
+
+
+def dyson_submit(server, geom, K, omega, V, sigma, q1, diagG, status=None):
+    """Queue one request (host numpy arrays; keep them alive until dyson_wait)."""
+    N = V.shape[0]
+    req = dyson_request()
+    req.geom = geom
+    req.K = int(K)
+    req.omega, req.V = _ptr(omega, "f8", K), _ptr(V, "f8", N)
+    req.sigma, req.q1 = _ptr(sigma, "c16", K * N), _ptr(q1, "f8", N)
+    req.diagG, req.status = _ptr(diagG, "c16", K * N), _ptr(status, "i4", K)
+    t = C.c_uint64()
+    _check(load().dyson_submit(server, C.byref(req), C.byref(t)))
+    return t.value
+
+
+def dyson_poll(server, ticket):
+    d = C.c_int()
+    _check(load().dyson_poll(server, C.c_uint64(ticket), C.byref(d)))
+    return bool(d.value)
+
+
+def dyson_wait(server, ticket):
+    """Block until done; returns (latency_ms from submission, run_ms from admission)."""
+    lat, run = C.c_double(), C.c_double()
+    _check(load().dyson_wait(server, C.c_uint64(ticket), C.byref(lat), C.byref(run)))
+    return lat.value, run.value
+
+
+def dyson_server_stats(server):
+    st = dyson_server_stats_t()
+    _check(load().dyson_server_stats(server, C.byref(st)))
+    return {f: getattr(st, f) for f, _ in st._fields_}
 
 
 class Plan:
