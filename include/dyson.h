@@ -117,6 +117,10 @@ int dyson_plan_footprint(const dyson_geometry* geom, size_t* bytes);
  * Create a plan on the current CUDA device: validates geom, builds the
  * domain-decomposition maps and allocates all device workspace for up to
  * geom->max_freqs frequencies.  *out is set on success.
+ * Slice width W = (sites of one slice: h in 2D, Ly*h in 3D, h the tallest
+ * subdomain) rounded up to a multiple of 4 must be <= 256, and for W > 64 the
+ * sweep row buffer (Lx * W complex entries in the form's precision) must leave
+ * room for the copy ring in shared memory; otherwise DYSON_E_UNSUPPORTED.
  */
 int dyson_plan_create(const dyson_geometry* geom, dyson_plan* out);
 
@@ -153,7 +157,9 @@ int dyson_solve_info(dyson_plan plan, int K, double* alpha_beta, int* steps, int
 
 /*
  * y = H(i w_k) x for K frequencies by the nearest-neighbour stencil (Eq. 1),
- * H never stored.  x, y complex[K][N] (complex128).
+ * H never stored.  x, y complex[K][N] (complex128).  With DYSON_MEM_DEVICE all
+ * inputs are read in place and K may exceed the plan's max_freqs; with host
+ * buffers they are staged through the plan (K <= max_freqs).
  */
 int dyson_apply_H(dyson_plan plan, int K, const double* omega, const double* V,
                   const double* sigma, const double* x, double* y, int mem_kind, void* stream);

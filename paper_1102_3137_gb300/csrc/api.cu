@@ -66,9 +66,9 @@ int build_part(const dyson_geometry* in, Part* out, bool gpu) {
     if (i < g.p - 1) g.ylayer[i] = c++;
   }
   g.W = (g.T * hmax + 3) & ~3;   // multiple of 4: 16-byte aligned rows and bulk copies
-  if (gpu && g.W > DY_MAXW_SMEM)
-    return fail(DYSON_E_UNSUPPORTED, "slice width " + std::to_string(g.W) +
-                                         " exceeds 64 (shared-memory subdomain factorization)");
+  if (gpu && g.W > DY_MAXW)
+    return fail(DYSON_E_UNSUPPORTED, "slice width " + std::to_string(g.W) + " exceeds " +
+                                         std::to_string(DY_MAXW));
   long long ndd = (long long)g.p * g.Lx * g.W + (long long)(g.p - 1) * g.A;
   if (ndd > (1LL << 30)) return fail(DYSON_E_UNSUPPORTED, "lattice too large");
   g.Ndd = (int)ndd;
@@ -78,6 +78,10 @@ int build_part(const dyson_geometry* in, Part* out, bool gpu) {
   if (in->precision != DYSON_FP64 && in->precision != DYSON_MIXED)
     return fail(DYSON_E_BAD_ARG, "precision must be DYSON_FP64 or DYSON_MIXED");
   const bool mixed = in->precision == DYSON_MIXED;
+  if (gpu && dyson_internal_sweep_smem(g, mixed) == 0)
+    return fail(DYSON_E_UNSUPPORTED, "slice width " + std::to_string(g.W) + " with Lx = " +
+                                         std::to_string(g.Lx) +
+                                         ": the sweep row buffer does not fit shared memory");
   g.t = in->t;
   g.mu = in->mu;
   g.krylov_tol = in->krylov_tol > 0 ? in->krylov_tol : (mixed ? 1e-5 : 1e-13);
@@ -105,7 +109,7 @@ int build_part(const dyson_geometry* in, Part* out, bool gpu) {
 
 enum {
   B_V, B_OMEGA, B_SIGMA, B_Q1, B_DD2NAT, B_G, B_G64, B_DIAGB, B_Q, B_ACC, B_U, B_V1, B_V2, B_V3,
-  B_YSCR, B_BND, B_IFV, B_PRE, B_LAN, B_MAXT, B_ST, B_OUT, B_STATUS, B_SWEEPS, B_COUNT
+  B_YSCR, B_BND, B_IFV, B_PRE, B_LAN, B_MAXT, B_ST, B_OUT, B_STATUS, B_SWEEPS, B_FWORK, B_COUNT
 };
 
 size_t layout(const Geo& g, int K, bool mixed, size_t off[B_COUNT]) {
@@ -136,6 +140,7 @@ size_t layout(const Geo& g, int K, bool mixed, size_t off[B_COUNT]) {
   sz[B_OUT] = Kz * g.N * sizeof(cxd);
   sz[B_STATUS] = Kz * sizeof(int);
   sz[B_SWEEPS] = Kz * g.p * sizeof(unsigned long long);
+  sz[B_FWORK] = g.W > DY_MAXW_SMEM ? (size_t)DY_FACTOR_CTAS * 2 * g.W * g.W * sizeof(cxd) : 0;
   size_t o = 0;
   for (int k = 0; k < B_COUNT; ++k) {
     off[k] = o;
@@ -403,6 +408,7 @@ int dyson_plan_create(const dyson_geometry* geom, dyson_plan* out) {
   b.st = at<int>(p, B_ST);
   b.out = at<cxd>(p, B_OUT);
   b.sweeps = at<unsigned long long>(p, B_SWEEPS);
+  b.fwork = p->g.W > DY_MAXW_SMEM ? at<cxd>(p, B_FWORK) : nullptr;
   p->status_d = at<int>(p, B_STATUS);
   p->profile = false;
   p->n_prof = 0;
@@ -542,19 +548,29 @@ int dyson_work_counters(dyson_plan p, int K, unsigned long long* sweeps) {
 int dyson_apply_H(dyson_plan p, int K, const double* omega, const double* V, const double* sigma,
                   const double* x, double* y, int mem_kind, void* stream) {
   int rc;
-  if ((rc = check_plan(p)) || (rc = check_K(p, K)) || (rc = check_mem(mem_kind))) return rc;
+  if ((rc = check_plan(p)) || (rc = check_mem(mem_kind))) return rc;
+  // device buffers are read in place, so K is not bounded by the plan's capacity
+  if (K < 1 || (mem_kind == DYSON_MEM_HOST && K > p->Kcap))
+    return fail(DYSON_E_BAD_ARG, "K must be >= 1 (and <= max_freqs with host buffers)");
   if (!x || !y) return fail(DYSON_E_BAD_ARG, "x and y must not be NULL");
   cudaStream_t s = (cudaStream_t)stream;
-  if ((rc = stage_inputs(p, K, omega, V, sigma, nullptr, s))) return rc;
   const size_t bytes = (size_t)K * p->g.N * sizeof(cxd);
   const cxd* xd = reinterpret_cast<const cxd*>(x);
   cxd* yd = reinterpret_cast<cxd*>(y);
-  if (mem_kind == DYSON_MEM_HOST) {
+  const double *Vd = V, *wd = omega;
+  const cxd* sd = reinterpret_cast<const cxd*>(sigma);
+  if (mem_kind == DYSON_MEM_HOST) {          // stage into the plan; device inputs are read in place
+    if ((rc = stage_inputs(p, K, omega, V, sigma, nullptr, s))) return rc;
     CK(cudaMemcpyAsync(p->b.u, x, bytes, cudaMemcpyHostToDevice, s));
     xd = p->b.u;
     yd = p->b.out;
+    Vd = p->b.V;
+    wd = p->b.omega;
+    sd = p->b.sigma;
+  } else if (!omega || !V || !sigma) {
+    return fail(DYSON_E_BAD_ARG, "omega, V and sigma must not be NULL");
   }
-  LK(launch_spmv<double>(p->g, p->b.V, p->b.omega, p->b.sigma, xd, yd, K, s));
+  LK(launch_spmv<double>(p->g, Vd, wd, sd, xd, yd, K, s));
   if (mem_kind == DYSON_MEM_HOST) CK(cudaMemcpyAsync(y, yd, bytes, cudaMemcpyDeviceToHost, s));
   return finish(mem_kind, s);
 }
@@ -562,19 +578,29 @@ int dyson_apply_H(dyson_plan p, int K, const double* omega, const double* V, con
 int dyson_apply_H_c64(dyson_plan p, int K, const double* omega, const double* V,
                       const double* sigma, const float* x, float* y, int mem_kind, void* stream) {
   int rc;
-  if ((rc = check_plan(p)) || (rc = check_K(p, K)) || (rc = check_mem(mem_kind))) return rc;
+  if ((rc = check_plan(p)) || (rc = check_mem(mem_kind))) return rc;
+  // device buffers are read in place, so K is not bounded by the plan's capacity
+  if (K < 1 || (mem_kind == DYSON_MEM_HOST && K > p->Kcap))
+    return fail(DYSON_E_BAD_ARG, "K must be >= 1 (and <= max_freqs with host buffers)");
   if (!x || !y) return fail(DYSON_E_BAD_ARG, "x and y must not be NULL");
   cudaStream_t s = (cudaStream_t)stream;
-  if ((rc = stage_inputs(p, K, omega, V, sigma, nullptr, s))) return rc;
   const size_t bytes = (size_t)K * p->g.N * sizeof(cxf);
   const cxf* xd = reinterpret_cast<const cxf*>(x);
   cxf* yd = reinterpret_cast<cxf*>(y);
-  if (mem_kind == DYSON_MEM_HOST) {
+  const double *Vd = V, *wd = omega;
+  const cxd* sd = reinterpret_cast<const cxd*>(sigma);
+  if (mem_kind == DYSON_MEM_HOST) {          // stage into the plan; device inputs are read in place
+    if ((rc = stage_inputs(p, K, omega, V, sigma, nullptr, s))) return rc;
     CK(cudaMemcpyAsync(p->b.u, x, bytes, cudaMemcpyHostToDevice, s));
     xd = reinterpret_cast<const cxf*>(p->b.u);
     yd = reinterpret_cast<cxf*>(p->b.out);
+    Vd = p->b.V;
+    wd = p->b.omega;
+    sd = p->b.sigma;
+  } else if (!omega || !V || !sigma) {
+    return fail(DYSON_E_BAD_ARG, "omega, V and sigma must not be NULL");
   }
-  LK(launch_spmv<float>(p->g, p->b.V, p->b.omega, p->b.sigma, xd, yd, K, s));
+  LK(launch_spmv<float>(p->g, Vd, wd, sd, xd, yd, K, s));
   if (mem_kind == DYSON_MEM_HOST) CK(cudaMemcpyAsync(y, yd, bytes, cudaMemcpyDeviceToHost, s));
   return finish(mem_kind, s);
 }

@@ -24,6 +24,7 @@
 #define DY_WARPS (DY_THREADS / 32)
 #define DY_MAXW 256         // widest slice the sweep kernels take
 #define DY_MAXW_SMEM 64     // widest slice the shared-memory factor kernel takes
+#define DY_FACTOR_CTAS 304  // persistent grid of the wide-slice factor kernel (2 per SM on 152 SMs)
 
 // per-frequency state words
 enum {
@@ -140,6 +141,7 @@ struct Bufs {
   int* st;              // [K][ST_N]
   cxd* out;             // [K][N] diag(G), natural order
   unsigned long long* sweeps;  // [K][p] subdomain sweeps performed (work accounting)
+  cxd* fwork;           // [DY_FACTOR_CTAS][2][W][W] wide-slice factor workspace (W > 64 only)
 };
 
 // interface Krylov vector slots inside ifv
@@ -173,6 +175,9 @@ int dyson_internal_solve_enqueue(dyson_plan_s* p, int K, const double* omega, co
                                  const double* sigma, const double* q1, double* diagG, int* status,
                                  int mem_kind, void* stream);
 size_t dyson_internal_plan_bytes(dyson_plan_s* p);
+// Dynamic shared memory of the sweep-based solver kernels for this geometry in
+// the given form; 0 when the slice width and x extent do not fit on chip.
+size_t dyson_internal_sweep_smem(const Geo& g, bool mixed);
 
 // ---------------------------------------------------------------- host launchers
 template <typename R, typename S>

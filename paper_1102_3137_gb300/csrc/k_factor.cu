@@ -143,6 +143,147 @@ __global__ void __launch_bounds__(DY_THREADS) k_factor(Geo g, Bufs b) {
   }
 }
 
+// ---------------------------------------------------------------- wide slices
+// 64 < W <= 256 (3D slabs): a W x W block no longer fits shared memory.  The
+// same recursion runs on global memory, which at these sizes stays in L2: the
+// forward g_s is formed and inverted in place in its final slot of b.g (or
+// b.g64), and the backward pass keeps G_{s+1,s+1} and the product g_s G_{s+1}
+// in two W x W matrices of a per-CTA workspace.  A persistent grid of
+// DY_FACTOR_CTAS CTAs walks the (subdomain, frequency) units, so the workspace
+// is bounded by the grid, not by K.
+
+// In-place Gauss-Jordan on a global W x W matrix.  Step k caches pivot row k
+// and the column multipliers A[r][k] / A[k][k] on chip; every other element is
+// then owned by exactly one thread, so one barrier per phase suffices.
+__device__ void gj_invert_global(cxd* A, int W, cxd* prow, cxd* fcol) {
+  const int n = W * W;
+  for (int k = 0; k < W; ++k) {
+    __syncthreads();                         // step k-1 finished by every thread
+    const cxd piv = cinv(A[(size_t)k * W + k]);
+    for (int e = threadIdx.x; e < W; e += DY_THREADS) {
+      prow[e] = A[(size_t)k * W + e];
+      fcol[e] = A[(size_t)e * W + k] * piv;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n; e += DY_THREADS) {
+      const int r = e / W, c = e - r * W;
+      cxd v;
+      if (r == k) v = (c == k) ? piv : prow[c] * piv;
+      else if (c == k) v = -fcol[r];
+      else v = A[e] - fcol[r] * prow[c];
+      A[e] = v;
+    }
+  }
+  __syncthreads();
+}
+
+// C = base + scale * X Y for global W x W matrices (base may be null: C = X Y),
+// in 32 x 32 output tiles staged through shared memory; W need not be a
+// multiple of 32.  C must not alias X or Y.
+__device__ void gmem_matmul(cxd* C, const cxd* X, const cxd* Y, const cxd* base, double scale,
+                            int W, cxd (*tx)[32], cxd (*ty)[32]) {
+  const int tid = threadIdx.x, lc = tid & 31, lr = tid >> 5;   // 8 row groups x 32 columns
+  const int nt = (W + 31) / 32;
+  for (int tile = 0; tile < nt * nt; ++tile) {
+    const int r0 = (tile / nt) * 32, c0 = (tile % nt) * 32;
+    cxd acc[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    for (int k0 = 0; k0 < W; k0 += 32) {
+      __syncthreads();                       // previous tiles fully read
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const int r = lr + 8 * m;
+        tx[r][lc] = (r0 + r < W && k0 + lc < W) ? X[(size_t)(r0 + r) * W + k0 + lc] : cxd{0, 0};
+        ty[r][lc] = (k0 + r < W && c0 + lc < W) ? Y[(size_t)(k0 + r) * W + c0 + lc] : cxd{0, 0};
+      }
+      __syncthreads();
+#pragma unroll 8
+      for (int k = 0; k < 32; ++k) {
+        const cxd yv = ty[k][lc];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) acc[m] = cfma(tx[lr + 8 * m][k], yv, acc[m]);
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const int r = r0 + lr + 8 * m, c = c0 + lc;
+      if (r < W && c < W) {
+        const size_t e = (size_t)r * W + c;
+        C[e] = base ? base[e] + scale * acc[m] : acc[m];
+      }
+    }
+  }
+  __syncthreads();
+}
+
+template <typename S>
+__global__ void __launch_bounds__(DY_THREADS) k_factor_big(Geo g, Bufs b, int K) {
+  __shared__ cxd prow[DY_MAXW], fcol[DY_MAXW];
+  __shared__ cxd tx[32][32], ty[32][32];
+  constexpr bool two = sizeof(S) != sizeof(double);
+  const int W = g.W, Lx = g.Lx, T = g.T;
+  const size_t n = (size_t)W * W;
+  const double t = g.t, t2 = g.t * g.t;
+  cxd* Gw = b.fwork + (size_t)blockIdx.x * 2 * n;   // G_{s+1,s+1}
+  cxd* Pw = Gw + n;                                  // g_s G_{s+1,s+1}
+  for (int unit = blockIdx.x; unit < g.p * K; unit += gridDim.x) {
+    const int i = unit % g.p, kf = unit / g.p, w = T * g.h[i];
+    const size_t uoff = ((size_t)kf * g.p + i) * (size_t)Lx * n;
+    cxd* gout = (two ? b.g64 : reinterpret_cast<cxd*>(b.g)) + uoff;
+    cx<S>* gsw = reinterpret_cast<cx<S>*>(b.g) + uoff;
+    cxd* dB = b.diagB + (size_t)kf * g.Ndd + (size_t)i * Lx * W;
+    // forward: g_s = (D_s - t^2 g_{s-1})^-1, formed and inverted in place
+    for (int s = 0; s < Lx; ++s) {
+      cxd* A = gout + (size_t)s * n;
+      const cxd* Ap = A - n;
+      __syncthreads();                       // g_{s-1} complete
+      for (int e = threadIdx.x; e < (int)n; e += DY_THREADS) {
+        const int r = e / W, c = e - r * W;
+        cxd v = {0, 0};
+        if (r < w && c < w) {
+          if (s > 0) v = (-t2) * Ap[e];
+          if (r == c) {
+            v = v + dyson_diag(g, b, kf, sub_nat(g, i, s, r));
+          } else if (slice_adjacent<double>(r, c, T)) {
+            v.x += t;
+          }
+        } else if (r == c) {
+          v = cxd{1, 0};                     // padding: identity, inverted to itself
+        }
+        A[e] = v;
+      }
+      gj_invert_global(A, W, prow, fcol);
+      for (int e = threadIdx.x; e < (int)n; e += DY_THREADS) {
+        const int r = e / W, c = e - r * W;
+        cxd v = A[e];
+        if (r >= w || c >= w) {
+          v = cxd{0, 0};
+          A[e] = v;
+        }
+        if (two) gsw[(size_t)s * n + e] = cconv<S>(v);
+      }
+    }
+    __syncthreads();
+    // backward: Gw holds G_{s+1,s+1}
+    const cxd* glast = gout + (size_t)(Lx - 1) * n;
+    for (int e = threadIdx.x; e < (int)n; e += DY_THREADS) Gw[e] = glast[e];
+    for (int r = threadIdx.x; r < W; r += DY_THREADS)
+      dB[(size_t)(Lx - 1) * W + r] = (r < w) ? glast[(size_t)r * W + r] : cxd{0, 0};
+    for (int s = Lx - 2; s >= 0; --s) {
+      const cxd* gs = gout + (size_t)s * n;
+      gmem_matmul(Pw, gs, Gw, nullptr, 0.0, W, tx, ty);   // g_s G_{s+1}
+      gmem_matmul(Gw, Pw, gs, gs, t2, W, tx, ty);         // g_s + t^2 g_s G_{s+1} g_s
+      for (int r = threadIdx.x; r < W; r += DY_THREADS)
+        dB[(size_t)s * W + r] = (r < w) ? Gw[(size_t)r * W + r] : cxd{0, 0};
+    }
+    if (i == g.p - 1) {
+      cxd* dI = b.diagB + (size_t)kf * g.Ndd + g.ifc_off;
+      const size_t m = (size_t)(g.p - 1) * g.A;
+      for (size_t e = threadIdx.x; e < m; e += DY_THREADS) dI[e] = cxd{0, 0};
+    }
+    __syncthreads();                         // workspace reads done before the next unit
+  }
+}
+
 // Tridiagonal preconditioner of the interface Schur system.  The Schur
 // complement S = C - E^T B^-1 E (Eq. 4) is never formed; its cheap
 // approximation keeps C and the diagonal of B^-1 next to the interface:
@@ -181,7 +322,13 @@ __global__ void __launch_bounds__(DY_THREADS) k_precond(Geo g, Bufs b) {
 
 template <typename R, typename S>
 cudaError_t launch_factor(const Geo& g, const Bufs& b, int K, cudaStream_t st) {
-  if (g.W > DY_MAXW_SMEM) return cudaErrorInvalidValue;
+  if (g.W > DY_MAXW_SMEM) {
+    // wide slices: FP64 recursion in global memory (both forms recurse in FP64)
+    if (sizeof(R) != sizeof(double) || g.W > DY_MAXW || !b.fwork) return cudaErrorInvalidValue;
+    int units = g.p * K;
+    k_factor_big<S><<<units < DY_FACTOR_CTAS ? units : DY_FACTOR_CTAS, DY_THREADS, 0, st>>>(g, b, K);
+    return cudaGetLastError();
+  }
   size_t smem = 3 * (size_t)g.W * g.W * sizeof(cx<R>);
   cudaError_t e = raise_smem_limit((const void*)k_factor<R, S>, smem);
   if (e != cudaSuccess) return e;

@@ -162,6 +162,7 @@ struct Pipe {
   void* ring;      // S slots in dynamic shared memory
   void* ybuf;      // forward intermediates in shared memory, or null (global scratch)
   int S;
+  int CR;          // rows of a slice block per streamed chunk (= W unless W > 64)
   unsigned seq;    // blocks issued (= consumed) so far by this CTA
   int* err;        // shared flag: a bounded wait ran out
 };
@@ -208,8 +209,8 @@ struct SweepArgs {
 struct SweepLayout {
   int RPW, G, CPG;
 };
-__host__ __device__ inline SweepLayout sweep_layout(int W) {
-  int rpw = (W + DY_WARPS - 1) / DY_WARPS, p2 = 1;
+__host__ __device__ inline SweepLayout sweep_layout(int rows, int W) {
+  int rpw = (rows + DY_WARPS - 1) / DY_WARPS, p2 = 1;
   while (p2 < rpw) p2 <<= 1;
   SweepLayout L;
   L.RPW = p2;
@@ -226,10 +227,20 @@ __host__ __device__ inline SweepLayout sweep_layout(int W) {
 // GB300 FP64 issue is ~1/64 of FP32, so keeping conversions out of the
 // dependent chain matters as much as keeping global loads out of it.
 template <typename R>
+__device__ void sweep_chunked(const Geo& g, int i, const SweepArgs<R>& a, cx<R>* sm, Pipe& pp,
+                              unsigned long long* cnt);
+
+// WD selects the row-chunked form at compile time, so the kernels for narrow
+// slices carry none of its code (or its registers).
+template <typename R, bool WD>
 __device__ void sweep(const Geo& g, int i, const SweepArgs<R>& a, cx<R>* sm, Pipe& pp,
                       unsigned long long* cnt) {
+  if constexpr (WD) {
+    sweep_chunked<R>(g, i, a, sm, pp, cnt);
+    return;
+  }
   const int W = g.W, Lx = g.Lx, T = g.T, w = T * g.h[i];
-  const SweepLayout L = sweep_layout(W);
+  const SweepLayout L = sweep_layout(W, W);
   cx<R>* zbuf = sm;                      // [2][W]: z of the current and of the next slice
   cx<R>* ring = reinterpret_cast<cx<R>*>(pp.ring);
   cx<R>* yb = pp.ybuf ? reinterpret_cast<cx<R>*>(pp.ybuf) : a.y;   // [Lx][W] row buffer
@@ -376,6 +387,127 @@ __device__ void sweep(const Geo& g, int i, const SweepArgs<R>& a, cx<R>* sm, Pip
   if (tid == 0 && cnt) *cnt += 1;
 }
 
+// Wide slices (W > 64, 3D slabs): a slice block no longer fits a ring slot, so
+// it streams as NC = W / CR chunks of CR rows; each chunk's rows are finished
+// as soon as it arrives and its slot is released after a barrier.  The row
+// buffer yb is always on chip on this path.
+template <typename R>
+__device__ void sweep_chunked(const Geo& g, int i, const SweepArgs<R>& a, cx<R>* sm, Pipe& pp,
+                              unsigned long long* cnt) {
+  const int W = g.W, Lx = g.Lx, T = g.T, w = T * g.h[i];
+  const int CR = pp.CR, NC = W / CR;
+  const SweepLayout L = sweep_layout(CR, W);
+  cx<R>* zbuf = sm;
+  cx<R>* ring = reinterpret_cast<cx<R>*>(pp.ring);
+  cx<R>* yb = reinterpret_cast<cx<R>*>(pp.ybuf);
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int rr = lane / L.G, cg = lane - rr * L.G;
+  const int lrow = wid * L.RPW + rr;     // row inside a chunk
+  const bool rvalid = lrow < CR;
+  const bool owner = rvalid && cg == 0;
+  const int rot = (W % L.G == 0) ? (rr * L.G) % W : 0;
+  const R t = (R)g.t;
+  const int WW = W * W, CW = CR * W;
+  const uint32_t bytes = (uint32_t)(CW * sizeof(cx<R>));
+  const int NL = 2 * Lx - 1, NQ = NL * NC;
+  const int S = pp.S;
+  const int nrow = Lx * W;
+  auto slice_of = [&](int n) { return n < Lx ? n : 2 * Lx - 2 - n; };
+  auto issue = [&](int q) {
+    const unsigned qq = pp.seq + q;
+    const int slot = (int)(qq % S);
+    const int n = q / NC, c = q - n * NC;
+    bulk_load(ring + (size_t)slot * CW, a.g + (size_t)slice_of(n) * WW + (size_t)c * CW, bytes,
+              pp.bar + slot);
+  };
+
+  __syncthreads();
+  if (tid == 0) {
+    fence_proxy_async();
+    for (int q = 0; q < S && q < NQ; ++q) issue(q);
+  }
+  for (int e = tid; e < nrow; e += DY_THREADS) {
+    const int s = e / W, j = e - s * W;
+    cxd v = {0, 0};
+    if (j < w) {
+      if (a.src) {
+        v = a.in_scale * a.src[e];
+      } else {
+        cx<R> u = {0, 0};
+        if (a.lay_lo && j < T) u = u + t * a.lay_lo[s + Lx * j];
+        if (a.lay_hi && j >= w - T) u = u + t * a.lay_hi[s + Lx * (j - (w - T))];
+        yb[e] = u;
+        continue;
+      }
+    }
+    yb[e] = cconv<R>(v);
+  }
+  __syncthreads();
+  for (int e = tid; e < W; e += DY_THREADS) zbuf[e] = yb[e];
+  __syncthreads();
+  for (int n = 0; n < NL; ++n) {
+    const int s = slice_of(n);
+    const cx<R>* zc = zbuf + (n & 1) * W;
+    cx<R>* zn = zbuf + ((n + 1) & 1) * W;
+    for (int c = 0; c < NC; ++c) {
+      const int q = n * NC + c;
+      const unsigned qq = pp.seq + q;
+      const int slot = (int)(qq % S);
+      if (!mbar_wait(pp.bar + slot, (qq / S) & 1u)) *pp.err = 1;
+      const cx<R>* grow = ring + (size_t)slot * CW + (size_t)lrow * W;
+      cx<R> acc = {0, 0};
+      if (rvalid) {
+#pragma unroll 4
+        for (int k = 0; k < L.CPG; ++k) {
+          const int base = cg + L.G * k;
+          if (base < W) {
+            int col = base + rot;
+            if (col >= W) col -= W;
+            acc = cfma(grow[col], zc[col], acc);
+          }
+        }
+      }
+      for (int off = L.G >> 1; off > 0; off >>= 1) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+      }
+      if (owner) {
+        const int row = c * CR + lrow;
+        if (n < Lx) {                    // forward: row s of yb becomes y_s
+          yb[(size_t)s * W + row] = acc;
+          zn[row] = (s + 1 < Lx) ? yb[(size_t)(s + 1) * W + row] - t * acc : acc;
+        } else {                         // backward: row s of yb becomes x_s
+          const cx<R> xv = yb[(size_t)s * W + row] - t * acc;
+          yb[(size_t)s * W + row] = xv;
+          zn[row] = xv;
+        }
+      }
+      __syncthreads();                   // chunk slot released; rows of z for n+1 written
+      if (tid == 0 && q + S < NQ) {
+        fence_proxy_async();
+        issue(q + S);
+      }
+    }
+  }
+  for (int e = tid; e < nrow; e += DY_THREADS) {
+    const int s = e / W, j = e - s * W;
+    if (j >= w) continue;
+    const cx<R> xr = yb[e];
+    if (a.dst) {
+      const cxd xd = a.out_scale * cconv<double>(xr);
+      cxd* d = a.dst + e;
+      if (a.dst_op == 0) *d = xd;
+      else if (a.dst_op == 1) *d = *d + xd;
+      else if (a.dst_op == 2) *d = *d - xd;
+      else *d = -xd;
+    }
+    if (a.bnd_lo && j < T) a.bnd_lo[s + Lx * j] = xr;
+    if (a.bnd_hi && j >= w - T) a.bnd_hi[s + Lx * (j - (w - T))] = xr;
+  }
+  pp.seq += NQ;
+  if (tid == 0 && cnt) *cnt += 1;
+}
+
 template <typename R>
 __device__ __forceinline__ SweepArgs<R> sweep_base(const Geo& g, const Bufs& b, int kf, int i) {
   SweepArgs<R> a;
@@ -422,9 +554,13 @@ __device__ __forceinline__ cx<R> shfl_down_c(cx<R> v, int d) {
 // b_x = r_x inv_x), stored in z; backward z_x = -c'_x z_{x+1} + d'_x.  Each
 // lane composes the maps of its 4 sites, a 5-step warp scan composes across
 // lanes, then the lanes finish their sites: ~9 dependent steps per 128 sites.
+//
+// r is the COCG residual, rewritten in this kernel between calls: it must be
+// read through the coherent path, never as const __restrict__ (which lets the
+// compiler use non-coherent loads whose cached lines can be stale by the next
+// iteration).  The preconditioner factors are read-only for the kernel's life.
 template <typename R>
-__device__ void precond_apply(const Geo& g, const Bufs& b, int kf, int i,
-                              const cx<R>* __restrict__ r, cx<R>* __restrict__ z) {
+__device__ void precond_apply(const Geo& g, const Bufs& b, int kf, int i, const cx<R>* r, cx<R>* z) {
   constexpr int E = 4, CH = 32 * E;
   const int Lx = g.Lx, A = g.A;
   const cx<R>* __restrict__ pre = reinterpret_cast<const cx<R>*>(b.pre) + ((size_t)kf * nifc(g) + (size_t)i * A) * 2;
@@ -568,7 +704,7 @@ __device__ void cluster_sum_r(cg::cluster_group& cl, RedSmem& rs, int& phase, in
 // inner solves (refined in FP64 one level up) run entirely in complex64.
 // Right-hand side in IF_B, solution in IF_X.  Returns the iteration count;
 // *conv is set to 0 if the cap was hit.
-template <typename R>
+template <typename R, bool WD>
 __device__ int schur_cocg(cg::cluster_group& cl, RedSmem& rs, int& phase, const Geo& g,
                           const Bufs& b, int kf, int i, double tol, cx<R>* sm, Pipe& pp,
                           int* conv) {
@@ -624,7 +760,7 @@ __device__ int schur_cocg(cg::cluster_group& cl, RedSmem& rs, int& phase, const 
     }
     ++it;
     cl.sync();                                  // P of both neighbour layers is final
-    sweep<R>(g, i, sa, sm, pp, sweep_cnt(g, b, kf, i));   // B^-1 E p on this subdomain
+    sweep<R, WD>(g, i, sa, sm, pp, sweep_cnt(g, b, kf, i));   // B^-1 E p on this subdomain
     cl.sync();                                  // boundary values of every subdomain written
     C v1[1] = {{0, 0}};
     if (has) {
@@ -739,7 +875,7 @@ __device__ void residual_H(const Geo& g, const Bufs& b, int kf, int i, const cxd
 // sc: the solve runs on rhs / sc and its result is scaled back by sc, so the
 // R-precision recurrences work on O(1) numbers (the squared norms of the
 // shrinking refinement residuals would leave float range otherwise).
-template <typename R>
+template <typename R, bool WD>
 __device__ int solve_H(cg::cluster_group& cl, RedSmem& rs, int& phase, const Geo& g,
                        const Bufs& b, int kf, int i, const cxd* rhs, cxd* xout, bool zero_B,
                        double sc, double tol, cx<R>* sm, Pipe& pp, int* conv) {
@@ -759,7 +895,7 @@ __device__ int solve_H(cg::cluster_group& cl, RedSmem& rs, int& phase, const Geo
     sa.dst_op = 0;
     sa.bnd_lo = bnd_ptr<R>(g, b, kf, i, 0);
     sa.bnd_hi = bnd_ptr<R>(g, b, kf, i, 1);
-    sweep<R>(g, i, sa, sm, pp, sweep_cnt(g, b, kf, i));
+    sweep<R, WD>(g, i, sa, sm, pp, sweep_cnt(g, b, kf, i));
     cl.sync();
     if (has) {
       const cx<R>* bl_i = bnd_ptr<R>(g, b, kf, i, 1);
@@ -771,7 +907,7 @@ __device__ int solve_H(cg::cluster_group& cl, RedSmem& rs, int& phase, const Geo
     for (int a = threadIdx.x; a < A; a += DY_THREADS) Bv[(size_t)i * A + a] = cconv<R>(isc * rc[a]);
   }
   __syncthreads();
-  int it = schur_cocg<R>(cl, rs, phase, g, b, kf, i, tol, sm, pp, conv);
+  int it = schur_cocg<R, WD>(cl, rs, phase, g, b, kf, i, tol, sm, pp, conv);
   cl.sync();
   const cx<R>* X = ifv_ptr<R>(g, b, kf, IF_X);
   SweepArgs<R> sb = sweep_base<R>(g, b, kf, i);
@@ -780,7 +916,7 @@ __device__ int solve_H(cg::cluster_group& cl, RedSmem& rs, int& phase, const Geo
   sb.dst = xout + i * nsub;
   sb.out_scale = sc;
   sb.dst_op = zero_B ? 3 : 2;
-  sweep<R>(g, i, sb, sm, pp, sweep_cnt(g, b, kf, i));
+  sweep<R, WD>(g, i, sb, sm, pp, sweep_cnt(g, b, kf, i));
   if (has) {
     cxd* xc = xout + g.ifc_off + (size_t)i * A;
     for (int a = threadIdx.x; a < A; a += DY_THREADS) xc[a] = sc * cconv<double>(X[(size_t)i * A + a]);
@@ -789,25 +925,52 @@ __device__ int solve_H(cg::cluster_group& cl, RedSmem& rs, int& phase, const Geo
 }
 
 constexpr size_t YBUF_MAX = 64 * 1024;   // forward intermediates kept on chip up to this size
+
+// Shared-memory plan of a sweep: ring of S slots of CR x W entries (CR = W when
+// a whole slice block fits a slot, the W <= 64 strips; row chunks otherwise),
+// two z vectors, and the on-chip row buffer when it fits.
+struct RingPlan {
+  int CR, S;
+  size_t ybuf, smem;
+};
 template <typename R>
-__host__ __device__ inline size_t ybuf_bytes(int W, int Lx) {
-  const size_t b = (size_t)Lx * W * sizeof(cx<R>);
-  return b <= YBUF_MAX ? b : 0;
+__host__ __device__ inline RingPlan ring_plan(int W, int Lx) {
+  RingPlan rp;
+  const size_t cs = sizeof(cx<R>);
+  const size_t yb = (size_t)Lx * W * cs;
+  if (W <= DY_MAXW_SMEM) {
+    rp.ybuf = yb <= YBUF_MAX ? yb : 0;
+    rp.CR = W;
+    long S = ((long)100 * 1024 - (long)rp.ybuf) / (long)(W * W * cs);   // two CTAs per SM
+    rp.S = (int)(S > MAX_STAGES ? MAX_STAGES : (S < 2 ? 2 : S));
+  } else {
+    rp.ybuf = yb;                                                       // one CTA per SM
+    const long budget = (long)200 * 1024 - (long)yb - (long)(2 * W * cs);
+    // largest divisor of W whose chunks leave >= 4 ring slots (>= 2 as a last
+    // resort); a chunk row is W entries, a multiple of 32 bytes, so any row count
+    // keeps the bulk copies 16-byte aligned
+    rp.CR = 0;
+    rp.S = 0;
+    for (int want = 4; want >= 2 && !rp.CR; want -= 2)
+      for (int cr = W; cr >= 1; --cr) {
+        if (W % cr) continue;
+        const long S = budget / (long)((size_t)cr * W * cs);
+        if (S >= want) {
+          rp.CR = cr;
+          rp.S = (int)(S > MAX_STAGES ? MAX_STAGES : S);
+          break;
+        }
+      }
+  }
+  rp.smem = rp.CR ? (size_t)rp.S * rp.CR * W * cs + (size_t)2 * W * cs + rp.ybuf : 0;
+  return rp;
 }
-// copy-ring depth: what is left of a ~100 KB per-CTA budget (two CTAs per SM)
 template <typename R>
-__host__ __device__ inline int ring_stages(int W, int Lx) {
-  const long slot = (long)W * W * (long)sizeof(cx<R>);
-  long S = ((long)100 * 1024 - (long)ybuf_bytes<R>(W, Lx)) / slot;
-  if (S > MAX_STAGES) S = MAX_STAGES;
-  if (S < 2) S = 2;
-  return (int)S;
-}
+__host__ __device__ inline size_t ybuf_bytes(int W, int Lx) { return ring_plan<R>(W, Lx).ybuf; }
 template <typename R>
-__host__ __device__ inline size_t solver_smem(int W, int Lx) {
-  return (size_t)ring_stages<R>(W, Lx) * W * W * sizeof(cx<R>) + (size_t)2 * W * sizeof(cx<R>) +
-         ybuf_bytes<R>(W, Lx);
-}
+__host__ __device__ inline int ring_stages(int W, int Lx) { return ring_plan<R>(W, Lx).S; }
+template <typename R>
+__host__ __device__ inline size_t solver_smem(int W, int Lx) { return ring_plan<R>(W, Lx).smem; }
 
 // ---------------------------------------------------------------- kernels
 // u = X q_j  (Sec. 2.3 Eqs. 6-8), with u = v - w computed as the solution of
@@ -817,7 +980,7 @@ __host__ __device__ inline size_t solver_smem(int W, int Lx) {
 //   mixed = 1: sweeps in complex64 (R = float).  w_B is refined against FP64
 //              residuals of B, u against FP64 residuals of H, each until the
 //              relative residual is below refine_tol.
-template <typename R>
+template <typename R, bool WD>
 __global__ void __launch_bounds__(DY_THREADS, 2) k_xmatvec(Geo g, Bufs b, int j, int mixed) {
   cg::cluster_group cl = cg::this_cluster();
   __shared__ RedSmem rs;
@@ -829,13 +992,15 @@ __global__ void __launch_bounds__(DY_THREADS, 2) k_xmatvec(Geo g, Bufs b, int j,
   if (st[ST_DONE]) return;                 // same value in every CTA of the cluster
   Pipe pp;
   pp.bar = bars;
-  pp.S = ring_stages<R>(g.W, g.Lx);
+  const RingPlan rp = ring_plan<R>(g.W, g.Lx);
+  pp.S = rp.S;
+  pp.CR = rp.CR;
   pp.ring = smem_raw;
   pp.seq = 0;
   pp.err = &err;
   pipe_init(pp);
-  cx<R>* sm = reinterpret_cast<cx<R>*>(smem_raw + (size_t)pp.S * g.W * g.W * sizeof(cx<R>));
-  pp.ybuf = ybuf_bytes<R>(g.W, g.Lx) ? (void*)(sm + 2 * g.W) : nullptr;
+  cx<R>* sm = reinterpret_cast<cx<R>*>(smem_raw + (size_t)rp.S * rp.CR * g.W * sizeof(cx<R>));
+  pp.ybuf = rp.ybuf ? (void*)(sm + 2 * g.W) : nullptr;
   layer_diag<R>(g, b, kf, i);
   int phase = 0;
   const bool has = i < p - 1;
@@ -850,7 +1015,7 @@ __global__ void __launch_bounds__(DY_THREADS, 2) k_xmatvec(Geo g, Bufs b, int j,
     sa.src = q + i * nsub;
     sa.bnd_lo = bnd_ptr<R>(g, b, kf, i, 0);
     sa.bnd_hi = bnd_ptr<R>(g, b, kf, i, 1);
-    sweep<R>(g, i, sa, sm, pp, sweep_cnt(g, b, kf, i));
+    sweep<R, WD>(g, i, sa, sm, pp, sweep_cnt(g, b, kf, i));
     cl.sync();
     cx<R>* Bv = ifv_ptr<R>(g, b, kf, IF_B);
     if (has) {
@@ -861,7 +1026,7 @@ __global__ void __launch_bounds__(DY_THREADS, 2) k_xmatvec(Geo g, Bufs b, int j,
         Bv[(size_t)i * A + a] = (R)g.t * (bl_i[a] + bl_n[a]) - cconv<R>(qc[a]);
     }
     __syncthreads();
-    iters += schur_cocg<R>(cl, rs, phase, g, b, kf, i, g.krylov_tol, sm, pp, &conv);
+    iters += schur_cocg<R, WD>(cl, rs, phase, g, b, kf, i, g.krylov_tol, sm, pp, &conv);
     conv_all &= conv;
     solves = 1;
     cl.sync();
@@ -871,7 +1036,7 @@ __global__ void __launch_bounds__(DY_THREADS, 2) k_xmatvec(Geo g, Bufs b, int j,
     sb.lay_hi = has ? X + (size_t)i * A : nullptr;
     sb.dst = u + i * nsub;
     sb.dst_op = 0;
-    sweep<R>(g, i, sb, sm, pp, sweep_cnt(g, b, kf, i));
+    sweep<R, WD>(g, i, sb, sm, pp, sweep_cnt(g, b, kf, i));
     if (has) {
       cxd* uc = u + g.ifc_off + (size_t)i * A;
       for (int a = threadIdx.x; a < A; a += DY_THREADS) uc[a] = -cconv<double>(X[(size_t)i * A + a]);
@@ -886,7 +1051,7 @@ __global__ void __launch_bounds__(DY_THREADS, 2) k_xmatvec(Geo g, Bufs b, int j,
       sa.src = q + i * nsub;
       sa.dst = wv + i * nsub;
       sa.dst_op = 0;
-      sweep<R>(g, i, sa, sm, pp, sweep_cnt(g, b, kf, i));
+      sweep<R, WD>(g, i, sa, sm, pp, sweep_cnt(g, b, kf, i));
       for (int r = 0; r < g.refine_max; ++r) {
         __syncthreads();
         double rn, qn;
@@ -898,7 +1063,7 @@ __global__ void __launch_bounds__(DY_THREADS, 2) k_xmatvec(Geo g, Bufs b, int j,
         sc.src = rv + i * nsub;
         sc.dst = wv + i * nsub;
         sc.dst_op = 1;
-        sweep<R>(g, i, sc, sm, pp, sweep_cnt(g, b, kf, i));
+        sweep<R, WD>(g, i, sc, sm, pp, sweep_cnt(g, b, kf, i));
       }
     }
     cl.sync();                             // w_B of the neighbour subdomains is final
@@ -917,6 +1082,7 @@ __global__ void __launch_bounds__(DY_THREADS, 2) k_xmatvec(Geo g, Bufs b, int j,
         hr[k] = v;
       }
     }
+    __syncthreads();                       // interface entries of hr are written by other threads
     double hn;
     {
       cxd v1[1] = {{0, 0}};
@@ -927,7 +1093,7 @@ __global__ void __launch_bounds__(DY_THREADS, 2) k_xmatvec(Geo g, Bufs b, int j,
       hn = sqrt(v1[0].x);
     }
     if (hn > 0.0) {
-      iters += solve_H<R>(cl, rs, phase, g, b, kf, i, hr, u, true, hn, g.krylov_tol, sm, pp, &conv);
+      iters += solve_H<R, WD>(cl, rs, phase, g, b, kf, i, hr, u, true, hn, g.krylov_tol, sm, pp, &conv);
       conv_all &= conv;
       ++solves;
     } else {
@@ -942,7 +1108,7 @@ __global__ void __launch_bounds__(DY_THREADS, 2) k_xmatvec(Geo g, Bufs b, int j,
       cluster_sum<2>(cl, rs, phase, p, v2);
       if (v2[0].x <= g.refine_tol * g.refine_tol * v2[1].x) break;
       ++refines;
-      iters += solve_H<R>(cl, rs, phase, g, b, kf, i, rv, wv, false, sqrt(v2[0].x), g.krylov_tol, sm,
+      iters += solve_H<R, WD>(cl, rs, phase, g, b, kf, i, rv, wv, false, sqrt(v2[0].x), g.krylov_tol, sm,
                           pp, &conv);
       conv_all &= conv;
       ++solves;
@@ -986,6 +1152,8 @@ __global__ void __launch_bounds__(DY_THREADS) k_lanczos(Geo g, Bufs b, int j) {
   cxd* acc = b.acc + (size_t)kf * Ndd;
   cxd* lan = b.lan + (size_t)kf * (g.k_max + 1) * 2;
   const cxd beta_j = (j > 0) ? lan[2 * j + 1] : cxd{0, 0};
+  // read before the first cluster barrier: CTA 0 updates it once all CTAs passed the last one
+  const double maxT_prev = b.maxT[kf];
 
   cxd v1[1] = {{0, 0}};
   for (int e = threadIdx.x; e < n; e += DY_THREADS) {
@@ -1037,7 +1205,7 @@ __global__ void __launch_bounds__(DY_THREADS) k_lanczos(Geo g, Bufs b, int j) {
   cluster_sum<2>(cl, rs, phase, p, v2);
   const cxd rr = v2[0];
   const cxd beta = csqrt_principal(rr);
-  const double maxT = fmax(b.maxT[kf], sqrt(cabs2(alpha)));
+  const double maxT = fmax(maxT_prev, sqrt(cabs2(alpha)));
   const double babs = sqrt(cabs2(beta));
   int done = 0, flag = 0;
   if (j == g.k_max - 1) {
@@ -1143,7 +1311,7 @@ __global__ void k_status(const int* st, int K, int* status) {
 }
 
 // w = blkdiag(B^-1, 0) q for DD-layout vectors (Eq. 7), one CTA per subdomain.
-template <typename R>
+template <typename R, bool WD>
 __global__ void __launch_bounds__(DY_THREADS, 2) k_bsolve(Geo g, Bufs b, const cxd* q, cxd* w) {
   __shared__ __align__(8) uint64_t bars[MAX_STAGES];
   __shared__ int err;
@@ -1152,18 +1320,20 @@ __global__ void __launch_bounds__(DY_THREADS, 2) k_bsolve(Geo g, Bufs b, const c
   const size_t nsub = (size_t)g.Lx * g.W;
   Pipe pp;
   pp.bar = bars;
-  pp.S = ring_stages<R>(g.W, g.Lx);
+  const RingPlan rp = ring_plan<R>(g.W, g.Lx);
+  pp.S = rp.S;
+  pp.CR = rp.CR;
   pp.ring = smem_raw;
   pp.seq = 0;
   pp.err = &err;
   pipe_init(pp);
-  cx<R>* sm = reinterpret_cast<cx<R>*>(smem_raw + (size_t)pp.S * g.W * g.W * sizeof(cx<R>));
-  pp.ybuf = ybuf_bytes<R>(g.W, g.Lx) ? (void*)(sm + 2 * g.W) : nullptr;
+  cx<R>* sm = reinterpret_cast<cx<R>*>(smem_raw + (size_t)rp.S * rp.CR * g.W * sizeof(cx<R>));
+  pp.ybuf = rp.ybuf ? (void*)(sm + 2 * g.W) : nullptr;
   SweepArgs<R> sa = sweep_base<R>(g, b, kf, i);
   sa.src = q + (size_t)kf * g.Ndd + i * nsub;
   sa.dst = w + (size_t)kf * g.Ndd + i * nsub;
   sa.dst_op = 0;
-  sweep<R>(g, i, sa, sm, pp, sweep_cnt(g, b, kf, i));
+  sweep<R, WD>(g, i, sa, sm, pp, sweep_cnt(g, b, kf, i));
   if (i < g.p - 1)
     for (int a = threadIdx.x; a < g.A; a += DY_THREADS)
       w[(size_t)kf * g.Ndd + g.ifc_off + (size_t)i * g.A + a] = cxd{0, 0};
@@ -1197,12 +1367,20 @@ cudaError_t launch_cluster(Kern kern, dim3 grid, int cx_, size_t smem, cudaStrea
 
 template <typename R>
 size_t sweep_smem(const Geo& g) { return solver_smem<R>(g.W, g.Lx); }
+template <typename R>
+bool sweep_chunked_form(const Geo& g) { return ring_plan<R>(g.W, g.Lx).CR < g.W; }
 
 }  // namespace
 
+size_t dyson_internal_sweep_smem(const Geo& g, bool mixed) {
+  return mixed ? sweep_smem<float>(g) : sweep_smem<double>(g);
+}
+
 template <typename R>
 cudaError_t launch_xmatvec(const Geo& g, const Bufs& b, int K, int j, int mixed, cudaStream_t st) {
-  return launch_cluster(k_xmatvec<R>, dim3(g.p, K), g.p, sweep_smem<R>(g), st, g, b, j, mixed);
+  if (sweep_chunked_form<R>(g))
+    return launch_cluster(k_xmatvec<R, true>, dim3(g.p, K), g.p, sweep_smem<R>(g), st, g, b, j, mixed);
+  return launch_cluster(k_xmatvec<R, false>, dim3(g.p, K), g.p, sweep_smem<R>(g), st, g, b, j, mixed);
 }
 template cudaError_t launch_xmatvec<double>(const Geo&, const Bufs&, int, int, int, cudaStream_t);
 template cudaError_t launch_xmatvec<float>(const Geo&, const Bufs&, int, int, int, cudaStream_t);
@@ -1248,9 +1426,12 @@ template <typename R>
 cudaError_t launch_bsolve(const Geo& g, const Bufs& b, int K, const cxd* q_dd, cxd* w_dd,
                           cudaStream_t st) {
   size_t smem = sweep_smem<R>(g);
-  cudaError_t e = raise_smem_limit((const void*)k_bsolve<R>, smem);
+  const bool wide = sweep_chunked_form<R>(g);
+  const void* fn = wide ? (const void*)k_bsolve<R, true> : (const void*)k_bsolve<R, false>;
+  cudaError_t e = raise_smem_limit(fn, smem);
   if (e != cudaSuccess) return e;
-  k_bsolve<R><<<dim3(g.p, K), DY_THREADS, smem, st>>>(g, b, q_dd, w_dd);
+  if (wide) k_bsolve<R, true><<<dim3(g.p, K), DY_THREADS, smem, st>>>(g, b, q_dd, w_dd);
+  else k_bsolve<R, false><<<dim3(g.p, K), DY_THREADS, smem, st>>>(g, b, q_dd, w_dd);
   return cudaGetLastError();
 }
 template cudaError_t launch_bsolve<double>(const Geo&, const Bufs&, int, const cxd*, cxd*, cudaStream_t);

@@ -71,10 +71,25 @@ def test_bad_geometry_rejected_without_gpu(lib, bad):
 
 
 def test_wide_slices_reported_unsupported(lib):
-    g = D.make_geometry((32, 32, 32), p=2, k_max=4, max_freqs=1)
+    g = D.make_geometry((32, 32, 32), p=2, k_max=4, max_freqs=1)      # W = 32 * 16 = 512
     with pytest.raises(D.DysonError) as e:
         D.dyson_plan_footprint(g)
     assert e.value.code == -4
+
+
+def test_wide_slices_within_limits(lib):
+    # 32^3 with p = 8: W = 128, taken by the global-memory factor and chunked sweeps;
+    # the footprint carries the factor workspace (304 CTAs x 2 W x W FP64 matrices)
+    g = D.make_geometry((32, 32, 32), p=8, k_max=48, max_freqs=1)
+    assert D.dyson_plan_footprint(g) > 304 * 2 * 128 * 128 * 16
+    # W = 256 with Lx = 64: the FP64 row buffer (256 KB) cannot stay on chip,
+    # the complex64 one (128 KB) can
+    g = D.make_geometry((64, 16, 33), p=2, k_max=4, max_freqs=1)
+    with pytest.raises(D.DysonError) as e:
+        D.dyson_plan_footprint(g)
+    assert e.value.code == -4 and "row buffer" in str(e.value)
+    g.precision = D.DYSON_MIXED
+    assert D.dyson_plan_footprint(g) > 0
 
 
 def test_footprint(lib):

@@ -14,11 +14,10 @@ from oracle import dyson_oracle as O
 from paper_1102_3137_gb300 import dyson as D
 from paper_1102_3137_gb300 import inputs as I
 
-pytestmark = pytest.mark.gpu
+from parity_util import (OPEN, TOL_FP64, TOL_MIXED, oracle_parts, oracle_sensitivity, plan_for,
+                         relerr, stepwise_check, wl)
 
-TOL_FP64 = 1e-10
-TOL_MIXED = 1e-6
-OPEN = (False, False, False)
+pytestmark = pytest.mark.gpu
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -26,18 +25,6 @@ def built():
     from paper_1102_3137_gb300 import build
     build.build()
     D.load()
-
-
-def wl(L, p, k, K=4, seed=11, b_max=0.5, trap=0.01, beta=10.0):
-    return I.Workload("t", tuple(L), -1.0, 0.0, trap, b_max, beta, K, p, k, seed)
-
-
-def relerr(a, b):
-    return float(np.max(np.abs(a - b) / np.abs(b)))
-
-
-def plan_for(w, precision=D.DYSON_FP64, K=None, **kw):
-    return D.Plan(w.L, w.t, w.mu, w.p, w.k, precision, max_freqs=K or w.K, **kw)
 
 
 # ------------------------------------------------------------------ stencil (Eq. 1)
@@ -134,50 +121,6 @@ def test_xmatvec(L, p, precision, tol):
 # (k past closure) give the exact diagonal and are compared directly.
 
 
-def oracle_parts(w, omega_k, V, sigma_k):
-    z = O.dyson_diagonal(omega_k, w.mu, V, sigma_k)
-    subs = O.Subdomains(w.L, OPEN, w.t, z, w.p)
-    full = O.FullLattice(w.L, OPEN, w.t, z)
-    return subs, (lambda q: full.solve(q) - subs.solve(q))
-
-
-def oracle_sensitivity(w, subs, X, q1, eps, seed=0):
-    """Largest relative change of the oracle's diagonal when X q is perturbed by relative eps."""
-    rng = np.random.default_rng(seed)
-    base = subs.diagB + O.cs_lanczos(X, q1, w.k)[0]
-
-    def Xp(q):
-        u = X(q)
-        n = np.linalg.norm(u) / np.sqrt(u.size)
-        return u + eps * n * (rng.normal(size=u.shape) + 1j * rng.normal(size=u.shape))
-
-    pert = subs.diagB + O.cs_lanczos(Xp, q1, w.k)[0]
-    return base, float(np.max(np.abs(pert - base) / np.abs(base)))
-
-
-def stepwise_check(w, pl, kf, subs, X, q1, out_k, info, tol):
-    n = int(info["steps"][kf])
-    Q = D.dyson_lanczos_basis(pl.handle, kf, n + 1, w.N)
-    al = info["alpha"][kf, :n]
-    be = info["beta"][kf, 1:n]
-    Qk = Q[:n].T
-    T = np.diag(al) + np.diag(be, 1) + np.diag(be, -1)
-    q1n = q1 / np.sqrt(q1 @ q1)
-    assert np.max(np.abs(Q[0] - q1n)) <= 1e-14 * np.max(np.abs(q1n))
-    nrm = np.linalg.norm(Qk, axis=0)
-    G = Qk.T @ Qk
-    assert np.max(np.abs(G - np.eye(n)) / np.outer(nrm, nrm)) <= tol
-    XQ = np.stack([X(Qk[:, j]) for j in range(n)], 1)
-    R = XQ - Qk @ T
-    R[:, n - 1] -= Q[n]                       # raw residual beta_{k+1} q_{k+1} of the last step
-    scale = np.abs(XQ) + np.abs(Qk) @ np.abs(T)
-    scale[:, n - 1] += np.abs(Q[n])
-    assert np.max(np.abs(R)) <= tol * np.max(scale)
-    ref = subs.diagB + np.einsum("ij,jk,ik->i", Qk, T, Qk)
-    assert relerr(out_k, ref) <= tol
-    return n
-
-
 @pytest.mark.parametrize("precision,tol", [(D.DYSON_FP64, TOL_FP64), (D.DYSON_MIXED, TOL_MIXED)])
 def test_solve_terminated_square16(precision, tol):
     """16x16, p = 2 (m = 16), k cap 24: the Krylov space of X closes, Eq. 10 holds and
@@ -256,6 +199,23 @@ def test_device_pointers_and_batch_invariance():
     for k in (0, 5):
         one = pl.solve(omega[k:k + 1], V, np.ascontiguousarray(sigma[k:k + 1]), q1)
         assert np.array_equal(one[0], ref[k])
+
+
+@pytest.mark.parametrize("L,p,k", [((40, 64), 4, 12), ((24, 20), 3, 6), ((6, 9, 16), 2, 6)])
+@pytest.mark.parametrize("precision", [D.DYSON_FP64, D.DYSON_MIXED])
+def test_repeat_is_bitwise(L, p, k, precision):
+    """Every reduction has a fixed order, so repeated solves agree bit for bit and
+    take the same inner iterations.  Lx*W is not a multiple of the CTA size in these
+    geometries, so a site's owner thread changes between the subdomain and
+    interface phases: a missing barrier between them shows up here."""
+    w = wl(L, p, k, K=5, seed=23)
+    omega, V, sigma, q1 = I.make_inputs(w)
+    pl = plan_for(w, precision)
+    ref = pl.solve(omega, V, sigma, q1)
+    it0 = pl.info(w.K)["iters"].copy()
+    for _ in range(3):
+        assert np.array_equal(pl.solve(omega, V, sigma, q1), ref)
+        assert np.array_equal(pl.info(w.K)["iters"], it0)
 
 
 def test_iteration_cap_reports_status():
