@@ -195,6 +195,18 @@ cudaError_t launch_spmv(const Geo& g, const double* V, const double* omega, cons
 template <typename R>
 cudaError_t launch_bsolve(const Geo& g, const Bufs& b, int K, const cxd* q_dd, cxd* w_dd,
                           cudaStream_t st);
+// the X-matvec and subdomain-solve launchers exist for complex64 (k_xmatvec_c64.cu)
+// and complex128 (k_xmatvec_c128.cu)
+template <>
+cudaError_t launch_xmatvec<float>(const Geo& g, const Bufs& b, int K, int j, int mixed, cudaStream_t st);
+template <>
+cudaError_t launch_xmatvec<double>(const Geo& g, const Bufs& b, int K, int j, int mixed, cudaStream_t st);
+template <>
+cudaError_t launch_bsolve<float>(const Geo& g, const Bufs& b, int K, const cxd* q_dd, cxd* w_dd,
+                                 cudaStream_t st);
+template <>
+cudaError_t launch_bsolve<double>(const Geo& g, const Bufs& b, int K, const cxd* q_dd, cxd* w_dd,
+                                  cudaStream_t st);
 cudaError_t launch_gather(const Geo& g, const Bufs& b, int K, const cxd* nat, cxd* dd,
                           size_t dd_stride, cudaStream_t st);
 cudaError_t launch_scatter(const Geo& g, const Bufs& b, int K, const cxd* dd, cxd* nat,

@@ -69,8 +69,20 @@ __device__ __forceinline__ void smem_matmul(cx<R>* C, const cx<R>* X, const cx<R
 }
 
 // R: arithmetic of the recursion; S: storage of the g_s handed to the sweeps.
-// With S != R (mixed form) the g_s are kept in R in b.g64 for the backward
-// pass and rounded to S only for the sweeps.
+//
+// FP64 form (S == R): one-sided recursion, g_s left-connected for every s,
+// stored row-major for the 8-warp sweeps.
+//
+// Mixed form (S != R): two-sided recursion, so that the complex64 sweeps can
+// run two chains at once (one from each end).  With m = Lx / 2:
+//   left   g_s = (D_s - t^2 g_{s-1})^-1            s < m
+//   right  g_s = (D_s - t^2 g_{s+1})^-1            s > m
+//   middle G_mm = (D_m - t^2 g_{m-1} - t^2 g_{m+1})^-1
+//   G_ss = g_s + t^2 g_s G_{s+1,s+1} g_s  (s < m),  g_s + t^2 g_s G_{s-1,s-1} g_s  (s > m)
+// Slot s holds g_s, or G_mm for s = m.  The recursion runs in R (FP64) with
+// the factors kept in b.g64; the complex64 copy in b.g is written with column
+// pairs interleaved: entry (r, c) of a block at ((c / 2) W + r) 2 + c % 2, so
+// that the lane owning row r reads columns 2k, 2k+1 as one 16-byte word.
 template <typename R, typename S>
 __global__ void __launch_bounds__(DY_THREADS) k_factor(Geo g, Bufs b) {
   using C = cx<R>;
@@ -88,11 +100,14 @@ __global__ void __launch_bounds__(DY_THREADS) k_factor(Geo g, Bufs b) {
   cxd* dB = b.diagB + (size_t)kf * g.Ndd + (size_t)i * Lx * W;
   const R t = (R)g.t, t2 = (R)(g.t * g.t);
 
-  // forward: g_s = (D_s - t^2 g_{s-1})^-1, A holds g_{s-1} on entry
-  for (int s = 0; s < Lx; ++s) {
+  // A = D_s - t^2 (pa + pb); pa may be A itself (each entry is read and
+  // written by the same thread), either may be null
+  auto form = [&](int s, const C* pa, const C* pb) {
     for (int e = threadIdx.x; e < n; e += DY_THREADS) {
       int r = e / W, c = e - r * W;
-      C v = (s > 0) ? (-t2) * A[e] : C{0, 0};
+      C v = {0, 0};
+      if (pa) v = v - t2 * pa[e];
+      if (pb) v = v - t2 * pb[e];
       if (r < w && c < w) {
         if (r == c) {
           cxd d = dyson_diag(g, b, kf, sub_nat(g, i, s, r));
@@ -105,6 +120,9 @@ __global__ void __launch_bounds__(DY_THREADS) k_factor(Geo g, Bufs b) {
       }
       A[e] = v;
     }
+  };
+  // invert A in place, zero its padding and store it in slot s
+  auto invert_store = [&](int s) {
     gj_invert<R>(A, W);
     for (int e = threadIdx.x; e < n; e += DY_THREADS) {
       int r = e / W, c = e - r * W;
@@ -112,28 +130,56 @@ __global__ void __launch_bounds__(DY_THREADS) k_factor(Geo g, Bufs b) {
       if (r >= w || c >= w) v = C{0, 0};
       A[e] = v;
       gout[(size_t)s * n + e] = v;
-      if (two) gsw[(size_t)s * n + e] = cconv<S>(v);
+      if (two) gsw[(size_t)s * n + ((size_t)(c >> 1) * W + r) * 2 + (c & 1)] = cconv<S>(v);
     }
     __syncthreads();
-  }
-  // backward: A holds G_{s+1,s+1}
-  for (int r = threadIdx.x; r < W; r += DY_THREADS)
-    dB[(size_t)(Lx - 1) * W + r] = (r < w) ? cconv<double>(A[r * W + r]) : cxd{0, 0};
-  for (int s = Lx - 2; s >= 0; --s) {
+  };
+  auto diag_out = [&](int s) {
+    for (int r = threadIdx.x; r < W; r += DY_THREADS)
+      dB[(size_t)s * W + r] = (r < w) ? cconv<double>(A[r * W + r]) : cxd{0, 0};
+  };
+  // A <- g_s + t^2 g_s A g_s with g_s from slot s (A = G of the neighbour toward the start)
+  auto grow_G = [&](int s) {
     for (int e = threadIdx.x; e < n; e += DY_THREADS) Bm[e] = gout[(size_t)s * n + e];
     __syncthreads();
-    smem_matmul<R>(Cm, Bm, A, W);            // g_s G_{s+1}
+    smem_matmul<R>(Cm, Bm, A, W);
     __syncthreads();
     for (int e = threadIdx.x; e < n; e += DY_THREADS) {
       int r = e / W, c = e - r * W;
       C acc = {0, 0};
       const C* xr = Cm + r * W;
       for (int k = 0; k < W; ++k) acc = cfma(xr[k], Bm[k * W + c], acc);
-      A[e] = Bm[e] + t2 * acc;               // g_s + t^2 g_s G_{s+1} g_s
+      A[e] = Bm[e] + t2 * acc;
     }
     __syncthreads();
-    for (int r = threadIdx.x; r < W; r += DY_THREADS)
-      dB[(size_t)s * W + r] = (r < w) ? cconv<double>(A[r * W + r]) : cxd{0, 0};
+    diag_out(s);
+  };
+
+  if constexpr (!two) {
+    for (int s = 0; s < Lx; ++s) {          // forward: A holds g_{s-1} on entry
+      form(s, s > 0 ? A : nullptr, nullptr);
+      invert_store(s);
+    }
+    diag_out(Lx - 1);                        // backward: A holds G_{s+1,s+1}
+    for (int s = Lx - 2; s >= 0; --s) grow_G(s);
+  } else {
+    const int m = Lx / 2;
+    for (int s = 0; s < m; ++s) {           // left chain
+      form(s, s > 0 ? A : nullptr, nullptr);
+      invert_store(s);
+    }
+    for (int s = Lx - 1; s > m; --s) {      // right chain
+      form(s, s < Lx - 1 ? A : nullptr, nullptr);
+      invert_store(s);
+    }
+    form(m, m > 0 ? gout + (size_t)(m - 1) * n : nullptr,
+         m < Lx - 1 ? gout + (size_t)(m + 1) * n : nullptr);
+    invert_store(m);                         // G_mm
+    diag_out(m);
+    for (int s = m - 1; s >= 0; --s) grow_G(s);
+    for (int e = threadIdx.x; e < n; e += DY_THREADS) A[e] = gout[(size_t)m * n + e];
+    __syncthreads();
+    for (int s = m + 1; s < Lx; ++s) grow_G(s);
   }
   // interface part of diag(B^-1) is zero (blkdiag(B^-1, 0), Eq. 9)
   if (i == g.p - 1) {

@@ -1,1135 +1,9 @@
-// Lanczos-based low-rank correction: the per-step kernels.
-//
-// Every kernel here runs one thread-block cluster per frequency with one CTA
-// per subdomain (cluster = p CTAs, grid = p x K).  CTA i owns subdomain i's
-// slice block of every DD-layout vector and interface layer i (i < p-1).
-// Reductions over a frequency's lattice are two-level: a fixed-order
-// block reduction, then every CTA reads the p partials from distributed
-// shared memory in rank order, so all CTAs of a cluster hold bit-identical
-// scalars and take identical branch decisions (no CTA can leave a cluster
-// barrier behind).  Every kernel that reads peers' shared memory ends with a
-// cluster barrier, so no CTA exits while a peer may still be reading it.
-//
-// X-"matvec" (Sec. 2.3, Eqs. 6-8).  The paper defines u = v - w with
-// H v = q and w = blkdiag(B^-1, 0) q.  Eliminating the subdomain unknowns
-// of H v = q gives, without ever forming S = C - E^T B^-1 E (Eq. 4),
-//     y   = S^-1 (E^T B^-1 q_B - q_C),
-//     u_B = B^-1 E y,   u_C = -y,
-// which is exactly v - w with no cancellation.  S y = r is solved by COCG
-// (conjugate orthogonal CG: CG in the bilinear form, valid for complex
-// symmetric S) whose S-products are subdomain solves with boundary-only
-// right-hand sides.
-#include <cooperative_groups.h>
-
-#include "dyson_common.cuh"
-
-namespace cg = cooperative_groups;
+// Lanczos step, start vector and the small per-frequency kernels (the
+// X-matvec and subdomain-solve kernels, which carry the block sweeps, are
+// compiled in k_xmatvec_c64.cu and k_xmatvec_c128.cu).
+#include "solve_device.cuh"
 
 namespace {
-
-constexpr double TERM_TOL = 1e-12;    // |beta_{j+1}| <= TERM_TOL * max|T|: invariant subspace
-constexpr double BRK_TOL = 1e-14;     // |r^T r| <= BRK_TOL * ||r||^2: breakdown
-constexpr int KMAX_SMEM = 256;        // largest Lanczos rank cap
-
-__device__ __forceinline__ size_t own_idx(const Geo& g, int i, int e, int nsub) {
-  return e < nsub ? (size_t)i * nsub + e : (size_t)g.ifc_off + (size_t)i * g.A + (e - nsub);
-}
-__device__ __forceinline__ int own_count(const Geo& g, int i) {
-  return g.Lx * g.W + (i < g.p - 1 ? g.A : 0);
-}
-
-// ---------------------------------------------------------------- reductions
-struct RedSmem {
-  cxd wred[DY_WARPS * 8];
-  cxd slot[2 * 8];
-  cxd res[8];
-};
-
-__device__ __forceinline__ cxd warp_sum(cxd v) {
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    v.x += __shfl_xor_sync(0xffffffffu, v.x, off);
-    v.y += __shfl_xor_sync(0xffffffffu, v.y, off);
-  }
-  return v;
-}
-
-// Sum NV complex partials over the whole cluster; every thread gets the totals.
-template <int NV>
-__device__ void cluster_sum(cg::cluster_group& cl, RedSmem& rs, int& phase, int p, cxd (&v)[NV]) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
-  if (lane == 0) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) rs.wred[wid * 8 + k] = v[k];
-  }
-  __syncthreads();
-  if (threadIdx.x < NV) {
-    cxd s = {0, 0};
-    for (int w = 0; w < DY_WARPS; ++w) s = s + rs.wred[w * 8 + threadIdx.x];
-    rs.slot[phase * 8 + threadIdx.x] = s;
-  }
-  cl.sync();
-  if (threadIdx.x < NV) {
-    cxd s = {0, 0};
-    for (int r = 0; r < p; ++r) {
-      const cxd* rem = cl.map_shared_rank(rs.slot, r);
-      s = s + rem[phase * 8 + threadIdx.x];
-    }
-    rs.res[threadIdx.x] = s;
-  }
-  __syncthreads();
-#pragma unroll
-  for (int k = 0; k < NV; ++k) v[k] = rs.res[k];
-  phase ^= 1;
-}
-
-// CTA-local sum (no cluster exchange)
-template <int NV>
-__device__ void block_sum(RedSmem& rs, cxd (&v)[NV]) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
-  __syncthreads();
-  if (lane == 0) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) rs.wred[wid * 8 + k] = v[k];
-  }
-  __syncthreads();
-  if (threadIdx.x < NV) {
-    cxd s = {0, 0};
-    for (int w = 0; w < DY_WARPS; ++w) s = s + rs.wred[w * 8 + threadIdx.x];
-    rs.res[threadIdx.x] = s;
-  }
-  __syncthreads();
-#pragma unroll
-  for (int k = 0; k < NV; ++k) v[k] = rs.res[k];
-  __syncthreads();
-}
-
-// ---------------------------------------------------------------- async copies
-// g_s blocks stream from HBM into a ring of shared-memory slots with 1D bulk
-// copies (cp.async.bulk, completion counted on an mbarrier per slot).  Every
-// wait is bounded by the global timer: on time-out the kernel records
-// DYSON_ST_WAIT_TIMEOUT and goes on (no CTA may leave its cluster's barriers).
-constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;   // 2 s
-constexpr int ST_WAIT_TIMEOUT = 16;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void fence_mbar_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes) : "memory");
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}" : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const unsigned long long t0 = global_ns();
-  while (!mbar_try_wait(bar, parity))
-    if (global_ns() - t0 > WAIT_LIMIT_NS) return false;
-  return true;
-}
-
-// Per-CTA copy pipeline: S slots of one W x W block each, one mbarrier per slot.
-struct Pipe {
-  uint64_t* bar;   // [S] in static shared memory
-  void* ring;      // S slots in dynamic shared memory
-  void* ybuf;      // forward intermediates in shared memory, or null (global scratch)
-  int S;
-  int CR;          // rows of a slice block per streamed chunk (= W unless W > 64)
-  unsigned seq;    // blocks issued (= consumed) so far by this CTA
-  int* err;        // shared flag: a bounded wait ran out
-};
-
-constexpr int MAX_STAGES = 8;
-
-__device__ void pipe_init(Pipe& pp) {
-  if (threadIdx.x == 0) {
-    for (int k = 0; k < pp.S; ++k) mbar_init(pp.bar + k, 1);
-    *pp.err = 0;
-    fence_mbar_init();
-  }
-  __syncthreads();
-}
-
-// ---------------------------------------------------------------- block sweep
-// Solve B_i x = rhs by block forward/back substitution with the stored
-// left-connected inverses g_s (Eq. 7 and the S-products):
-//   forward  y_s = g_s (rhs_s - t y_{s-1})
-//   backward x_s = y_s - t g_s x_{s+1}
-// The right-hand side is either a full DD block (src) or boundary-only,
-// t times an interface-layer vector on the first/last slow rows (E y).
-// The 2 Lx - 1 blocks the two passes read stream through the copy ring.
-template <typename R>
-struct SweepArgs {
-  const cx<R>* g;      // [Lx][W][W] this subdomain's factors
-  cx<R>* y;            // [Lx][W] scratch for the forward intermediates
-  const cxd* src;      // full right-hand side (subdomain block) or null
-  const cx<R>* lay_lo; // interface layer below (i-1), boundary mode
-  const cx<R>* lay_hi; // interface layer above (i), boundary mode
-  cxd* dst;            // full solution out (subdomain block) or null
-  int dst_op;          // 0 store, 1 add, 2 subtract, 3 store negated
-  double in_scale;     // src is multiplied by this when rounded to R
-  double out_scale;    // x is multiplied by this when written to dst
-  cx<R>* bnd_lo;       // solution on the lowest slow row, layer layout (or null)
-  cx<R>* bnd_hi;       // solution on the highest slow row
-};
-
-// Thread layout of the block products y = g_s z (g_s complex symmetric, so its
-// row r is also its column r and rows are read contiguously): warp w owns rows
-// [w*RPW, (w+1)*RPW); inside the warp lane = rr*G + cg, row group rr, column
-// class cg (columns cg, cg+G, ...: CPG of them); the G partial sums of a row
-// are added with log2(G) butterfly shuffles and lane rr*G finishes the row.
-struct SweepLayout {
-  int RPW, G, CPG;
-};
-__host__ __device__ inline SweepLayout sweep_layout(int rows, int W) {
-  int rpw = (rows + DY_WARPS - 1) / DY_WARPS, p2 = 1;
-  while (p2 < rpw) p2 <<= 1;
-  SweepLayout L;
-  L.RPW = p2;
-  L.G = 32 / p2;
-  L.CPG = (W + L.G - 1) / L.G;
-  return L;
-}
-
-// The sequential slice loop touches only shared memory (or the per-unit
-// scratch) and R-precision registers: a parallel pre-pass converts the
-// right-hand side into the row buffer yb (rhs_s in row s), the forward pass
-// overwrites row s with y_s, the backward pass with x_s, and a parallel
-// post-pass converts the rows to FP64 and writes the requested outputs.  On
-// GB300 FP64 issue is ~1/64 of FP32, so keeping conversions out of the
-// dependent chain matters as much as keeping global loads out of it.
-template <typename R>
-__device__ void sweep_chunked(const Geo& g, int i, const SweepArgs<R>& a, cx<R>* sm, Pipe& pp,
-                              unsigned long long* cnt);
-
-// WD selects the row-chunked form at compile time, so the kernels for narrow
-// slices carry none of its code (or its registers).
-template <typename R, bool WD>
-__device__ void sweep(const Geo& g, int i, const SweepArgs<R>& a, cx<R>* sm, Pipe& pp,
-                      unsigned long long* cnt) {
-  if constexpr (WD) {
-    sweep_chunked<R>(g, i, a, sm, pp, cnt);
-    return;
-  }
-  const int W = g.W, Lx = g.Lx, T = g.T, w = T * g.h[i];
-  const SweepLayout L = sweep_layout(W, W);
-  cx<R>* zbuf = sm;                      // [2][W]: z of the current and of the next slice
-  cx<R>* ring = reinterpret_cast<cx<R>*>(pp.ring);
-  cx<R>* yb = pp.ybuf ? reinterpret_cast<cx<R>*>(pp.ybuf) : a.y;   // [Lx][W] row buffer
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int rr = lane / L.G, cg = lane - rr * L.G;
-  const int row = wid * L.RPW + rr;      // the row this lane works on
-  const bool rvalid = row < W;
-  const bool owner = rvalid && cg == 0;  // finishes the row
-  // rows of one warp are W entries apart, i.e. in the same banks; starting each
-  // row group at a different multiple of G spreads a warp's accesses over all banks
-  const int rot = (W % L.G == 0) ? (rr * L.G) % W : 0;
-  const R t = (R)g.t;
-  const int WW = W * W;
-  const uint32_t bytes = (uint32_t)(WW * sizeof(cx<R>));
-  const int NL = 2 * Lx - 1;
-  const int S = pp.S;
-  const int nrow = Lx * W;
-  auto slice_of = [&](int n) { return n < Lx ? n : 2 * Lx - 2 - n; };
-  auto issue = [&](int n) {
-    const unsigned q = pp.seq + n;
-    const int slot = (int)(q % S);
-    bulk_load(ring + (size_t)slot * WW, a.g + (size_t)slice_of(n) * WW, bytes, pp.bar + slot);
-  };
-
-  __syncthreads();                       // previous users of ring, zbuf and yb are done
-  if (tid == 0) {
-    fence_proxy_async();
-    for (int n = 0; n < S && n < NL; ++n) issue(n);
-  }
-  // ---- pre-pass: right-hand side rows in R precision
-  for (int e = tid; e < nrow; e += DY_THREADS) {
-    const int s = e / W, j = e - s * W;
-    cxd v = {0, 0};
-    if (j < w) {
-      if (a.src) {
-        v = a.in_scale * a.src[e];
-      } else {
-        cx<R> u = {0, 0};
-        if (a.lay_lo && j < T) u = u + t * a.lay_lo[s + Lx * j];
-        if (a.lay_hi && j >= w - T) u = u + t * a.lay_hi[s + Lx * (j - (w - T))];
-        yb[e] = u;
-        continue;
-      }
-    }
-    yb[e] = cconv<R>(v);
-  }
-  __syncthreads();
-  if (owner) zbuf[row] = yb[row];
-  // Rows are read two slices ahead into ping-pong registers: with yb in shared
-  // memory this costs nothing, with the global scratch it hides the latency.
-  cx<R> fA = {0, 0}, fB = {0, 0};
-  if (owner) {
-    if (Lx > 1) fA = yb[W + row];
-    if (Lx > 2) fB = yb[2 * W + row];
-  }
-  __syncthreads();
-
-  // one slice of either pass: wait for g_s, row products, butterfly
-  auto product = [&](int n) -> cx<R> {
-    const unsigned q = pp.seq + n;
-    const int slot = (int)(q % S);
-    if (!mbar_wait(pp.bar + slot, (q / S) & 1u)) *pp.err = 1;
-    const cx<R>* grow = ring + (size_t)slot * WW + (size_t)row * W;
-    const cx<R>* zc = zbuf + (n & 1) * W;
-    cx<R> acc = {0, 0};
-    if (rvalid) {
-#pragma unroll 4
-      for (int k = 0; k < L.CPG; ++k) {
-        const int base = cg + L.G * k;   // columns interleaved over the group's lanes
-        if (base < W) {
-          int col = base + rot;          // rotated per row group: no bank conflicts
-          if (col >= W) col -= W;
-          acc = cfma(grow[col], zc[col], acc);
-        }
-      }
-    }
-    for (int off = L.G >> 1; off > 0; off >>= 1) {
-      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
-      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
-    }
-    return acc;
-  };
-  auto finish = [&](int n) {
-    __syncthreads();                     // slot n and z of slice n fully read; z of n+1 written
-    if (tid == 0 && n + S < NL) {
-      fence_proxy_async();
-      issue(n + S);
-    }
-  };
-  // forward: y_s = g_s (rhs_s - t y_{s-1}); row s of yb becomes y_s
-  auto fwd = [&](int s, cx<R>& f) {
-    const cx<R> m = product(s);
-    if (owner) {
-      cx<R>* zn = zbuf + ((s + 1) & 1) * W;
-      yb[(size_t)s * W + row] = m;
-      zn[row] = (s + 1 < Lx) ? f - t * m : m;   // x_{Lx-1} = y_{Lx-1}
-      if (s + 3 < Lx) f = yb[(size_t)(s + 3) * W + row];
-    }
-    finish(s);
-  };
-  for (int s = 0; s < Lx; s += 2) {
-    fwd(s, fA);
-    if (s + 1 < Lx) fwd(s + 1, fB);
-  }
-  // backward: x_s = y_s - t g_s x_{s+1}; row s of yb becomes x_s
-  cx<R> yA = {0, 0}, yB = {0, 0};
-  if (owner && Lx > 1) {
-    yA = yb[(size_t)(Lx - 2) * W + row];
-    if (Lx > 2) yB = yb[(size_t)(Lx - 3) * W + row];
-  }
-  auto bwd = [&](int s, cx<R>& yv) {
-    const int n = 2 * Lx - 2 - s;
-    const cx<R> m = product(n);
-    if (owner) {
-      cx<R>* zn = zbuf + ((n + 1) & 1) * W;
-      const cx<R> xv = yv - t * m;
-      yb[(size_t)s * W + row] = xv;
-      zn[row] = xv;
-      if (s >= 2) yv = yb[(size_t)(s - 2) * W + row];
-    }
-    finish(n);
-  };
-  for (int s = Lx - 2; s >= 0; s -= 2) {
-    bwd(s, yA);
-    if (s - 1 >= 0) bwd(s - 1, yB);
-  }
-  // ---- post-pass: x rows to FP64 outputs
-  for (int e = tid; e < nrow; e += DY_THREADS) {
-    const int s = e / W, j = e - s * W;
-    if (j >= w) continue;
-    const cx<R> xr = yb[e];
-    if (a.dst) {
-      const cxd xd = a.out_scale * cconv<double>(xr);
-      cxd* d = a.dst + e;
-      if (a.dst_op == 0) *d = xd;
-      else if (a.dst_op == 1) *d = *d + xd;
-      else if (a.dst_op == 2) *d = *d - xd;
-      else *d = -xd;
-    }
-    if (a.bnd_lo && j < T) a.bnd_lo[s + Lx * j] = xr;
-    if (a.bnd_hi && j >= w - T) a.bnd_hi[s + Lx * (j - (w - T))] = xr;
-  }
-  pp.seq += NL;
-  if (tid == 0 && cnt) *cnt += 1;
-}
-
-// Wide slices (W > 64, 3D slabs): a slice block no longer fits a ring slot, so
-// it streams as NC = W / CR chunks of CR rows; each chunk's rows are finished
-// as soon as it arrives and its slot is released after a barrier.  The row
-// buffer yb is always on chip on this path.
-template <typename R>
-__device__ void sweep_chunked(const Geo& g, int i, const SweepArgs<R>& a, cx<R>* sm, Pipe& pp,
-                              unsigned long long* cnt) {
-  const int W = g.W, Lx = g.Lx, T = g.T, w = T * g.h[i];
-  const int CR = pp.CR, NC = W / CR;
-  const SweepLayout L = sweep_layout(CR, W);
-  cx<R>* zbuf = sm;
-  cx<R>* ring = reinterpret_cast<cx<R>*>(pp.ring);
-  cx<R>* yb = reinterpret_cast<cx<R>*>(pp.ybuf);
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int rr = lane / L.G, cg = lane - rr * L.G;
-  const int lrow = wid * L.RPW + rr;     // row inside a chunk
-  const bool rvalid = lrow < CR;
-  const bool owner = rvalid && cg == 0;
-  const int rot = (W % L.G == 0) ? (rr * L.G) % W : 0;
-  const R t = (R)g.t;
-  const int WW = W * W, CW = CR * W;
-  const uint32_t bytes = (uint32_t)(CW * sizeof(cx<R>));
-  const int NL = 2 * Lx - 1, NQ = NL * NC;
-  const int S = pp.S;
-  const int nrow = Lx * W;
-  auto slice_of = [&](int n) { return n < Lx ? n : 2 * Lx - 2 - n; };
-  auto issue = [&](int q) {
-    const unsigned qq = pp.seq + q;
-    const int slot = (int)(qq % S);
-    const int n = q / NC, c = q - n * NC;
-    bulk_load(ring + (size_t)slot * CW, a.g + (size_t)slice_of(n) * WW + (size_t)c * CW, bytes,
-              pp.bar + slot);
-  };
-
-  __syncthreads();
-  if (tid == 0) {
-    fence_proxy_async();
-    for (int q = 0; q < S && q < NQ; ++q) issue(q);
-  }
-  for (int e = tid; e < nrow; e += DY_THREADS) {
-    const int s = e / W, j = e - s * W;
-    cxd v = {0, 0};
-    if (j < w) {
-      if (a.src) {
-        v = a.in_scale * a.src[e];
-      } else {
-        cx<R> u = {0, 0};
-        if (a.lay_lo && j < T) u = u + t * a.lay_lo[s + Lx * j];
-        if (a.lay_hi && j >= w - T) u = u + t * a.lay_hi[s + Lx * (j - (w - T))];
-        yb[e] = u;
-        continue;
-      }
-    }
-    yb[e] = cconv<R>(v);
-  }
-  __syncthreads();
-  for (int e = tid; e < W; e += DY_THREADS) zbuf[e] = yb[e];
-  __syncthreads();
-  for (int n = 0; n < NL; ++n) {
-    const int s = slice_of(n);
-    const cx<R>* zc = zbuf + (n & 1) * W;
-    cx<R>* zn = zbuf + ((n + 1) & 1) * W;
-    for (int c = 0; c < NC; ++c) {
-      const int q = n * NC + c;
-      const unsigned qq = pp.seq + q;
-      const int slot = (int)(qq % S);
-      if (!mbar_wait(pp.bar + slot, (qq / S) & 1u)) *pp.err = 1;
-      const cx<R>* grow = ring + (size_t)slot * CW + (size_t)lrow * W;
-      cx<R> acc = {0, 0};
-      if (rvalid) {
-#pragma unroll 4
-        for (int k = 0; k < L.CPG; ++k) {
-          const int base = cg + L.G * k;
-          if (base < W) {
-            int col = base + rot;
-            if (col >= W) col -= W;
-            acc = cfma(grow[col], zc[col], acc);
-          }
-        }
-      }
-      for (int off = L.G >> 1; off > 0; off >>= 1) {
-        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
-        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
-      }
-      if (owner) {
-        const int row = c * CR + lrow;
-        if (n < Lx) {                    // forward: row s of yb becomes y_s
-          yb[(size_t)s * W + row] = acc;
-          zn[row] = (s + 1 < Lx) ? yb[(size_t)(s + 1) * W + row] - t * acc : acc;
-        } else {                         // backward: row s of yb becomes x_s
-          const cx<R> xv = yb[(size_t)s * W + row] - t * acc;
-          yb[(size_t)s * W + row] = xv;
-          zn[row] = xv;
-        }
-      }
-      __syncthreads();                   // chunk slot released; rows of z for n+1 written
-      if (tid == 0 && q + S < NQ) {
-        fence_proxy_async();
-        issue(q + S);
-      }
-    }
-  }
-  for (int e = tid; e < nrow; e += DY_THREADS) {
-    const int s = e / W, j = e - s * W;
-    if (j >= w) continue;
-    const cx<R> xr = yb[e];
-    if (a.dst) {
-      const cxd xd = a.out_scale * cconv<double>(xr);
-      cxd* d = a.dst + e;
-      if (a.dst_op == 0) *d = xd;
-      else if (a.dst_op == 1) *d = *d + xd;
-      else if (a.dst_op == 2) *d = *d - xd;
-      else *d = -xd;
-    }
-    if (a.bnd_lo && j < T) a.bnd_lo[s + Lx * j] = xr;
-    if (a.bnd_hi && j >= w - T) a.bnd_hi[s + Lx * (j - (w - T))] = xr;
-  }
-  pp.seq += NQ;
-  if (tid == 0 && cnt) *cnt += 1;
-}
-
-template <typename R>
-__device__ __forceinline__ SweepArgs<R> sweep_base(const Geo& g, const Bufs& b, int kf, int i) {
-  SweepArgs<R> a;
-  const size_t nsub = (size_t)g.Lx * g.W;
-  a.g = reinterpret_cast<const cx<R>*>(b.g) + ((size_t)kf * g.p + i) * nsub * g.W;
-  a.y = reinterpret_cast<cx<R>*>(b.yscr) + ((size_t)kf * g.p + i) * nsub;
-  a.src = nullptr;
-  a.lay_lo = a.lay_hi = nullptr;
-  a.dst = nullptr;
-  a.dst_op = 0;
-  a.in_scale = a.out_scale = 1.0;
-  a.bnd_lo = a.bnd_hi = nullptr;
-  return a;
-}
-
-__device__ __forceinline__ unsigned long long* sweep_cnt(const Geo& g, const Bufs& b, int kf, int i) {
-  return b.sweeps ? b.sweeps + (size_t)kf * g.p + i : nullptr;
-}
-// boundary-row values and interface vectors are kept in the sweep precision R
-// (their buffers are sized for complex128, so either precision fits)
-template <typename R>
-__device__ __forceinline__ cx<R>* bnd_ptr(const Geo& g, const Bufs& b, int kf, int i, int hi) {
-  return reinterpret_cast<cx<R>*>(b.bnd) + (((size_t)kf * g.p + i) * 2 + hi) * g.A;
-}
-template <typename R>
-__device__ __forceinline__ cx<R>* ifv_ptr(const Geo& g, const Bufs& b, int kf, int slot) {
-  return reinterpret_cast<cx<R>*>(b.ifv) + ((size_t)kf * IF_N + slot) * nifc(g);
-}
-
-// ---------------------------------------------------------------- interface pieces
-template <typename R>
-__device__ __forceinline__ cx<R> shfl_up_c(cx<R> v, int d) {
-  return {__shfl_up_sync(0xffffffffu, v.x, d), __shfl_up_sync(0xffffffffu, v.y, d)};
-}
-template <typename R>
-__device__ __forceinline__ cx<R> shfl_down_c(cx<R> v, int d) {
-  return {__shfl_down_sync(0xffffffffu, v.x, d), __shfl_down_sync(0xffffffffu, v.y, d)};
-}
-
-// Apply the tridiagonal preconditioner along the x lines of layer i: z = M^-1 r.
-// Thomas substitution written as compositions of affine maps, one warp per
-// line, 128 sites (4 per lane) per pass with the boundary value carried from
-// pass to pass: forward d'_x = a_x d'_{x-1} + b_x (a_x = -t inv_x,
-// b_x = r_x inv_x), stored in z; backward z_x = -c'_x z_{x+1} + d'_x.  Each
-// lane composes the maps of its 4 sites, a 5-step warp scan composes across
-// lanes, then the lanes finish their sites: ~9 dependent steps per 128 sites.
-//
-// r is the COCG residual, rewritten in this kernel between calls: it must be
-// read through the coherent path, never as const __restrict__ (which lets the
-// compiler use non-coherent loads whose cached lines can be stale by the next
-// iteration).  The preconditioner factors are read-only for the kernel's life.
-template <typename R>
-__device__ void precond_apply(const Geo& g, const Bufs& b, int kf, int i, const cx<R>* r, cx<R>* z) {
-  constexpr int E = 4, CH = 32 * E;
-  const int Lx = g.Lx, A = g.A;
-  const cx<R>* __restrict__ pre = reinterpret_cast<const cx<R>*>(b.pre) + ((size_t)kf * nifc(g) + (size_t)i * A) * 2;
-  const R t = (R)g.t;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int tr = wid; tr < g.T; tr += DY_WARPS) {
-    const int o = Lx * tr;
-    cx<R> carry = {0, 0};                  // d'_{c0-1}
-    for (int c0 = 0; c0 < Lx; c0 += CH) {
-      const int x0 = c0 + lane * E;
-      cx<R> av[E], bv[E];
-      cx<R> FA = {1, 0}, FB = {0, 0};
-#pragma unroll
-      for (int k = 0; k < E; ++k) {
-        av[k] = cx<R>{1, 0};
-        bv[k] = cx<R>{0, 0};
-        if (x0 + k < Lx) {
-          const cx<R> inv = pre[o + x0 + k];
-          av[k] = (x0 + k == 0) ? cx<R>{0, 0} : (-t) * inv;
-          bv[k] = r[o + x0 + k] * inv;
-        }
-        FB = av[k] * FB + bv[k];
-        FA = av[k] * FA;
-      }
-#pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {   // inclusive scan: F_l o F_{l-d}
-        const cx<R> pa = shfl_up_c(FA, d), pb = shfl_up_c(FB, d);
-        if (lane >= d) {
-          FB = FA * pb + FB;
-          FA = FA * pa;
-        }
-      }
-      cx<R> v = shfl_up_c(FA * carry + FB, 1);   // d' before this lane's sites
-      if (lane == 0) v = carry;
-      else {
-        // shfl_up_c moved F_{l-1}(carry) of the previous lane
-      }
-#pragma unroll
-      for (int k = 0; k < E; ++k) {
-        v = av[k] * v + bv[k];
-        if (x0 + k < Lx) z[o + x0 + k] = v;
-      }
-      carry = cx<R>{__shfl_sync(0xffffffffu, v.x, 31), __shfl_sync(0xffffffffu, v.y, 31)};
-    }
-    __syncwarp();
-    cx<R> cz = {0, 0};                     // z_{c1+1}
-    const int nch = (Lx + CH - 1) / CH;
-    for (int c = nch - 1; c >= 0; --c) {
-      const int x0 = c * CH + lane * E;
-      cx<R> av[E], dv[E];
-      cx<R> HA = {1, 0}, HB = {0, 0};
-#pragma unroll
-      for (int k = E - 1; k >= 0; --k) {
-        const int x = x0 + k;
-        av[k] = cx<R>{1, 0};
-        dv[k] = cx<R>{0, 0};
-        if (x < Lx) {
-          av[k] = (x == Lx - 1) ? cx<R>{0, 0} : -pre[A + o + x];
-          dv[k] = z[o + x];
-        }
-        HB = av[k] * HB + dv[k];
-        HA = av[k] * HA;
-      }
-#pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {   // inclusive suffix scan: H_l o H_{l+d}
-        const cx<R> na = shfl_down_c(HA, d), nb = shfl_down_c(HB, d);
-        if (lane + d < 32) {
-          HB = HA * nb + HB;
-          HA = HA * na;
-        }
-      }
-      cx<R> v = shfl_down_c(HA * cz + HB, 1);     // z after this lane's sites
-      if (lane == 31) v = cz;
-#pragma unroll
-      for (int k = E - 1; k >= 0; --k) {
-        v = av[k] * v + dv[k];
-        if (x0 + k < Lx) z[o + x0 + k] = v;
-      }
-      cz = cx<R>{__shfl_sync(0xffffffffu, v.x, 0), __shfl_sync(0xffffffffu, v.y, 0)};
-    }
-  }
-}
-
-// (C p)[a] on layer l: the Dyson matrix restricted to the interface layer,
-// with its diagonal d_C precomputed in R precision.
-template <typename R>
-__device__ __forceinline__ cx<R> layer_C_apply(const Geo& g, const cx<R>* dC, const cx<R>* pv, int a) {
-  const int Lx = g.Lx, x = a % Lx, tr = a / Lx;
-  cx<R> nb = {0, 0};
-  if (x > 0) nb = nb + pv[a - 1];
-  if (x < Lx - 1) nb = nb + pv[a + 1];
-  if (tr > 0) nb = nb + pv[a - Lx];
-  if (tr < g.T - 1) nb = nb + pv[a + Lx];
-  return dC[a] * pv[a] + (R)g.t * nb;
-}
-
-// ---------------------------------------------------------------- reductions in R
-template <typename R>
-__device__ __forceinline__ cx<R> warp_sum_r(cx<R> v) {
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    v.x += __shfl_xor_sync(0xffffffffu, v.x, off);
-    v.y += __shfl_xor_sync(0xffffffffu, v.y, off);
-  }
-  return v;
-}
-// Cluster-wide sums in R precision (partials exchanged through the same
-// shared slots as cluster_sum, widened to double there).
-template <typename R, int NV>
-__device__ void cluster_sum_r(cg::cluster_group& cl, RedSmem& rs, int& phase, int p, cx<R> (&v)[NV]) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < NV; ++k) v[k] = warp_sum_r(v[k]);
-  if (lane == 0) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) rs.wred[wid * 8 + k] = cconv<double>(v[k]);
-  }
-  __syncthreads();
-  if (threadIdx.x < NV) {
-    cxd s = {0, 0};
-    for (int w = 0; w < DY_WARPS; ++w) s = s + rs.wred[w * 8 + threadIdx.x];
-    rs.slot[phase * 8 + threadIdx.x] = s;
-  }
-  cl.sync();
-  if (threadIdx.x < NV) {
-    cxd s = {0, 0};
-    for (int r = 0; r < p; ++r) {
-      const cxd* rem = cl.map_shared_rank(rs.slot, r);
-      s = s + rem[phase * 8 + threadIdx.x];
-    }
-    rs.res[threadIdx.x] = s;
-  }
-  __syncthreads();
-#pragma unroll
-  for (int k = 0; k < NV; ++k) v[k] = cconv<R>(rs.res[k]);
-  phase ^= 1;
-}
-
-// COCG for S y = b on the interface (S = C - E^T B^-1 E never formed), all in
-// precision R: the FP64 form solves to krylov_tol in FP64; the mixed form's
-// inner solves (refined in FP64 one level up) run entirely in complex64.
-// Right-hand side in IF_B, solution in IF_X.  Returns the iteration count;
-// *conv is set to 0 if the cap was hit.
-template <typename R, bool WD>
-__device__ int schur_cocg(cg::cluster_group& cl, RedSmem& rs, int& phase, const Geo& g,
-                          const Bufs& b, int kf, int i, double tol, cx<R>* sm, Pipe& pp,
-                          int* conv) {
-  using C = cx<R>;
-  const int p = g.p, A = g.A;
-  const bool has = i < p - 1;
-  C* X = ifv_ptr<R>(g, b, kf, IF_X);
-  C* Rv = ifv_ptr<R>(g, b, kf, IF_R);
-  C* Z = ifv_ptr<R>(g, b, kf, IF_Z);
-  C* P = ifv_ptr<R>(g, b, kf, IF_P);
-  C* SP = ifv_ptr<R>(g, b, kf, IF_SP);
-  const C* Bv = ifv_ptr<R>(g, b, kf, IF_B);
-  const C* dC = ifv_ptr<R>(g, b, kf, IF_D) + (size_t)i * A;
-  const size_t o = (size_t)i * A;
-  const C* bl_i = bnd_ptr<R>(g, b, kf, i, 1);
-  const C* bl_n = has ? bnd_ptr<R>(g, b, kf, i + 1, 0) : nullptr;
-  const R tr = (R)g.t;
-
-  if (has) {
-    for (int a = threadIdx.x; a < A; a += DY_THREADS) {
-      X[o + a] = C{0, 0};
-      Rv[o + a] = Bv[o + a];
-    }
-  }
-  __syncthreads();
-  if (has) precond_apply<R>(g, b, kf, i, Rv + o, Z + o);
-  __syncthreads();
-  C v2[2] = {{0, 0}, {0, 0}};
-  if (has) {
-    for (int a = threadIdx.x; a < A; a += DY_THREADS) {
-      C zz = Z[o + a], r = Rv[o + a];
-      P[o + a] = zz;
-      v2[0] = cfma(r, zz, v2[0]);
-      v2[1].x += cabs2(r);
-    }
-  }
-  cluster_sum_r<R, 2>(cl, rs, phase, p, v2);
-  C rho = v2[0];
-  const R bn = v2[1].x;
-  *conv = 1;
-  if (bn == (R)0) return 0;
-  SweepArgs<R> sa = sweep_base<R>(g, b, kf, i);
-  sa.lay_lo = (i > 0) ? P + (size_t)(i - 1) * A : nullptr;
-  sa.lay_hi = has ? P + o : nullptr;
-  sa.bnd_lo = bnd_ptr<R>(g, b, kf, i, 0);
-  sa.bnd_hi = bnd_ptr<R>(g, b, kf, i, 1);
-  const R tol2 = (R)(tol * tol);
-  int it = 0;
-  for (;;) {
-    if (it >= g.krylov_maxit) {
-      *conv = 0;
-      break;
-    }
-    ++it;
-    cl.sync();                                  // P of both neighbour layers is final
-    sweep<R, WD>(g, i, sa, sm, pp, sweep_cnt(g, b, kf, i));   // B^-1 E p on this subdomain
-    cl.sync();                                  // boundary values of every subdomain written
-    C v1[1] = {{0, 0}};
-    if (has) {
-      for (int a = threadIdx.x; a < A; a += DY_THREADS) {
-        C sp = layer_C_apply<R>(g, dC, P + o, a) - tr * (bl_i[a] + bl_n[a]);
-        SP[o + a] = sp;
-        v1[0] = cfma(P[o + a], sp, v1[0]);
-      }
-    }
-    cluster_sum_r<R, 1>(cl, rs, phase, p, v1);
-    const C alpha = cdiv(rho, v1[0]);
-    if (has) {
-      for (int a = threadIdx.x; a < A; a += DY_THREADS) {
-        X[o + a] = X[o + a] + alpha * P[o + a];
-        Rv[o + a] = Rv[o + a] - alpha * SP[o + a];
-      }
-    }
-    __syncthreads();
-    if (has) precond_apply<R>(g, b, kf, i, Rv + o, Z + o);
-    __syncthreads();
-    v2[0] = v2[1] = C{0, 0};
-    if (has) {
-      for (int a = threadIdx.x; a < A; a += DY_THREADS) {
-        C zz = Z[o + a], r = Rv[o + a];
-        v2[0] = cfma(r, zz, v2[0]);
-        v2[1].x += cabs2(r);
-      }
-    }
-    cluster_sum_r<R, 2>(cl, rs, phase, p, v2);
-    if (v2[1].x <= tol2 * bn) break;
-    const C beta = cdiv(v2[0], rho);
-    rho = v2[0];
-    if (has) {
-      for (int a = threadIdx.x; a < A; a += DY_THREADS) P[o + a] = Z[o + a] + beta * P[o + a];
-    }
-  }
-  return it;
-}
-
-// Layer diagonal d_C = i w + mu - V - Sigma on this CTA's interface layer, in
-// precision R, computed once per launch for the interface products.
-template <typename R>
-__device__ void layer_diag(const Geo& g, const Bufs& b, int kf, int i) {
-  if (i >= g.p - 1) return;
-  cx<R>* dC = ifv_ptr<R>(g, b, kf, IF_D) + (size_t)i * g.A;
-  for (int a = threadIdx.x; a < g.A; a += DY_THREADS)
-    dC[a] = cconv<R>(dyson_diag(g, b, kf, a + g.A * g.ylayer[i]));
-}
-
-// res = rhs - H x (mode 0: full H; mode 1: B only, no interface coupling),
-// FP64, on this CTA's entries.  Returns partials (||res||^2, ||rhs||^2).
-__device__ void residual_H(const Geo& g, const Bufs& b, int kf, int i, const cxd* rhs,
-                           const cxd* x, cxd* res, int mode, double* rn, double* qn) {
-  const int W = g.W, Lx = g.Lx, T = g.T, h = g.h[i], w = T * h, A = g.A;
-  const size_t nsub = (size_t)Lx * W;
-  const cxd* xs = x + i * nsub;
-  const double t = g.t;
-  double sr = 0, sq = 0;
-  for (int e = threadIdx.x; e < (int)nsub; e += DY_THREADS) {
-    const int s = e / W, j = e - s * W;
-    if (j >= w) continue;
-    const int tr = j % T, sl = j / T;
-    cxd d = dyson_diag(g, b, kf, sub_nat(g, i, s, j));
-    cxd nb = {0, 0};
-    if (s > 0) nb = nb + xs[e - W];
-    if (s < Lx - 1) nb = nb + xs[e + W];
-    if (tr > 0) nb = nb + xs[e - 1];
-    if (tr < T - 1) nb = nb + xs[e + 1];
-    if (sl > 0) nb = nb + xs[e - T];
-    if (sl < h - 1) nb = nb + xs[e + T];
-    if (mode == 0) {
-      if (sl == 0 && i > 0) nb = nb + x[g.ifc_off + (size_t)(i - 1) * A + s + Lx * tr];
-      if (sl == h - 1 && i < g.p - 1) nb = nb + x[g.ifc_off + (size_t)i * A + s + Lx * tr];
-    }
-    cxd hv = d * xs[e] + t * nb;
-    cxd q = rhs[i * nsub + e];
-    cxd rr = q - hv;
-    res[i * nsub + e] = rr;
-    sr += cabs2(rr);
-    sq += cabs2(q);
-  }
-  if (mode == 0 && i < g.p - 1) {
-    const size_t o = g.ifc_off + (size_t)i * A;
-    const cxd* xl = x + o;
-    const cxd* xb = x + i * nsub;           // subdomain i: its top row touches layer i
-    const cxd* xa = x + (i + 1) * nsub;     // subdomain i+1: its bottom row touches layer i
-    const int hi = T * (g.h[i] - 1);
-    for (int a = threadIdx.x; a < A; a += DY_THREADS) {
-      const int xx = a % Lx, tr = a / Lx;
-      cxd nb = {0, 0};
-      if (xx > 0) nb = nb + xl[a - 1];
-      if (xx < Lx - 1) nb = nb + xl[a + 1];
-      if (tr > 0) nb = nb + xl[a - Lx];
-      if (tr < T - 1) nb = nb + xl[a + Lx];
-      cxd hv = dyson_diag(g, b, kf, a + A * g.ylayer[i]) * xl[a] + t * nb;
-      hv = hv + t * (xb[(size_t)xx * W + hi + tr] + xa[(size_t)xx * W + tr]);
-      cxd q = rhs[o + a];
-      cxd rr = q - hv;
-      res[o + a] = rr;
-      sr += cabs2(rr);
-      sq += cabs2(q);
-    }
-  }
-  *rn = sr;
-  *qn = sq;
-}
-
-// x = H^-1 rhs by elimination of the subdomain unknowns, sweeps and the
-// interface solve in precision R:
-//   z = B^-1 rhs_B;  y = S^-1 (rhs_C - E^T z);  x_B = z - B^-1 E y;  x_C = y.
-// zero_B: rhs_B = 0 is known, so z = 0 and its sweep is skipped.
-// sc: the solve runs on rhs / sc and its result is scaled back by sc, so the
-// R-precision recurrences work on O(1) numbers (the squared norms of the
-// shrinking refinement residuals would leave float range otherwise).
-template <typename R, bool WD>
-__device__ int solve_H(cg::cluster_group& cl, RedSmem& rs, int& phase, const Geo& g,
-                       const Bufs& b, int kf, int i, const cxd* rhs, cxd* xout, bool zero_B,
-                       double sc, double tol, cx<R>* sm, Pipe& pp, int* conv) {
-  const int A = g.A;
-  const bool has = i < g.p - 1;
-  const size_t nsub = (size_t)g.Lx * g.W;
-  cx<R>* Bv = ifv_ptr<R>(g, b, kf, IF_B);
-  const cxd* rc = rhs + g.ifc_off + (size_t)i * A;
-  const R tr = (R)g.t;
-  const double isc = 1.0 / sc;
-  if (!zero_B) {
-    SweepArgs<R> sa = sweep_base<R>(g, b, kf, i);
-    sa.src = rhs + i * nsub;
-    sa.in_scale = isc;
-    sa.dst = xout + i * nsub;
-    sa.out_scale = sc;
-    sa.dst_op = 0;
-    sa.bnd_lo = bnd_ptr<R>(g, b, kf, i, 0);
-    sa.bnd_hi = bnd_ptr<R>(g, b, kf, i, 1);
-    sweep<R, WD>(g, i, sa, sm, pp, sweep_cnt(g, b, kf, i));
-    cl.sync();
-    if (has) {
-      const cx<R>* bl_i = bnd_ptr<R>(g, b, kf, i, 1);
-      const cx<R>* bl_n = bnd_ptr<R>(g, b, kf, i + 1, 0);
-      for (int a = threadIdx.x; a < A; a += DY_THREADS)
-        Bv[(size_t)i * A + a] = cconv<R>(isc * rc[a]) - tr * (bl_i[a] + bl_n[a]);
-    }
-  } else if (has) {
-    for (int a = threadIdx.x; a < A; a += DY_THREADS) Bv[(size_t)i * A + a] = cconv<R>(isc * rc[a]);
-  }
-  __syncthreads();
-  int it = schur_cocg<R, WD>(cl, rs, phase, g, b, kf, i, tol, sm, pp, conv);
-  cl.sync();
-  const cx<R>* X = ifv_ptr<R>(g, b, kf, IF_X);
-  SweepArgs<R> sb = sweep_base<R>(g, b, kf, i);
-  sb.lay_lo = (i > 0) ? X + (size_t)(i - 1) * A : nullptr;
-  sb.lay_hi = has ? X + (size_t)i * A : nullptr;
-  sb.dst = xout + i * nsub;
-  sb.out_scale = sc;
-  sb.dst_op = zero_B ? 3 : 2;
-  sweep<R, WD>(g, i, sb, sm, pp, sweep_cnt(g, b, kf, i));
-  if (has) {
-    cxd* xc = xout + g.ifc_off + (size_t)i * A;
-    for (int a = threadIdx.x; a < A; a += DY_THREADS) xc[a] = sc * cconv<double>(X[(size_t)i * A + a]);
-  }
-  return it;
-}
-
-constexpr size_t YBUF_MAX = 64 * 1024;   // forward intermediates kept on chip up to this size
-
-// Shared-memory plan of a sweep: ring of S slots of CR x W entries (CR = W when
-// a whole slice block fits a slot, the W <= 64 strips; row chunks otherwise),
-// two z vectors, and the on-chip row buffer when it fits.
-struct RingPlan {
-  int CR, S;
-  size_t ybuf, smem;
-};
-template <typename R>
-__host__ __device__ inline RingPlan ring_plan(int W, int Lx) {
-  RingPlan rp;
-  const size_t cs = sizeof(cx<R>);
-  const size_t yb = (size_t)Lx * W * cs;
-  if (W <= DY_MAXW_SMEM) {
-    rp.ybuf = yb <= YBUF_MAX ? yb : 0;
-    rp.CR = W;
-    long S = ((long)100 * 1024 - (long)rp.ybuf) / (long)(W * W * cs);   // two CTAs per SM
-    rp.S = (int)(S > MAX_STAGES ? MAX_STAGES : (S < 2 ? 2 : S));
-  } else {
-    rp.ybuf = yb;                                                       // one CTA per SM
-    const long budget = (long)200 * 1024 - (long)yb - (long)(2 * W * cs);
-    // largest divisor of W whose chunks leave >= 4 ring slots (>= 2 as a last
-    // resort); a chunk row is W entries, a multiple of 32 bytes, so any row count
-    // keeps the bulk copies 16-byte aligned
-    rp.CR = 0;
-    rp.S = 0;
-    for (int want = 4; want >= 2 && !rp.CR; want -= 2)
-      for (int cr = W; cr >= 1; --cr) {
-        if (W % cr) continue;
-        const long S = budget / (long)((size_t)cr * W * cs);
-        if (S >= want) {
-          rp.CR = cr;
-          rp.S = (int)(S > MAX_STAGES ? MAX_STAGES : S);
-          break;
-        }
-      }
-  }
-  rp.smem = rp.CR ? (size_t)rp.S * rp.CR * W * cs + (size_t)2 * W * cs + rp.ybuf : 0;
-  return rp;
-}
-template <typename R>
-__host__ __device__ inline size_t ybuf_bytes(int W, int Lx) { return ring_plan<R>(W, Lx).ybuf; }
-template <typename R>
-__host__ __device__ inline int ring_stages(int W, int Lx) { return ring_plan<R>(W, Lx).S; }
-template <typename R>
-__host__ __device__ inline size_t solver_smem(int W, int Lx) { return ring_plan<R>(W, Lx).smem; }
-
-// ---------------------------------------------------------------- kernels
-// u = X q_j  (Sec. 2.3 Eqs. 6-8), with u = v - w computed as the solution of
-// H u = q - H w = [0; q_C - E^T w_B]  (w = blkdiag(B^-1, 0) q, so B w_B = q_B),
-// i.e. y = S^-1 (E^T w_B - q_C), u_B = B^-1 E y, u_C = -y: no cancellation.
-//   mixed = 0: every sweep in R (= double), the interface solve to krylov_tol.
-//   mixed = 1: sweeps in complex64 (R = float).  w_B is refined against FP64
-//              residuals of B, u against FP64 residuals of H, each until the
-//              relative residual is below refine_tol.
-template <typename R, bool WD>
-__global__ void __launch_bounds__(DY_THREADS, 2) k_xmatvec(Geo g, Bufs b, int j, int mixed) {
-  cg::cluster_group cl = cg::this_cluster();
-  __shared__ RedSmem rs;
-  __shared__ __align__(8) uint64_t bars[MAX_STAGES];
-  __shared__ int err;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  const int i = blockIdx.x, kf = blockIdx.y, p = g.p, A = g.A;
-  int* st = b.st + (size_t)kf * ST_N;
-  if (st[ST_DONE]) return;                 // same value in every CTA of the cluster
-  Pipe pp;
-  pp.bar = bars;
-  const RingPlan rp = ring_plan<R>(g.W, g.Lx);
-  pp.S = rp.S;
-  pp.CR = rp.CR;
-  pp.ring = smem_raw;
-  pp.seq = 0;
-  pp.err = &err;
-  pipe_init(pp);
-  cx<R>* sm = reinterpret_cast<cx<R>*>(smem_raw + (size_t)rp.S * rp.CR * g.W * sizeof(cx<R>));
-  pp.ybuf = rp.ybuf ? (void*)(sm + 2 * g.W) : nullptr;
-  layer_diag<R>(g, b, kf, i);
-  int phase = 0;
-  const bool has = i < p - 1;
-  const size_t Ndd = g.Ndd, nsub = (size_t)g.Lx * g.W;
-  const cxd* q = b.Q + ((size_t)kf * (g.k_max + 1) + j) * Ndd;
-  cxd* u = b.u + (size_t)kf * Ndd;
-  int iters = 0, solves = 0, refines = 0, conv_all = 1, conv = 1;
-
-  if (!mixed) {
-    // w = B^-1 q_B, only its boundary rows are needed: E^T w
-    SweepArgs<R> sa = sweep_base<R>(g, b, kf, i);
-    sa.src = q + i * nsub;
-    sa.bnd_lo = bnd_ptr<R>(g, b, kf, i, 0);
-    sa.bnd_hi = bnd_ptr<R>(g, b, kf, i, 1);
-    sweep<R, WD>(g, i, sa, sm, pp, sweep_cnt(g, b, kf, i));
-    cl.sync();
-    cx<R>* Bv = ifv_ptr<R>(g, b, kf, IF_B);
-    if (has) {
-      const cx<R>* bl_i = bnd_ptr<R>(g, b, kf, i, 1);
-      const cx<R>* bl_n = bnd_ptr<R>(g, b, kf, i + 1, 0);
-      const cxd* qc = q + g.ifc_off + (size_t)i * A;
-      for (int a = threadIdx.x; a < A; a += DY_THREADS)
-        Bv[(size_t)i * A + a] = (R)g.t * (bl_i[a] + bl_n[a]) - cconv<R>(qc[a]);
-    }
-    __syncthreads();
-    iters += schur_cocg<R, WD>(cl, rs, phase, g, b, kf, i, g.krylov_tol, sm, pp, &conv);
-    conv_all &= conv;
-    solves = 1;
-    cl.sync();
-    const cx<R>* X = ifv_ptr<R>(g, b, kf, IF_X);
-    SweepArgs<R> sb = sweep_base<R>(g, b, kf, i);
-    sb.lay_lo = (i > 0) ? X + (size_t)(i - 1) * A : nullptr;
-    sb.lay_hi = has ? X + (size_t)i * A : nullptr;
-    sb.dst = u + i * nsub;
-    sb.dst_op = 0;
-    sweep<R, WD>(g, i, sb, sm, pp, sweep_cnt(g, b, kf, i));
-    if (has) {
-      cxd* uc = u + g.ifc_off + (size_t)i * A;
-      for (int a = threadIdx.x; a < A; a += DY_THREADS) uc[a] = -cconv<double>(X[(size_t)i * A + a]);
-    }
-  } else {
-    cxd* wv = b.v1 + (size_t)kf * Ndd;   // w_B, later the refinement corrections
-    cxd* rv = b.v2 + (size_t)kf * Ndd;   // FP64 residuals
-    cxd* hr = b.v3 + (size_t)kf * Ndd;   // right-hand side [0; q_C - E^T w_B]
-    // ---- w_B = B^-1 q_B, refined against FP64 residuals of B (subdomain-local)
-    {
-      SweepArgs<R> sa = sweep_base<R>(g, b, kf, i);
-      sa.src = q + i * nsub;
-      sa.dst = wv + i * nsub;
-      sa.dst_op = 0;
-      sweep<R, WD>(g, i, sa, sm, pp, sweep_cnt(g, b, kf, i));
-      for (int r = 0; r < g.refine_max; ++r) {
-        __syncthreads();
-        double rn, qn;
-        residual_H(g, b, kf, i, q, wv, rv, 1, &rn, &qn);
-        cxd v2[2] = {{rn, 0}, {qn, 0}};
-        block_sum<2>(rs, v2);
-        if (v2[0].x <= g.refine_tol * g.refine_tol * v2[1].x) break;
-        SweepArgs<R> sc = sweep_base<R>(g, b, kf, i);
-        sc.src = rv + i * nsub;
-        sc.dst = wv + i * nsub;
-        sc.dst_op = 1;
-        sweep<R, WD>(g, i, sc, sm, pp, sweep_cnt(g, b, kf, i));
-      }
-    }
-    cl.sync();                             // w_B of the neighbour subdomains is final
-    {
-      const int n = own_count(g, i);
-      const int hi = g.T * (g.h[i] - 1);
-      for (int e = threadIdx.x; e < n; e += DY_THREADS) {
-        size_t k = own_idx(g, i, e, (int)nsub);
-        cxd v = {0, 0};
-        if (e >= (int)nsub) {
-          const int a = e - (int)nsub, xx = a % g.Lx, tr = a / g.Lx;
-          const cxd ew = wv[i * nsub + (size_t)xx * g.W + hi + tr] +
-                         wv[(i + 1) * nsub + (size_t)xx * g.W + tr];
-          v = q[k] - g.t * ew;
-        }
-        hr[k] = v;
-      }
-    }
-    __syncthreads();                       // interface entries of hr are written by other threads
-    double hn;
-    {
-      cxd v1[1] = {{0, 0}};
-      if (has)
-        for (int a = threadIdx.x; a < A; a += DY_THREADS)
-          v1[0].x += cabs2(hr[g.ifc_off + (size_t)i * A + a]);
-      cluster_sum<1>(cl, rs, phase, p, v1);   // also: every CTA has read w_B before it is reused
-      hn = sqrt(v1[0].x);
-    }
-    if (hn > 0.0) {
-      iters += solve_H<R, WD>(cl, rs, phase, g, b, kf, i, hr, u, true, hn, g.krylov_tol, sm, pp, &conv);
-      conv_all &= conv;
-      ++solves;
-    } else {
-      const int n = own_count(g, i);
-      for (int e = threadIdx.x; e < n; e += DY_THREADS) u[own_idx(g, i, e, (int)nsub)] = cxd{0, 0};
-    }
-    for (int r = 0; r < g.refine_max && hn > 0.0; ++r) {
-      cl.sync();
-      double rn, qn;
-      residual_H(g, b, kf, i, hr, u, rv, 0, &rn, &qn);
-      cxd v2[2] = {{rn, 0}, {qn, 0}};
-      cluster_sum<2>(cl, rs, phase, p, v2);
-      if (v2[0].x <= g.refine_tol * g.refine_tol * v2[1].x) break;
-      ++refines;
-      iters += solve_H<R, WD>(cl, rs, phase, g, b, kf, i, rv, wv, false, sqrt(v2[0].x), g.krylov_tol, sm,
-                          pp, &conv);
-      conv_all &= conv;
-      ++solves;
-      __syncthreads();
-      const int n = own_count(g, i);
-      for (int e = threadIdx.x; e < n; e += DY_THREADS) {
-        size_t k = own_idx(g, i, e, (int)nsub);
-        u[k] = u[k] + wv[k];
-      }
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x == 0 && err) atomicOr(st + ST_STATUS, ST_WAIT_TIMEOUT);
-  if (i == 0 && threadIdx.x == 0) {
-    st[ST_ITERS] += iters;
-    st[ST_SOLVES] += solves;
-    st[ST_REFINE] += refines;
-    if (!conv_all) st[ST_STATUS] |= 4;
-  }
-  cl.sync();          // no CTA exits while a peer may still read its shared memory
-}
 
 // One step of complex-symmetric Lanczos on X with the bilinear form
 // (Sec. 2.1, Freund et al.), full CGS2 re-orthogonalisation in the same form,
@@ -1310,80 +184,13 @@ __global__ void k_status(const int* st, int K, int* status) {
     status[k] = st[(size_t)k * ST_N + ST_STATUS];
 }
 
-// w = blkdiag(B^-1, 0) q for DD-layout vectors (Eq. 7), one CTA per subdomain.
-template <typename R, bool WD>
-__global__ void __launch_bounds__(DY_THREADS, 2) k_bsolve(Geo g, Bufs b, const cxd* q, cxd* w) {
-  __shared__ __align__(8) uint64_t bars[MAX_STAGES];
-  __shared__ int err;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  const int i = blockIdx.x, kf = blockIdx.y;
-  const size_t nsub = (size_t)g.Lx * g.W;
-  Pipe pp;
-  pp.bar = bars;
-  const RingPlan rp = ring_plan<R>(g.W, g.Lx);
-  pp.S = rp.S;
-  pp.CR = rp.CR;
-  pp.ring = smem_raw;
-  pp.seq = 0;
-  pp.err = &err;
-  pipe_init(pp);
-  cx<R>* sm = reinterpret_cast<cx<R>*>(smem_raw + (size_t)rp.S * rp.CR * g.W * sizeof(cx<R>));
-  pp.ybuf = rp.ybuf ? (void*)(sm + 2 * g.W) : nullptr;
-  SweepArgs<R> sa = sweep_base<R>(g, b, kf, i);
-  sa.src = q + (size_t)kf * g.Ndd + i * nsub;
-  sa.dst = w + (size_t)kf * g.Ndd + i * nsub;
-  sa.dst_op = 0;
-  sweep<R, WD>(g, i, sa, sm, pp, sweep_cnt(g, b, kf, i));
-  if (i < g.p - 1)
-    for (int a = threadIdx.x; a < g.A; a += DY_THREADS)
-      w[(size_t)kf * g.Ndd + g.ifc_off + (size_t)i * g.A + a] = cxd{0, 0};
-  __syncthreads();
-  if (threadIdx.x == 0 && err) atomicOr(b.st + (size_t)kf * ST_N + ST_STATUS, ST_WAIT_TIMEOUT);
-}
-
-template <typename Kern, typename... Args>
-cudaError_t launch_cluster(Kern kern, dim3 grid, int cx_, size_t smem, cudaStream_t st,
-                           Args... args) {
-  cudaError_t e = raise_smem_limit((const void*)kern, smem);
-  if (e != cudaSuccess) return e;
-  if (cx_ > 8) {
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e != cudaSuccess) return e;
-  }
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = dim3(DY_THREADS);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = cx_;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kern, args...);
-}
-
-template <typename R>
-size_t sweep_smem(const Geo& g) { return solver_smem<R>(g.W, g.Lx); }
-template <typename R>
-bool sweep_chunked_form(const Geo& g) { return ring_plan<R>(g.W, g.Lx).CR < g.W; }
-
 }  // namespace
 
 size_t dyson_internal_sweep_smem(const Geo& g, bool mixed) {
   return mixed ? sweep_smem<float>(g) : sweep_smem<double>(g);
 }
 
-template <typename R>
-cudaError_t launch_xmatvec(const Geo& g, const Bufs& b, int K, int j, int mixed, cudaStream_t st) {
-  if (sweep_chunked_form<R>(g))
-    return launch_cluster(k_xmatvec<R, true>, dim3(g.p, K), g.p, sweep_smem<R>(g), st, g, b, j, mixed);
-  return launch_cluster(k_xmatvec<R, false>, dim3(g.p, K), g.p, sweep_smem<R>(g), st, g, b, j, mixed);
-}
-template cudaError_t launch_xmatvec<double>(const Geo&, const Bufs&, int, int, int, cudaStream_t);
-template cudaError_t launch_xmatvec<float>(const Geo&, const Bufs&, int, int, int, cudaStream_t);
+
 
 cudaError_t launch_lanczos(const Geo& g, const Bufs& b, int K, int j, cudaStream_t st) {
   if (g.k_max > KMAX_SMEM) return cudaErrorInvalidValue;
@@ -1422,17 +229,4 @@ cudaError_t launch_status(const Geo&, const Bufs& b, int K, int* status, cudaStr
   return cudaGetLastError();
 }
 
-template <typename R>
-cudaError_t launch_bsolve(const Geo& g, const Bufs& b, int K, const cxd* q_dd, cxd* w_dd,
-                          cudaStream_t st) {
-  size_t smem = sweep_smem<R>(g);
-  const bool wide = sweep_chunked_form<R>(g);
-  const void* fn = wide ? (const void*)k_bsolve<R, true> : (const void*)k_bsolve<R, false>;
-  cudaError_t e = raise_smem_limit(fn, smem);
-  if (e != cudaSuccess) return e;
-  if (wide) k_bsolve<R, true><<<dim3(g.p, K), DY_THREADS, smem, st>>>(g, b, q_dd, w_dd);
-  else k_bsolve<R, false><<<dim3(g.p, K), DY_THREADS, smem, st>>>(g, b, q_dd, w_dd);
-  return cudaGetLastError();
-}
-template cudaError_t launch_bsolve<double>(const Geo&, const Bufs&, int, const cxd*, cxd*, cudaStream_t);
-template cudaError_t launch_bsolve<float>(const Geo&, const Bufs&, int, const cxd*, cxd*, cudaStream_t);
+

@@ -2,7 +2,7 @@
 factor kernel and the row-chunked sweeps, against the oracle through the C ABI.
 
 Geometries and the paths they take (FP64 / mixed):
-  (6, 9, 16)  p = 2: W = 72   chunked sweep / whole-block ring slots
+  (6, 9, 16)  p = 2: W = 72   row chunks (FP64) / one chunk per block (complex64)
   (4, 16, 17) p = 2: W = 128  chunked / chunked
   (5, 12, 26) p = 2: W = 156  chunked, W not a multiple of the 32-wide tiles
   (3, 16, 33) p = 2: W = 256  the widest slice taken
