@@ -109,7 +109,7 @@ int build_part(const dyson_geometry* in, Part* out, bool gpu) {
 
 enum {
   B_V, B_OMEGA, B_SIGMA, B_Q1, B_DD2NAT, B_G, B_G64, B_DIAGB, B_Q, B_ACC, B_U, B_V1, B_V2, B_V3,
-  B_YSCR, B_BND, B_IFV, B_PRE, B_LAN, B_MAXT, B_ST, B_OUT, B_STATUS, B_SWEEPS, B_FWORK, B_COUNT
+  B_YSCR, B_BND, B_IFV, B_PRE, B_LAN, B_MAXT, B_ST, B_OUT, B_STATUS, B_SWEEPS, B_FWORK, B_OFFB, B_COUNT
 };
 
 size_t layout(const Geo& g, int K, bool mixed, size_t off[B_COUNT]) {
@@ -133,7 +133,7 @@ size_t layout(const Geo& g, int K, bool mixed, size_t off[B_COUNT]) {
   sz[B_YSCR] = Kz * g.p * nsub * cs;
   sz[B_BND] = Kz * g.p * 2 * g.A * sizeof(cxd);
   sz[B_IFV] = Kz * IF_N * nifc(g) * sizeof(cxd);
-  sz[B_PRE] = Kz * nifc(g) * 2 * sizeof(cxd);
+  sz[B_PRE] = Kz * nifc(g) * 3 * sizeof(cxd);
   sz[B_LAN] = Kz * (g.k_max + 1) * 2 * sizeof(cxd);
   sz[B_MAXT] = Kz * sizeof(double);
   sz[B_ST] = Kz * ST_N * sizeof(int);
@@ -141,6 +141,7 @@ size_t layout(const Geo& g, int K, bool mixed, size_t off[B_COUNT]) {
   sz[B_STATUS] = Kz * sizeof(int);
   sz[B_SWEEPS] = Kz * g.p * sizeof(unsigned long long);
   sz[B_FWORK] = g.W > DY_MAXW_SMEM ? (size_t)DY_FACTOR_CTAS * 2 * g.W * g.W * sizeof(cxd) : 0;
+  sz[B_OFFB] = Kz * g.p * nsub * sizeof(cxd);
   size_t o = 0;
   for (int k = 0; k < B_COUNT; ++k) {
     off[k] = o;
@@ -409,6 +410,7 @@ int dyson_plan_create(const dyson_geometry* geom, dyson_plan* out) {
   b.out = at<cxd>(p, B_OUT);
   b.sweeps = at<unsigned long long>(p, B_SWEEPS);
   b.fwork = p->g.W > DY_MAXW_SMEM ? at<cxd>(p, B_FWORK) : nullptr;
+  b.offB = at<cxd>(p, B_OFFB);
   p->status_d = at<int>(p, B_STATUS);
   p->profile = false;
   p->n_prof = 0;

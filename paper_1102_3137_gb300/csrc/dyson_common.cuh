@@ -126,6 +126,7 @@ struct Bufs {
   void* g;              // [K][p][Lx][W][W] slice factors g_s read by the sweeps (precision of the form)
   cxd* g64;             // [K][p][Lx][W][W] FP64 g_s kept for the mixed form's FP64 recursion
   cxd* diagB;           // [K][Ndd] diag(B^-1), zero on the interface
+  cxd* offB;            // [K][p][Lx][W] diag of G_{s,s+1} (B_i^-1 between slices s, s+1), or null
   cxd* Q;               // [K][k_max+1][Ndd] Lanczos vectors
   cxd* acc;             // [K][Ndd] running diag(Q T Q^T)
   cxd* u;               // [K][Ndd] X q
@@ -135,7 +136,7 @@ struct Bufs {
   void* yscr;           // [K][p][Lx][W] forward-sweep intermediates (precision of the form)
   cxd* bnd;             // [K][p][2][A] sweep values on the subdomain boundary rows
   cxd* ifv;             // [K][6][(p-1)*A] interface Krylov vectors
-  cxd* pre;             // [K][p-1][2][A] tridiagonal preconditioner factors
+  cxd* pre;             // [K][p-1][3][A] tridiagonal preconditioner factors
   cxd* lan;             // [K][k_max+1][2] (alpha_j, beta_j); beta_j couples q_{j-1}, q_j
   double* maxT;         // [K] running max |T| entry
   int* st;              // [K][ST_N]

@@ -877,7 +877,7 @@ __device__ __forceinline__ cx<R> shfl_down_c(cx<R> v, int d) {
 // Apply the tridiagonal preconditioner along the x lines of layer i: z = M^-1 r.
 // Thomas substitution written as compositions of affine maps, one warp per
 // line, 128 sites (4 per lane) per pass with the boundary value carried from
-// pass to pass: forward d'_x = a_x d'_{x-1} + b_x (a_x = -t inv_x,
+// pass to pass: forward d'_x = a_x d'_{x-1} + b_x (a_x = -e_{x-1} inv_x,
 // b_x = r_x inv_x), stored in z; backward z_x = -c'_x z_{x+1} + d'_x.  Each
 // lane composes the maps of its 4 sites, a 5-step warp scan composes across
 // lanes, then the lanes finish their sites: ~9 dependent steps per 128 sites.
@@ -890,8 +890,7 @@ template <typename R>
 __device__ void precond_apply(const Geo& g, const Bufs& b, int kf, int i, const cx<R>* r, cx<R>* z) {
   constexpr int E = 4, CH = 32 * E;
   const int Lx = g.Lx, A = g.A;
-  const cx<R>* __restrict__ pre = reinterpret_cast<const cx<R>*>(b.pre) + ((size_t)kf * nifc(g) + (size_t)i * A) * 2;
-  const R t = (R)g.t;
+  const cx<R>* __restrict__ pre = reinterpret_cast<const cx<R>*>(b.pre) + ((size_t)kf * nifc(g) + (size_t)i * A) * 3;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int tr = wid; tr < g.T; tr += DY_WARPS) {
     const int o = Lx * tr;
@@ -906,7 +905,7 @@ __device__ void precond_apply(const Geo& g, const Bufs& b, int kf, int i, const 
         bv[k] = cx<R>{0, 0};
         if (x0 + k < Lx) {
           const cx<R> inv = pre[o + x0 + k];
-          av[k] = (x0 + k == 0) ? cx<R>{0, 0} : (-t) * inv;
+          av[k] = pre[2 * A + o + x0 + k];     // -e_{x-1} inv_den[x] (0 at x = 0)
           bv[k] = r[o + x0 + k] * inv;
         }
         FB = av[k] * FB + bv[k];
