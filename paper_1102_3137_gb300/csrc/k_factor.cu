@@ -24,33 +24,29 @@ __device__ __forceinline__ bool slice_adjacent(int r, int c, int T) {
 }
 
 // In-place Gauss-Jordan inverse of the W x W matrix A (row-major, shared).
+// Step k: W threads cache the pivot row scaled by the pivot inverse in prow
+// (with the pivot inverse itself at prow[k]) and the pivot column in fcol;
+// every other entry then has one owner thread and needs one complex FMA, so
+// a step is W^2 FMAs and W reciprocals (not one reciprocal per thread).
 template <typename R>
-__device__ void gj_invert(cx<R>* A, int W) {
-  constexpr int MAXE = DY_MAXW_SMEM * DY_MAXW_SMEM / DY_THREADS;
-  cx<R> nv[MAXE];
+__device__ void gj_invert(cx<R>* A, int W, cx<R>* prow, cx<R>* fcol) {
   const int n = W * W;
   for (int k = 0; k < W; ++k) {
-    __syncthreads();
-    const cx<R> piv = cinv(A[k * W + k]);
-    int q = 0;
-    for (int e = threadIdx.x; e < n; e += DY_THREADS, ++q) {
-      int r = e / W, c = e - r * W;
-      cx<R> v;
-      if (r == k && c == k) {
-        v = piv;
-      } else if (r == k) {
-        v = A[k * W + c] * piv;
-      } else if (c == k) {
-        v = -(A[r * W + k] * piv);
-      } else {
-        cx<R> f = A[r * W + k] * piv;
-        v = A[e] - f * A[k * W + c];
-      }
-      nv[q] = v;
+    __syncthreads();                         // step k-1 finished by every thread
+    for (int e = threadIdx.x; e < W; e += DY_THREADS) {
+      const cx<R> piv = cinv(A[k * W + k]);
+      prow[e] = (e == k) ? piv : A[k * W + e] * piv;
+      fcol[e] = A[e * W + k];
     }
     __syncthreads();
-    q = 0;
-    for (int e = threadIdx.x; e < n; e += DY_THREADS, ++q) A[e] = nv[q];
+    for (int e = threadIdx.x; e < n; e += DY_THREADS) {
+      const int r = e / W, c = e - r * W;
+      cx<R> v;
+      if (r == k) v = prow[c];                        // scaled pivot row; piv at c = k
+      else if (c == k) v = -(fcol[r] * prow[k]);
+      else v = A[e] - fcol[r] * prow[c];
+      A[e] = v;
+    }
   }
   __syncthreads();
 }
@@ -93,6 +89,8 @@ __global__ void __launch_bounds__(DY_THREADS) k_factor(Geo g, Bufs b) {
   C* A = reinterpret_cast<C*>(smem_raw);
   C* Bm = A + n;
   C* Cm = Bm + n;
+  C* prow = Cm + n;                          // Gauss-Jordan pivot row / column caches
+  C* fcol = prow + W;
   constexpr bool two = sizeof(S) != sizeof(R);
   const size_t uoff = ((size_t)kf * g.p + i) * (size_t)Lx * n;
   C* gout = reinterpret_cast<C*>(two ? b.g64 : b.g) + uoff;
@@ -123,7 +121,7 @@ __global__ void __launch_bounds__(DY_THREADS) k_factor(Geo g, Bufs b) {
   };
   // invert A in place, zero its padding and store it in slot s
   auto invert_store = [&](int s) {
-    gj_invert<R>(A, W);
+    gj_invert<R>(A, W, prow, fcol);
     for (int e = threadIdx.x; e < n; e += DY_THREADS) {
       int r = e / W, c = e - r * W;
       C v = A[e];
@@ -150,12 +148,19 @@ __global__ void __launch_bounds__(DY_THREADS) k_factor(Geo g, Bufs b) {
     if (oB)
       for (int r = threadIdx.x; r < W; r += DY_THREADS)
         oB[(size_t)(s < sn ? s : sn) * W + r] = (r < w) ? cconv<double>((-t) * Cm[r * W + r]) : cxd{0, 0};
+    // g_s + t^2 (g_s A) g_s is complex symmetric: the upper triangle, then the mirror
     for (int e = threadIdx.x; e < n; e += DY_THREADS) {
       int r = e / W, c = e - r * W;
+      if (c < r) continue;
       C acc = {0, 0};
       const C* xr = Cm + r * W;
       for (int k = 0; k < W; ++k) acc = cfma(xr[k], Bm[k * W + c], acc);
       A[e] = Bm[e] + t2 * acc;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n; e += DY_THREADS) {
+      int r = e / W, c = e - r * W;
+      if (c < r) A[e] = A[c * W + r];
     }
     __syncthreads();
     diag_out(s);
@@ -397,7 +402,7 @@ cudaError_t launch_factor(const Geo& g, const Bufs& b, int K, cudaStream_t st) {
     k_factor_big<S><<<units < DY_FACTOR_CTAS ? units : DY_FACTOR_CTAS, DY_THREADS, 0, st>>>(g, b, K);
     return cudaGetLastError();
   }
-  size_t smem = 3 * (size_t)g.W * g.W * sizeof(cx<R>);
+  size_t smem = (3 * (size_t)g.W * g.W + 2 * (size_t)g.W) * sizeof(cx<R>);
   cudaError_t e = raise_smem_limit((const void*)k_factor<R, S>, smem);
   if (e != cudaSuccess) return e;
   k_factor<R, S><<<dim3(g.p, K), DY_THREADS, smem, st>>>(g, b);
