@@ -371,37 +371,37 @@ __device__ void sweep_pair(const Geo& g, int i, const SweepArgs<float>& a, cxf* 
   const bool v0 = r0 < W, v1 = WF > 32 && r1 < W;
   auto sliceL = [&](int n) { return n <= m ? n : 2 * m - n; };
   auto sliceR = [&](int n) { return n < qR ? Lx - 1 - n : m + 1 + (n - qR); };
-  auto slotL = [&](int n) { return (int)((pp.seq + (unsigned)n) % (unsigned)SL); };
-  auto slotR = [&](int n) { return SL + (int)((pp.seq2 + (unsigned)n) % (unsigned)SR); };
-  auto parL = [&](int n) { return ((pp.seq + (unsigned)n) / (unsigned)SL) & 1u; };
-  auto parR = [&](int n) { return ((pp.seq2 + (unsigned)n) / (unsigned)SR) & 1u; };
-  auto issueL = [&](int n) {
-    const int sl = slotL(n);
-    bulk_load(ring + (size_t)sl * WW, a.g + (size_t)sliceL(n) * WW, bytes, pp.bar + sl);
+  // the chains consume their blocks in order: slot and phase parity advance
+  // by one step at a time (no division on the critical path); the block of
+  // step n + S_c reuses the slot of step n
+  int curL = (int)(pp.seq % (unsigned)SL), curR = SL + (int)(pp.seq2 % (unsigned)SR);
+  uint32_t phL = (pp.seq / (unsigned)SL) & 1u, phR = (pp.seq2 / (unsigned)SR) & 1u;
+  auto issue_at = [&](int slot, int slice) {
+    bulk_load(ring + (size_t)slot * WW, a.g + (size_t)slice * WW, bytes, pp.bar + slot);
   };
-  auto issueR = [&](int n) {
-    const int sl = slotR(n);
-    bulk_load(ring + (size_t)sl * WW, a.g + (size_t)sliceR(n) * WW, bytes, pp.bar + sl);
-  };
-  // wait for the block of step n, product with z, release the slot
+  // Wait for the block of step n, product with z, refill the slot.  The
+  // slot's loads have completed (their values are in p0, p1) before the warp
+  // barrier, so the copy that overwrites it needs no proxy fence.
   auto stepL = [&](int n, const C* z, C& p0, C& p1) {
-    const int sl = slotL(n);
-    if (!mbar_wait(pp.bar + sl, parL(n))) *pp.err = 1;
+    const int sl = curL;
+    if (!mbar_wait(pp.bar + sl, phL)) *pp.err = 1;
     pair_product<WF>(ring + (size_t)sl * WW, z, W, lane, p0, p1);
     __syncwarp();
-    if (lane == 0 && n + SL < NLL) {
-      fence_proxy_async();
-      issueL(n + SL);
+    if (lane == 0 && n + SL < NLL) issue_at(sl, sliceL(n + SL));
+    if (++curL == SL) {
+      curL = 0;
+      phL ^= 1u;
     }
   };
   auto stepR = [&](int n, const C* z, C& p0, C& p1) {
-    const int sl = slotR(n);
-    if (!mbar_wait(pp.bar + sl, parR(n))) *pp.err = 1;
+    const int sl = curR;
+    if (!mbar_wait(pp.bar + sl, phR)) *pp.err = 1;
     pair_product<WF>(ring + (size_t)sl * WW, z, W, lane, p0, p1);
     __syncwarp();
-    if (lane == 0 && n + SR < NLR) {
-      fence_proxy_async();
-      issueR(n + SR);
+    if (lane == 0 && n + SR < NLR) issue_at(sl, sliceR(n + SR));
+    if (++curR == SL + SR) {
+      curR = SL;
+      phR ^= 1u;
     }
   };
   auto rd = [&](int s, int r) { return yb[(size_t)s * W + r]; };
@@ -409,8 +409,8 @@ __device__ void sweep_pair(const Geo& g, int i, const SweepArgs<float>& a, cxf* 
   __syncthreads();                       // previous users of ring, z buffers and yb are done
   if (tid == 0) {
     fence_proxy_async();
-    for (int n = 0; n < SL && n < NLL; ++n) issueL(n);
-    for (int n = 0; n < SR && n < NLR; ++n) issueR(n);
+    for (int n = 0; n < SL && n < NLL; ++n) issue_at((int)((pp.seq + n) % (unsigned)SL), sliceL(n));
+    for (int n = 0; n < SR && n < NLR; ++n) issue_at(SL + (int)((pp.seq2 + n) % (unsigned)SR), sliceR(n));
   }
   sweep_prepass<float>(g, i, a, yb);
   __syncthreads();
