@@ -73,6 +73,7 @@ int build_part(const dyson_geometry* in, Part* out, bool gpu) {
   if (ndd > (1LL << 30)) return fail(DYSON_E_UNSUPPORTED, "lattice too large");
   g.Ndd = (int)ndd;
   g.ifc_off = g.p * g.Lx * g.W;
+  g.penta = (g.T == 1 && g.W <= DY_MAXW_SMEM) ? 1 : 0;
   g.k_max = in->k_max;
   if (g.k_max < 1 || g.k_max > 256) return fail(DYSON_E_BAD_ARG, "k_max must be in 1..256");
   if (in->precision != DYSON_FP64 && in->precision != DYSON_MIXED)
@@ -109,7 +110,7 @@ int build_part(const dyson_geometry* in, Part* out, bool gpu) {
 
 enum {
   B_V, B_OMEGA, B_SIGMA, B_Q1, B_DD2NAT, B_G, B_G64, B_DIAGB, B_Q, B_ACC, B_U, B_V1, B_V2, B_V3,
-  B_YSCR, B_BND, B_IFV, B_PRE, B_LAN, B_MAXT, B_ST, B_OUT, B_STATUS, B_SWEEPS, B_FWORK, B_OFFB, B_COUNT
+  B_YSCR, B_BND, B_IFV, B_PRE, B_LAN, B_MAXT, B_ST, B_OUT, B_STATUS, B_SWEEPS, B_FWORK, B_OFFB, B_OFF2, B_COUNT
 };
 
 size_t layout(const Geo& g, int K, bool mixed, size_t off[B_COUNT]) {
@@ -142,6 +143,7 @@ size_t layout(const Geo& g, int K, bool mixed, size_t off[B_COUNT]) {
   sz[B_SWEEPS] = Kz * g.p * sizeof(unsigned long long);
   sz[B_FWORK] = g.W > DY_MAXW_SMEM ? (size_t)DY_FACTOR_CTAS * 2 * g.W * g.W * sizeof(cxd) : 0;
   sz[B_OFFB] = Kz * g.p * nsub * sizeof(cxd);
+  sz[B_OFF2] = g.penta ? Kz * g.p * nsub * sizeof(cxd) : 0;
   size_t o = 0;
   for (int k = 0; k < B_COUNT; ++k) {
     off[k] = o;
@@ -411,6 +413,7 @@ int dyson_plan_create(const dyson_geometry* geom, dyson_plan* out) {
   b.sweeps = at<unsigned long long>(p, B_SWEEPS);
   b.fwork = p->g.W > DY_MAXW_SMEM ? at<cxd>(p, B_FWORK) : nullptr;
   b.offB = at<cxd>(p, B_OFFB);
+  b.off2 = p->g.penta ? at<cxd>(p, B_OFF2) : nullptr;
   p->status_d = at<int>(p, B_STATUS);
   p->profile = false;
   p->n_prof = 0;

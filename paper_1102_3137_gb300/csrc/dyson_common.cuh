@@ -114,6 +114,7 @@ struct Geo {
   int h[DY_MAXP];      // subdomain heights along the slow axis
   int s0[DY_MAXP];     // subdomain start along the slow axis
   int ylayer[DY_MAXP]; // slow coordinate of interface layer l
+  int penta;           // interface preconditioner keeps the distance-2 coupling (2D strips, W <= 64)
 };
 
 // Device buffers of one plan; every per-frequency array is [K_cap][...].
@@ -127,6 +128,7 @@ struct Bufs {
   cxd* g64;             // [K][p][Lx][W][W] FP64 g_s kept for the mixed form's FP64 recursion
   cxd* diagB;           // [K][Ndd] diag(B^-1), zero on the interface
   cxd* offB;            // [K][p][Lx][W] diag of G_{s,s+1} (B_i^-1 between slices s, s+1), or null
+  cxd* off2;            // [K][p][Lx][W] diag of G_{s,s+2} on the boundary rows (2D strips), or null
   cxd* Q;               // [K][k_max+1][Ndd] Lanczos vectors
   cxd* acc;             // [K][Ndd] running diag(Q T Q^T)
   cxd* u;               // [K][Ndd] X q

@@ -91,6 +91,8 @@ __global__ void __launch_bounds__(DY_THREADS) k_factor(Geo g, Bufs b) {
   C* Cm = Bm + n;
   C* prow = Cm + n;                          // Gauss-Jordan pivot row / column caches
   C* fcol = prow + W;
+  C* Gprev = fcol + W;                       // [2][W] columns of the last off-diagonal block at the boundary rows
+  C* Gmid = Gprev + 2 * W;                   // [2][W] rows of G_{m+1,m} at the boundary rows (two-sided)
   constexpr bool two = sizeof(S) != sizeof(R);
   const size_t uoff = ((size_t)kf * g.p + i) * (size_t)Lx * n;
   C* gout = reinterpret_cast<C*>(two ? b.g64 : b.g) + uoff;
@@ -137,10 +139,17 @@ __global__ void __launch_bounds__(DY_THREADS) k_factor(Geo g, Bufs b) {
       dB[(size_t)s * W + r] = (r < w) ? cconv<double>(A[r * W + r]) : cxd{0, 0};
   };
   cxd* oB = b.offB ? b.offB + ((size_t)kf * g.p + i) * (size_t)Lx * W : nullptr;
+  // distance-2 couplings on the two boundary rows (2D strips: row 0 below,
+  // row w-1 above): G_{s,s2} = -t g_s G_{sn,s2} with s2 = 2 sn - s, from the
+  // columns of the previous step's off-diagonal block G_{sn,s2}
+  cxd* o2 = (b.off2 && T == 1) ? b.off2 + ((size_t)kf * g.p + i) * (size_t)Lx * W : nullptr;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   // A <- g_s + t^2 g_s A g_s with g_s from slot s (A = G of the neighbour toward
   // the start, slice sn); -t g_s A is the off-diagonal block G_{s,sn}, whose
-  // diagonal the interface preconditioner uses (stored at min(s, sn))
-  auto grow_G = [&](int s, int sn) {
+  // diagonal the interface preconditioner uses (stored at min(s, sn)).
+  // prevc: boundary columns of G_{sn,s2} (null if s2 is outside the strip);
+  // mid: also keep the boundary rows of G_{s,sn} in Gmid
+  auto grow_G = [&](int s, int sn, const C* prevc, bool mid) {
     for (int e = threadIdx.x; e < n; e += DY_THREADS) Bm[e] = gout[(size_t)s * n + e];
     __syncthreads();
     smem_matmul<R>(Cm, Bm, A, W);
@@ -148,6 +157,25 @@ __global__ void __launch_bounds__(DY_THREADS) k_factor(Geo g, Bufs b) {
     if (oB)
       for (int r = threadIdx.x; r < W; r += DY_THREADS)
         oB[(size_t)(s < sn ? s : sn) * W + r] = (r < w) ? cconv<double>((-t) * Cm[r * W + r]) : cxd{0, 0};
+    if (o2) {
+      const int s2 = 2 * sn - s;
+      if (prevc && wid < 2) {                // warp jj: boundary row jj ? w-1 : 0
+        const int j = wid ? w - 1 : 0;
+        C acc = {0, 0};
+        for (int c = lane; c < W; c += 32) acc = cfma(Bm[j * W + c], prevc[wid * W + c], acc);
+        for (int off = 16; off > 0; off >>= 1) {
+          acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+          acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+        }
+        if (lane == 0) o2[(size_t)(s < s2 ? s : s2) * W + j] = cconv<double>((-t) * acc);
+      }
+      __syncthreads();                       // prevc read before Gprev is rewritten
+      for (int e = threadIdx.x; e < 2 * W; e += DY_THREADS) {
+        const int jj = e / W, c = e - jj * W, j = jj ? w - 1 : 0;
+        Gprev[e] = (-t) * Cm[c * W + j];
+        if (mid) Gmid[e] = (-t) * Cm[j * W + c];
+      }
+    }
     // g_s + t^2 (g_s A) g_s is complex symmetric: the upper triangle, then the mirror
     for (int e = threadIdx.x; e < n; e += DY_THREADS) {
       int r = e / W, c = e - r * W;
@@ -172,7 +200,7 @@ __global__ void __launch_bounds__(DY_THREADS) k_factor(Geo g, Bufs b) {
       invert_store(s);
     }
     diag_out(Lx - 1);                        // backward: A holds G_{s+1,s+1}
-    for (int s = Lx - 2; s >= 0; --s) grow_G(s, s + 1);
+    for (int s = Lx - 2; s >= 0; --s) grow_G(s, s + 1, s < Lx - 2 ? Gprev : nullptr, false);
   } else {
     const int m = Lx / 2;
     for (int s = 0; s < m; ++s) {           // left chain
@@ -187,10 +215,12 @@ __global__ void __launch_bounds__(DY_THREADS) k_factor(Geo g, Bufs b) {
          m < Lx - 1 ? gout + (size_t)(m + 1) * n : nullptr);
     invert_store(m);                         // G_mm
     diag_out(m);
-    for (int s = m - 1; s >= 0; --s) grow_G(s, s + 1);
+    // right side first, so that the left side's first step finds G_{m,m+1}
+    for (int s = m + 1; s < Lx; ++s) grow_G(s, s - 1, s > m + 1 ? Gprev : nullptr, s == m + 1);
     for (int e = threadIdx.x; e < n; e += DY_THREADS) A[e] = gout[(size_t)m * n + e];
     __syncthreads();
-    for (int s = m + 1; s < Lx; ++s) grow_G(s, s - 1);
+    for (int s = m - 1; s >= 0; --s)
+      grow_G(s, s + 1, s < m - 1 ? Gprev : (m + 1 < Lx ? Gmid : nullptr), false);
   }
   // interface part of diag(B^-1) is zero (blkdiag(B^-1, 0), Eq. 9)
   if (i == g.p - 1) {
@@ -346,19 +376,20 @@ __global__ void __launch_bounds__(DY_THREADS) k_factor_big(Geo g, Bufs b, int K)
   }
 }
 
-// Tridiagonal preconditioner of the interface Schur system.  The Schur
-// complement S = C - E^T B^-1 E (Eq. 4) is never formed; its cheap
-// approximation keeps, on each x line of interface layer l, the entries of
-// S_ll within one site along x, which need only the diagonal and the first
-// off-diagonal blocks of B^-1 on the rows next to the layer (both from the
-// factorization):
-//   M[x][x]   = d_C(x) - t^2 (G_xx^{l,top} + G_xx^{l+1,bot})
+// Banded preconditioner of the interface Schur system.  The Schur complement
+// S = C - E^T B^-1 E (Eq. 4) is never formed; its cheap approximation keeps,
+// on each x line of interface layer l, the entries of S_ll within two sites
+// along x (one in 3D slabs), which need only the diagonal, first and second
+// off-diagonal blocks of B^-1 on the rows next to the layer, all from the
+// factorization:
+//   M[x][x]   = d_C(x) - t^2 (G_{x,x}^{l,top}   + G_{x,x}^{l+1,bot})
 //   M[x][x+1] = t      - t^2 (G_{x,x+1}^{l,top} + G_{x,x+1}^{l+1,bot})
-// (in 3D the in-plane y hopping is dropped).  Dropping the off-diagonal
-// correction (M[x][x+1] = t) needs ~1.8x the COCG iterations at the lowest
-// Matsubara frequency.  Thomas factors per x line, computed in FP64 and stored
-// in precision R: inv_den[x], c'[x] = e_x inv_den[x] and a[x] = -e_{x-1} inv_den[x],
-// e_x = M[x][x+1].
+//   M[x][x+2] =        - t^2 (G_{x,x+2}^{l,top} + G_{x,x+2}^{l+1,bot})
+// (in 3D the in-plane y hopping is dropped).  At the lowest Matsubara frequency
+// of the 128^2 workload COCG needs 16 iterations to 1e-5 with the diagonal
+// correction alone, 9 with the first off-diagonal and 6 with both.  Factors
+// per x line, M = L D L^T without conjugation, computed in FP64 and stored in
+// precision R: 1/d_x, l1_x, l2_x.
 template <typename R>
 __global__ void __launch_bounds__(DY_THREADS) k_precond(Geo g, Bufs b) {
   const int l = blockIdx.x, kf = blockIdx.y;
@@ -366,27 +397,34 @@ __global__ void __launch_bounds__(DY_THREADS) k_precond(Geo g, Bufs b) {
   const cxd* dB = b.diagB + (size_t)kf * g.Ndd;
   const size_t nsub = (size_t)Lx * W;
   const cxd* oB = b.offB + (size_t)kf * g.p * nsub;
+  const cxd* o2 = (g.penta && b.off2) ? b.off2 + (size_t)kf * g.p * nsub : nullptr;
   cx<R>* pre = reinterpret_cast<cx<R>*>(b.pre) + ((size_t)kf * nifc(g) + (size_t)l * A) * 3;
   const double t = g.t, t2 = g.t * g.t;
+  const cxd zero = {0, 0};
   for (int tr = threadIdx.x; tr < T; tr += DY_THREADS) {
     // row just below the layer: top row of subdomain l; just above: bottom row of l+1
     const size_t jb = (size_t)l * nsub + tr + T * (g.h[l] - 1);
     const size_t ja = (size_t)(l + 1) * nsub + tr;
-    cxd cprev = {0, 0}, eprev = {0, 0};
+    auto e1 = [&](int x) {                   // M[x][x+1]
+      return (x >= 0 && x + 1 < Lx) ? cxd{t, 0} - t2 * (oB[jb + (size_t)x * W] + oB[ja + (size_t)x * W]) : zero;
+    };
+    auto e2 = [&](int x) {                   // M[x][x+2]
+      return (o2 && x >= 0 && x + 2 < Lx) ? -(t2 * (o2[jb + (size_t)x * W] + o2[ja + (size_t)x * W])) : zero;
+    };
+    cxd d1 = zero, d2 = zero, l1p = zero;    // d_{x-1}, d_{x-2}, l1_{x-1}
     for (int x = 0; x < Lx; ++x) {
-      int a = x + Lx * tr;
-      int nat = a + A * g.ylayer[l];
-      cxd d = dyson_diag(g, b, kf, nat);
-      cxd m = d - t2 * (dB[jb + (size_t)x * W] + dB[ja + (size_t)x * W]);
-      cxd e = (x + 1 < Lx) ? cxd{t, 0} - t2 * (oB[jb + (size_t)x * W] + oB[ja + (size_t)x * W]) : cxd{0, 0};
-      cxd den = (x == 0) ? m : m - eprev * cprev;
-      cxd inv = cinv(den);
-      cxd cp = e * inv;
-      pre[a] = cconv<R>(inv);
-      pre[A + a] = cconv<R>(cp);
-      pre[2 * A + a] = cconv<R>((x == 0) ? cxd{0, 0} : -(eprev * inv));
-      cprev = cp;
-      eprev = e;
+      const int a = x + Lx * tr;
+      const cxd mxx = dyson_diag(g, b, kf, a + A * g.ylayer[l]) -
+                      t2 * (dB[jb + (size_t)x * W] + dB[ja + (size_t)x * W]);
+      const cxd l2 = (x >= 2) ? e2(x - 2) * cinv(d2) : zero;
+      const cxd l1 = (x >= 1) ? (e1(x - 1) - l2 * l1p * d2) * cinv(d1) : zero;
+      const cxd dx = mxx - l1 * l1 * d1 - l2 * l2 * d2;
+      pre[a] = cconv<R>(cinv(dx));
+      pre[A + a] = cconv<R>(l1);
+      pre[2 * A + a] = cconv<R>(l2);
+      d2 = d1;
+      d1 = dx;
+      l1p = l1;
     }
   }
 }
@@ -402,7 +440,7 @@ cudaError_t launch_factor(const Geo& g, const Bufs& b, int K, cudaStream_t st) {
     k_factor_big<S><<<units < DY_FACTOR_CTAS ? units : DY_FACTOR_CTAS, DY_THREADS, 0, st>>>(g, b, K);
     return cudaGetLastError();
   }
-  size_t smem = (3 * (size_t)g.W * g.W + 2 * (size_t)g.W) * sizeof(cx<R>);
+  size_t smem = (3 * (size_t)g.W * g.W + 6 * (size_t)g.W) * sizeof(cx<R>);
   cudaError_t e = raise_smem_limit((const void*)k_factor<R, S>, smem);
   if (e != cudaSuccess) return e;
   k_factor<R, S><<<dim3(g.p, K), DY_THREADS, smem, st>>>(g, b);

@@ -874,98 +874,140 @@ __device__ __forceinline__ cx<R> shfl_down_c(cx<R> v, int d) {
   return {__shfl_down_sync(0xffffffffu, v.x, d), __shfl_down_sync(0xffffffffu, v.y, d)};
 }
 
-// Apply the tridiagonal preconditioner along the x lines of layer i: z = M^-1 r.
-// Thomas substitution written as compositions of affine maps, one warp per
-// line, 128 sites (4 per lane) per pass with the boundary value carried from
-// pass to pass: forward d'_x = a_x d'_{x-1} + b_x (a_x = -e_{x-1} inv_x,
-// b_x = r_x inv_x), stored in z; backward z_x = -c'_x z_{x+1} + d'_x.  Each
-// lane composes the maps of its 4 sites, a 5-step warp scan composes across
-// lanes, then the lanes finish their sites: ~9 dependent steps per 128 sites.
+// Affine map on a pair of complex values: (s0, s1) -> (a s0 + b s1 + u, c s0 + d s1 + v).
+template <typename R>
+struct Aff2 {
+  cx<R> a, b, c, d, u, v;
+};
+template <typename R>
+__device__ __forceinline__ Aff2<R> aff_id() {
+  return {{1, 0}, {0, 0}, {0, 0}, {1, 0}, {0, 0}, {0, 0}};
+}
+// o after in
+template <typename R>
+__device__ __forceinline__ Aff2<R> aff_after(const Aff2<R>& o, const Aff2<R>& in) {
+  return {o.a * in.a + o.b * in.c, o.a * in.b + o.b * in.d, o.c * in.a + o.d * in.c,
+          o.c * in.b + o.d * in.d, o.a * in.u + o.b * in.v + o.u, o.c * in.u + o.d * in.v + o.v};
+}
+template <typename R>
+__device__ __forceinline__ Aff2<R> aff_shfl_up(const Aff2<R>& f, int d) {
+  return {shfl_up_c(f.a, d), shfl_up_c(f.b, d), shfl_up_c(f.c, d),
+          shfl_up_c(f.d, d), shfl_up_c(f.u, d), shfl_up_c(f.v, d)};
+}
+template <typename R>
+__device__ __forceinline__ Aff2<R> aff_shfl_down(const Aff2<R>& f, int d) {
+  return {shfl_down_c(f.a, d), shfl_down_c(f.b, d), shfl_down_c(f.c, d),
+          shfl_down_c(f.d, d), shfl_down_c(f.u, d), shfl_down_c(f.v, d)};
+}
+
+// Apply the banded interface preconditioner along the x lines of layer i:
+// z = M^-1 r with M = L D L^T (complex symmetric, no conjugation; L unit lower
+// with sub-diagonals l1, l2, l2 = 0 where only the tridiagonal part is kept):
+//   forward   y_x = r_x - l1_x y_{x-1} - l2_x y_{x-2},   w_x = y_x / d_x
+//   backward  z_x = w_x - l1_{x+1} z_{x+1} - l2_{x+2} z_{x+2}
+// Each recurrence is a chain of affine maps on the pair state (y_x, y_{x-1})
+// (resp. (z_x, z_{x+1})): one warp per line, 128 sites (4 per lane) per pass
+// with the state carried from pass to pass; each lane composes its 4 sites'
+// maps, a 5-step warp scan composes across lanes, then the lanes finish
+// their sites.  Factors per site: 1/d_x, l1_x, l2_x.
 //
 // r is the COCG residual, rewritten in this kernel between calls: it must be
 // read through the coherent path, never as const __restrict__ (which lets the
 // compiler use non-coherent loads whose cached lines can be stale by the next
 // iteration).  The preconditioner factors are read-only for the kernel's life.
+//
+// Not inlined: the scan's state would otherwise compete for registers with the
+// whole X-matvec kernel (capped at 128 per thread for two CTAs per SM) and
+// spill inside the sweeps.
 template <typename R>
-__device__ void precond_apply(const Geo& g, const Bufs& b, int kf, int i, const cx<R>* r, cx<R>* z) {
+__device__ __noinline__ void precond_apply(const Geo& g, const Bufs& b, int kf, int i, const cx<R>* r,
+                                           cx<R>* z) {
+  using C = cx<R>;
   constexpr int E = 4, CH = 32 * E;
   const int Lx = g.Lx, A = g.A;
-  const cx<R>* __restrict__ pre = reinterpret_cast<const cx<R>*>(b.pre) + ((size_t)kf * nifc(g) + (size_t)i * A) * 3;
+  const C* __restrict__ pre = reinterpret_cast<const C*>(b.pre) + ((size_t)kf * nifc(g) + (size_t)i * A) * 3;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const C zero = {0, 0};
   for (int tr = wid; tr < g.T; tr += DY_WARPS) {
     const int o = Lx * tr;
-    cx<R> carry = {0, 0};                  // d'_{c0-1}
+    const C* invd = pre + o;
+    const C* l1 = pre + A + o;
+    const C* l2 = pre + 2 * A + o;
+    C c0v = zero, c1v = zero;              // (y, y_prev) entering the pass
     for (int c0 = 0; c0 < Lx; c0 += CH) {
       const int x0 = c0 + lane * E;
-      cx<R> av[E], bv[E];
-      cx<R> FA = {1, 0}, FB = {0, 0};
+      // site x: (s0, s1) -> (-l1_x s0 - l2_x s1 + r_x, s0); the coefficients are
+      // re-read in the apply pass rather than held in registers
+      Aff2<R> P = aff_id<R>();
 #pragma unroll
       for (int k = 0; k < E; ++k) {
-        av[k] = cx<R>{1, 0};
-        bv[k] = cx<R>{0, 0};
-        if (x0 + k < Lx) {
-          const cx<R> inv = pre[o + x0 + k];
-          av[k] = pre[2 * A + o + x0 + k];     // -e_{x-1} inv_den[x] (0 at x = 0)
-          bv[k] = r[o + x0 + k] * inv;
-        }
-        FB = av[k] * FB + bv[k];
-        FA = av[k] * FA;
+        const int x = x0 + k;
+        if (x < Lx) P = aff_after(Aff2<R>{-l1[x], -l2[x], {1, 0}, zero, r[o + x], zero}, P);
       }
 #pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {   // inclusive scan: F_l o F_{l-d}
-        const cx<R> pa = shfl_up_c(FA, d), pb = shfl_up_c(FB, d);
-        if (lane >= d) {
-          FB = FA * pb + FB;
-          FA = FA * pa;
-        }
+      for (int d = 1; d < 32; d <<= 1) {   // inclusive scan: lanes l-d.. then l
+        const Aff2<R> q = aff_shfl_up(P, d);
+        if (lane >= d) P = aff_after(P, q);
       }
-      cx<R> v = shfl_up_c(FA * carry + FB, 1);   // d' before this lane's sites
-      if (lane == 0) v = carry;
-      else {
-        // shfl_up_c moved F_{l-1}(carry) of the previous lane
+      // state entering this lane: the previous lane's prefix applied to the carry
+      C s0 = P.a * c0v + P.b * c1v + P.u, s1 = P.c * c0v + P.d * c1v + P.v;
+      s0 = shfl_up_c(s0, 1);
+      s1 = shfl_up_c(s1, 1);
+      if (lane == 0) {
+        s0 = c0v;
+        s1 = c1v;
       }
 #pragma unroll
       for (int k = 0; k < E; ++k) {
-        v = av[k] * v + bv[k];
-        if (x0 + k < Lx) z[o + x0 + k] = v;
+        const int x = x0 + k;
+        if (x < Lx) {
+          const C y = r[o + x] - l1[x] * s0 - l2[x] * s1;
+          s1 = s0;
+          s0 = y;
+          z[o + x] = y * invd[x];
+        }
       }
-      carry = cx<R>{__shfl_sync(0xffffffffu, v.x, 31), __shfl_sync(0xffffffffu, v.y, 31)};
+      c0v = cx<R>{__shfl_sync(0xffffffffu, s0.x, 31), __shfl_sync(0xffffffffu, s0.y, 31)};
+      c1v = cx<R>{__shfl_sync(0xffffffffu, s1.x, 31), __shfl_sync(0xffffffffu, s1.y, 31)};
     }
     __syncwarp();
-    cx<R> cz = {0, 0};                     // z_{c1+1}
+    C e0v = zero, e1v = zero;              // (z, z_next) entering the pass from the right
     const int nch = (Lx + CH - 1) / CH;
     for (int c = nch - 1; c >= 0; --c) {
       const int x0 = c * CH + lane * E;
-      cx<R> av[E], dv[E];
-      cx<R> HA = {1, 0}, HB = {0, 0};
+      // site x: (s0, s1) -> (-l1_{x+1} s0 - l2_{x+2} s1 + w_x, s0)
+      auto m1 = [&](int x) { return (x + 1 < Lx) ? l1[x + 1] : zero; };
+      auto m2 = [&](int x) { return (x + 2 < Lx) ? l2[x + 2] : zero; };
+      Aff2<R> Q = aff_id<R>();
 #pragma unroll
       for (int k = E - 1; k >= 0; --k) {
         const int x = x0 + k;
-        av[k] = cx<R>{1, 0};
-        dv[k] = cx<R>{0, 0};
-        if (x < Lx) {
-          av[k] = (x == Lx - 1) ? cx<R>{0, 0} : -pre[A + o + x];
-          dv[k] = z[o + x];
-        }
-        HB = av[k] * HB + dv[k];
-        HA = av[k] * HA;
+        if (x < Lx) Q = aff_after(Aff2<R>{-m1(x), -m2(x), {1, 0}, zero, z[o + x], zero}, Q);
       }
 #pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {   // inclusive suffix scan: H_l o H_{l+d}
-        const cx<R> na = shfl_down_c(HA, d), nb = shfl_down_c(HB, d);
-        if (lane + d < 32) {
-          HB = HA * nb + HB;
-          HA = HA * na;
-        }
+      for (int d = 1; d < 32; d <<= 1) {   // inclusive suffix scan: lanes l+d.. then l
+        const Aff2<R> q = aff_shfl_down(Q, d);
+        if (lane + d < 32) Q = aff_after(Q, q);
       }
-      cx<R> v = shfl_down_c(HA * cz + HB, 1);     // z after this lane's sites
-      if (lane == 31) v = cz;
+      C s0 = Q.a * e0v + Q.b * e1v + Q.u, s1 = Q.c * e0v + Q.d * e1v + Q.v;
+      s0 = shfl_down_c(s0, 1);
+      s1 = shfl_down_c(s1, 1);
+      if (lane == 31) {
+        s0 = e0v;
+        s1 = e1v;
+      }
 #pragma unroll
       for (int k = E - 1; k >= 0; --k) {
-        v = av[k] * v + dv[k];
-        if (x0 + k < Lx) z[o + x0 + k] = v;
+        const int x = x0 + k;
+        if (x < Lx) {
+          const C v = z[o + x] - m1(x) * s0 - m2(x) * s1;
+          s1 = s0;
+          s0 = v;
+          z[o + x] = v;
+        }
       }
-      cz = cx<R>{__shfl_sync(0xffffffffu, v.x, 0), __shfl_sync(0xffffffffu, v.y, 0)};
+      e0v = cx<R>{__shfl_sync(0xffffffffu, s0.x, 0), __shfl_sync(0xffffffffu, s0.y, 0)};
+      e1v = cx<R>{__shfl_sync(0xffffffffu, s1.x, 0), __shfl_sync(0xffffffffu, s1.y, 0)};
     }
   }
 }
