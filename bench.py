@@ -44,11 +44,14 @@ def peaks():
 
 
 def kernel_source_hash():
+    """Hash of every kernel source (any change invalidates recorded ncu traffic)."""
     import hashlib
     h = hashlib.sha256()
-    for f in ("k_solve.cu", "dyson_common.cuh"):
-        with open(os.path.join(ROOT, "paper_1102_3137_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    csrc = os.path.join(ROOT, "paper_1102_3137_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith(".cuh") or (f.startswith("k_") and f.endswith(".cu")):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(fh.read())
     return h.hexdigest()[:16]
 
 

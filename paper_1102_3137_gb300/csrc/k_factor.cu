@@ -44,7 +44,7 @@ __device__ void gj_invert(cx<R>* A, int W, cx<R>* prow, cx<R>* fcol) {
       cx<R> v;
       if (r == k) v = prow[c];                        // scaled pivot row; piv at c = k
       else if (c == k) v = -(fcol[r] * prow[k]);
-      else v = A[e] - fcol[r] * prow[c];
+      else v = cfma(-fcol[r], prow[c], A[e]);   // 4 FP64 FMAs, not a product and a difference
       A[e] = v;
     }
   }
@@ -257,7 +257,7 @@ __device__ void gj_invert_global(cxd* A, int W, cxd* prow, cxd* fcol) {
       cxd v;
       if (r == k) v = (c == k) ? piv : prow[c] * piv;
       else if (c == k) v = -fcol[r];
-      else v = A[e] - fcol[r] * prow[c];
+      else v = cfma(-fcol[r], prow[c], A[e]);   // 4 FP64 FMAs, not a product and a difference
       A[e] = v;
     }
   }

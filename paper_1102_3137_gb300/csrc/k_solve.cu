@@ -38,8 +38,8 @@ __global__ void __launch_bounds__(DY_THREADS) k_lanczos(Geo g, Bufs b, int j) {
   const cxd alpha = v1[0];
   for (int e = threadIdx.x; e < n; e += DY_THREADS) {
     size_t k = own_idx(g, i, e, nsub);
-    cxd rv = u[k] - alpha * qj[k];
-    if (qm) rv = rv - beta_j * qm[k];
+    cxd rv = cfma(-alpha, qj[k], u[k]);
+    if (qm) rv = cfma(-beta_j, qm[k], rv);
     r[k] = rv;
   }
   for (int pass = 0; pass < 2; ++pass) {
@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(DY_THREADS) k_lanczos(Geo g, Bufs b, int j) {
     for (int e = threadIdx.x; e < n; e += DY_THREADS) {
       size_t k = own_idx(g, i, e, nsub);
       cxd rv = r[k];
-      for (int m = 0; m <= j; ++m) rv = rv - hs[m] * Q[(size_t)m * Ndd + k];
+      for (int m = 0; m <= j; ++m) rv = cfma(-hs[m], Q[(size_t)m * Ndd + k], rv);   // fused: 4 FP64 ops
       r[k] = rv;
     }
     __syncthreads();
