@@ -288,6 +288,26 @@ def run_ours(a, rank, world, local_rank):
         ms1 = e0.elapsed_time(e1)
         extra["one_frequency_per_launch"] = dict(value=w.K * w.N / (ms1 / 1e3), ms_all=ms1)
         p1.close()
+        # exact diagonal as its own mode: one subdomain, so diag(H^-1) = diag(B^-1)
+        # from the slice recursion alone (no interface, no Lanczos), FP64; its
+        # throughput, and the truncation error of the low-rank result against it
+        pe = D.Plan(w.L, w.t, w.mu, 1, 1, D.DYSON_FP64, max_freqs=w.K)
+        oute = torch.zeros_like(out)
+        ste = torch.zeros_like(st)
+        D.dyson_solve(pe.handle, w.K, om, Vd, sg, qd, oute, ste, ss)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(nf):
+            D.dyson_solve(pe.handle, w.K, om, Vd, sg, qd, oute, ste, ss)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_e = e0.elapsed_time(e1) / nf
+        exact = oute.cpu().numpy()
+        tr = np.abs(res - exact) / np.abs(exact)
+        extra["exact_p1"] = dict(value=w.K * w.N / (ms_e / 1e3), ms_per_step=ms_e, form="fp64",
+                                 lowrank_truncation_error=dict(max=float(tr.max()),
+                                                               median=float(np.median(tr))))
+        pe.close()
 
     # the complex64 stencil SpMV (row a1, y = H(i w_k) x) on a batch far larger than L2:
     # algorithmic 32 B per site-frequency (x c64 8 + y c64 8 + Sigma c128 16; V stays in L2)

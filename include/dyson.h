@@ -92,6 +92,11 @@ typedef struct {
   double refine_tol;  /* mixed form: relative FP64 residual after refinement; 0 = 1e-13 */
   int refine_max;     /* mixed form: most refinement passes per solve; 0 = default (6) */
   int max_freqs;      /* most frequencies one dyson_solve call may carry (>= 1) */
+  double eta;         /* frequency axis.  0: Matsubara, H_ii = i w_k + mu - V_i - Sigma_i
+                         (Eq. 1).  > 0: real axis, i w_k -> w + i eta (the retarded form
+                         Sec. 2 notes after Eq. 1); omega[] then holds real frequencies w
+                         and Sigma the retarded self-energy (Im Sigma <= 0 keeps Im H_ii >=
+                         eta > 0, which the factorization relies on).  Must be >= 0. */
 } dyson_geometry;
 
 /* Library version string. */
@@ -118,9 +123,12 @@ int dyson_plan_footprint(const dyson_geometry* geom, size_t* bytes);
  * domain-decomposition maps and allocates all device workspace for up to
  * geom->max_freqs frequencies.  *out is set on success.
  * Slice width W = (sites of one slice: h in 2D, Ly*h in 3D, h the tallest
- * subdomain) rounded up to a multiple of 4 must be <= 256, and for W > 64 the
- * sweep row buffer (Lx * W complex entries in the form's precision) must leave
- * room for the copy ring in shared memory; otherwise DYSON_E_UNSUPPORTED.
+ * subdomain) rounded up to a multiple of 4 must be <= 256, and, with p > 1,
+ * for W > 64 the sweep row buffer (Lx * W complex entries in the form's
+ * precision) must leave room for the copy ring in shared memory; otherwise
+ * DYSON_E_UNSUPPORTED.  With p = 1 the solve is the exact slice recursion
+ * (no interface, no sweeps), so only the width limit applies; the sweep
+ * entry points (dyson_subdomain_solve, dyson_xmatvec) then check it per call.
  */
 int dyson_plan_create(const dyson_geometry* geom, dyson_plan* out);
 

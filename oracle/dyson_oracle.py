@@ -52,6 +52,13 @@ def dyson_diagonal(omega: float, mu: float, V: np.ndarray, sigma: np.ndarray) ->
     return 1j * omega + mu - V - sigma
 
 
+def dyson_diagonal_real(omega: float, eta: float, mu: float, V: np.ndarray,
+                        sigma: np.ndarray) -> np.ndarray:
+    """Real-frequency form of Eq. 1, i w -> w + i eta (the remark after Eq. 1):
+    H_ii(w) = w + i eta + mu - V_i - Sigma_i(w), Sigma the retarded self-energy."""
+    return omega + 1j * eta + mu - V - sigma
+
+
 def _axis_pairs(dims, periodic):
     """Nearest-neighbour pairs (i, j) of a box with dims (first fastest)."""
     n = int(np.prod(dims))
@@ -370,15 +377,22 @@ def cs_lanczos(matvec, q1, k_max: int, term_tol: float = 1e-12, brk_tol: float =
 # --------------------------------------------------------------------------
 
 
+def axis_diagonal(omega_k, mu, V, sigma_k, eta: float = 0.0) -> np.ndarray:
+    """The Dyson diagonal on the Matsubara axis (eta = 0) or the real axis (eta > 0)."""
+    if eta > 0.0:
+        return dyson_diagonal_real(omega_k, eta, mu, V, sigma_k)
+    return dyson_diagonal(omega_k, mu, V, sigma_k)
+
+
 def lowrank_diag(L, periodic, t, mu, V, sigma_k, omega_k, q1, p: int, k_max: int,
-                 return_info: bool = False):
+                 return_info: bool = False, eta: float = 0.0):
     """diag(H^-1) = diag(blkdiag(B^-1, 0)) + diag(Q_k T_k Q_k^T)   (Eq. 9).
 
     X q = H^-1 q - blkdiag(B^-1, 0) q by one direct H solve and the
     subdomain solves (Eqs. 6-8); p = 1 has no interface, X = 0 and the
-    result is the exact recursion.
+    result is the exact recursion.  eta > 0: real frequency axis.
     """
-    z = dyson_diagonal(omega_k, mu, V, sigma_k)
+    z = axis_diagonal(omega_k, mu, V, sigma_k, eta)
     subs = Subdomains(L, periodic, t, z, p)
     if p == 1:
         acc = np.zeros(site_count(L), dtype=np.complex128)
@@ -400,17 +414,17 @@ def lowrank_diag(L, periodic, t, mu, V, sigma_k, omega_k, q1, p: int, k_max: int
     return res
 
 
-def xmatvec(L, periodic, t, mu, V, sigma_k, omega_k, p, q):
+def xmatvec(L, periodic, t, mu, V, sigma_k, omega_k, p, q, eta: float = 0.0):
     """One X-'matvec' u = H^-1 q - blkdiag(B^-1, 0) q (Eqs. 6-8), natural order."""
-    z = dyson_diagonal(omega_k, mu, V, sigma_k)
+    z = axis_diagonal(omega_k, mu, V, sigma_k, eta)
     subs = Subdomains(L, periodic, t, z, p)
     full = FullLattice(L, periodic, t, z)
     return full.solve(q) - subs.solve(q)
 
 
-def apply_H(L, periodic, t, mu, V, sigma_k, omega_k, x):
+def apply_H(L, periodic, t, mu, V, sigma_k, omega_k, x, eta: float = 0.0):
     """y = H x by the stencil (Eq. 1), natural order, without forming H."""
-    z = dyson_diagonal(omega_k, mu, V, sigma_k)
+    z = axis_diagonal(omega_k, mu, V, sigma_k, eta)
     y = z * x
     for i, j in _axis_pairs(list(L), list(periodic[:len(L)])):
         y[i] += t * x[j]

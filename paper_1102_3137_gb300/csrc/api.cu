@@ -79,12 +79,15 @@ int build_part(const dyson_geometry* in, Part* out, bool gpu) {
   if (in->precision != DYSON_FP64 && in->precision != DYSON_MIXED)
     return fail(DYSON_E_BAD_ARG, "precision must be DYSON_FP64 or DYSON_MIXED");
   const bool mixed = in->precision == DYSON_MIXED;
-  if (gpu && dyson_internal_sweep_smem(g, mixed) == 0)
+  // a single subdomain needs no sweeps (X = 0: the solve is the recursion alone)
+  if (gpu && g.p > 1 && dyson_internal_sweep_smem(g, mixed) == 0)
     return fail(DYSON_E_UNSUPPORTED, "slice width " + std::to_string(g.W) + " with Lx = " +
                                          std::to_string(g.Lx) +
                                          ": the sweep row buffer does not fit shared memory");
   g.t = in->t;
   g.mu = in->mu;
+  if (!(in->eta >= 0.0)) return fail(DYSON_E_BAD_ARG, "eta must be >= 0 (0: Matsubara axis)");
+  g.eta = in->eta;
   g.krylov_tol = in->krylov_tol > 0 ? in->krylov_tol : (mixed ? 1e-5 : 1e-13);
   g.krylov_maxit = in->krylov_maxit > 0 ? in->krylov_maxit : 1000;
   g.refine_tol = in->refine_tol > 0 ? in->refine_tol : 1e-13;
@@ -198,6 +201,16 @@ int check_plan(dyson_plan p) {
   if (!p) return fail(DYSON_E_BAD_ARG, "plan is NULL");
   cudaError_t e = cudaSetDevice(p->device);
   if (e != cudaSuccess) return fail(DYSON_E_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+  return DYSON_OK;
+}
+
+// the entry points that sweep the subdomains (every geometry with p > 1 passed
+// this at plan creation)
+int check_sweeps(dyson_plan p) {
+  if (dyson_internal_sweep_smem(p->g, p->mixed) == 0)
+    return fail(DYSON_E_UNSUPPORTED, "slice width " + std::to_string(p->g.W) + " with Lx = " +
+                                         std::to_string(p->g.Lx) +
+                                         ": the sweep row buffer does not fit shared memory");
   return DYSON_OK;
 }
 
@@ -630,6 +643,7 @@ int dyson_subdomain_solve(dyson_plan p, int K, const double* omega, const double
                           void* stream) {
   int rc;
   if ((rc = check_plan(p)) || (rc = check_K(p, K)) || (rc = check_mem(mem_kind))) return rc;
+  if ((rc = check_sweeps(p))) return rc;
   if (!q || !w) return fail(DYSON_E_BAD_ARG, "q and w must not be NULL");
   cudaStream_t s = (cudaStream_t)stream;
   if ((rc = stage_inputs(p, K, omega, V, sigma, nullptr, s))) return rc;
@@ -653,6 +667,7 @@ int dyson_xmatvec(dyson_plan p, int K, const double* omega, const double* V, con
                   const double* q, double* u, int mem_kind, void* stream) {
   int rc;
   if ((rc = check_plan(p)) || (rc = check_K(p, K)) || (rc = check_mem(mem_kind))) return rc;
+  if ((rc = check_sweeps(p))) return rc;
   if (!q || !u) return fail(DYSON_E_BAD_ARG, "q and u must not be NULL");
   cudaStream_t s = (cudaStream_t)stream;
   if ((rc = stage_inputs(p, K, omega, V, sigma, nullptr, s))) return rc;

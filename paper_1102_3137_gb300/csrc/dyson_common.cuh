@@ -115,6 +115,7 @@ struct Geo {
   int s0[DY_MAXP];     // subdomain start along the slow axis
   int ylayer[DY_MAXP]; // slow coordinate of interface layer l
   int penta;           // interface preconditioner keeps the distance-2 coupling (2D strips, W <= 64)
+  double eta;          // 0: Matsubara axis; > 0: real axis w + i eta
 };
 
 // Device buffers of one plan; every per-frequency array is [K_cap][...].
@@ -152,10 +153,13 @@ enum { IF_X = 0, IF_R = 1, IF_Z = 2, IF_P = 3, IF_SP = 4, IF_B = 5, IF_D = 6, IF
 
 __host__ __device__ __forceinline__ size_t nifc(const Geo& g) { return (size_t)(g.p > 1 ? g.p - 1 : 1) * g.A; }
 
-// H_ii(i w) = i w + mu - V_i - Sigma_i(i w)   (Eq. 1)
+// H_ii(i w) = i w + mu - V_i - Sigma_i(i w)   (Eq. 1); on the real axis
+// (eta > 0) i w -> w + i eta
 __device__ __forceinline__ cxd dyson_diag(const Geo& g, const Bufs& b, int kf, int nat) {
   cxd s = b.sigma[(size_t)kf * g.N + nat];
-  return {g.mu - b.V[nat] - s.x, b.omega[kf] - s.y};
+  const double w = b.omega[kf];
+  return g.eta > 0.0 ? cxd{w + g.mu - b.V[nat] - s.x, g.eta - s.y}
+                     : cxd{g.mu - b.V[nat] - s.x, w - s.y};
 }
 
 // natural index of row j of slice s in subdomain i

@@ -23,7 +23,8 @@ __global__ void __launch_bounds__(DY_THREADS) k_spmv(Geo g, const double* __rest
   for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
     const int xi = n % Lx, rest = n / Lx, yi = rest % Ly, zi = rest / Ly;
     const cxd s = sk[n];
-    const cx<R> d = {(R)(g.mu - V[n] - s.x), (R)(w - s.y)};
+    const cx<R> d = g.eta > 0.0 ? cx<R>{(R)(w + g.mu - V[n] - s.x), (R)(g.eta - s.y)}
+                                : cx<R>{(R)(g.mu - V[n] - s.x), (R)(w - s.y)};
     cx<R> nb = {0, 0};
     if (xi > 0) nb = nb + xk[n - 1];
     if (xi < Lx - 1) nb = nb + xk[n + 1];

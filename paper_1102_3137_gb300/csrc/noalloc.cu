@@ -110,6 +110,8 @@ extern "C" int dyson_subdomain_diag_noalloc(const dyson_geometry* geom, int K, c
   g.ifc_off = g.p * g.Lx * g.W;
   g.t = geom->t;
   g.mu = geom->mu;
+  if (!(geom->eta >= 0.0)) return dyson_internal_fail(DYSON_E_BAD_ARG, "noalloc: eta must be >= 0");
+  g.eta = geom->eta;
   const size_t b_map = align256((size_t)ndd * sizeof(int));
   const size_t b_diag = align256((size_t)K * ndd * sizeof(cxd));
   const size_t b_g = align256((size_t)K * g.p * g.Lx * g.W * g.W * sizeof(cxd));

@@ -33,7 +33,8 @@ class dyson_geometry(C.Structure):
     _fields_ = [("dim", C.c_int), ("L", C.c_int * 3), ("t", C.c_double), ("mu", C.c_double),
                 ("p", C.c_int), ("k_max", C.c_int), ("precision", C.c_int),
                 ("krylov_tol", C.c_double), ("krylov_maxit", C.c_int),
-                ("refine_tol", C.c_double), ("refine_max", C.c_int), ("max_freqs", C.c_int)]
+                ("refine_tol", C.c_double), ("refine_max", C.c_int), ("max_freqs", C.c_int),
+                ("eta", C.c_double)]
 
 
 class dyson_request(C.Structure):
@@ -162,7 +163,7 @@ def _stream(stream):
 
 
 def make_geometry(L, t=-1.0, mu=0.0, p=1, k_max=16, precision=DYSON_FP64, max_freqs=1,
-                  krylov_tol=0.0, krylov_maxit=0, refine_tol=0.0, refine_max=0):
+                  krylov_tol=0.0, krylov_maxit=0, refine_tol=0.0, refine_max=0, eta=0.0):
     g = dyson_geometry()
     g.dim = len(L)
     for d in range(3):
@@ -170,6 +171,7 @@ def make_geometry(L, t=-1.0, mu=0.0, p=1, k_max=16, precision=DYSON_FP64, max_fr
     g.t, g.mu, g.p, g.k_max, g.precision = float(t), float(mu), int(p), int(k_max), int(precision)
     g.krylov_tol, g.krylov_maxit = float(krylov_tol), int(krylov_maxit)
     g.refine_tol, g.refine_max, g.max_freqs = float(refine_tol), int(refine_max), int(max_freqs)
+    g.eta = float(eta)
     return g
 
 

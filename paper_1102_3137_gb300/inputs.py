@@ -72,12 +72,23 @@ def trap_potential(L: tuple, c: float) -> np.ndarray:
     return np.ascontiguousarray(np.transpose(r2)).ravel() * c
 
 
-def make_inputs(w: Workload, K: int | None = None, seed: int | None = None):
+def real_grid(t: float, K: int) -> np.ndarray:
+    """K real frequencies spanning the band of the lattice and a margin: [-(4|t|+1), 4|t|+1]
+    (the 2D band edge is 4|t|; in 3D, 6|t|, the grid then stops inside the band)."""
+    e = 4.0 * abs(t) + 1.0
+    return np.linspace(-e, e, K) if K > 1 else np.zeros(1)
+
+
+def make_inputs(w: Workload, K: int | None = None, seed: int | None = None, axis: str = "matsubara"):
     """Draw (omega[K], V[N], sigma[K, N] complex128, q1[N] real) for a workload.
 
     The self-energy samples a_i, b_i and the start vector q1 come from one
     numpy Generator seeded with the workload's seed, in that order, so every
     consumer of the same (workload, seed) sees identical arrays.
+    axis = "matsubara": omega are the fermionic Matsubara frequencies and
+    Sigma_i(i w_k) = a_i - i b_i sign(w_k).  axis = "real": omega is a real
+    grid across the band and Sigma_i(w) = a_i - i b_i, the retarded form
+    (Im Sigma <= 0 for every w).
     """
     K = w.K if K is None else K
     seed = w.seed if seed is None else seed
@@ -86,9 +97,11 @@ def make_inputs(w: Workload, K: int | None = None, seed: int | None = None):
     a = rng.uniform(-1.0, 1.0, N)
     b = rng.uniform(0.0, w.b_max, N)
     q1 = rng.uniform(-1.0, 1.0, N)
-    omega = matsubara(w.beta, K)
+    if axis not in ("matsubara", "real"):
+        raise ValueError("axis must be 'matsubara' or 'real'")
+    omega = matsubara(w.beta, K) if axis == "matsubara" else real_grid(w.t, K)
     V = trap_potential(w.L, w.trap)
-    sign = np.sign(omega)[:, None]
+    sign = np.sign(omega)[:, None] if axis == "matsubara" else np.ones((K, 1))
     sigma = a[None, :] - 1j * b[None, :] * sign
     return omega, V, np.ascontiguousarray(sigma.astype(np.complex128)), q1
 

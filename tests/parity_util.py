@@ -23,8 +23,8 @@ def plan_for(w, precision=D.DYSON_FP64, K=None, **kw):
     return D.Plan(w.L, w.t, w.mu, w.p, w.k, precision, max_freqs=K or w.K, **kw)
 
 
-def oracle_parts(w, omega_k, V, sigma_k):
-    z = O.dyson_diagonal(omega_k, w.mu, V, sigma_k)
+def oracle_parts(w, omega_k, V, sigma_k, eta=0.0):
+    z = O.axis_diagonal(omega_k, w.mu, V, sigma_k, eta)
     subs = O.Subdomains(w.L, OPEN, w.t, z, w.p)
     full = O.FullLattice(w.L, OPEN, w.t, z)
     return subs, (lambda q: full.solve(q) - subs.solve(q))

@@ -92,6 +92,15 @@ def test_wide_slices_within_limits(lib):
     assert D.dyson_plan_footprint(g) > 0
 
 
+def test_real_axis_eta_validated(lib):
+    g = D.make_geometry((16, 16), p=2, k_max=4, max_freqs=1, eta=-0.1)
+    with pytest.raises(D.DysonError) as e:
+        D.dyson_plan_footprint(g)
+    assert e.value.code == -1
+    g.eta = 0.05
+    assert D.dyson_plan_footprint(g) > 0
+
+
 def test_footprint(lib):
     g = D.make_geometry((128, 128), p=4, k_max=32, max_freqs=64)
     b = D.dyson_plan_footprint(g)

@@ -387,3 +387,53 @@ def test_inputs_reproducible_and_physical():
     assert V[0] == pytest.approx(0.01 * 2 * 7.5 ** 2)
     z = 1j * omega[:, None] - V[None] - sigma
     assert np.all(z.imag > 0)
+
+
+# ------------------------------------------------------------------ real frequency axis
+
+def test_real_axis_closed_form_dense():
+    """Real axis (i w -> w + i eta): homogeneous periodic lattice,
+    G_ii = (1/N) sum_q 1/(w + i eta + mu - Sigma - eps_q)."""
+    L = (6, 5)
+    w, eta, mu, sig = 0.7, 0.05, 0.2, 0.4 - 0.3j
+    z = O.dyson_diagonal_real(w, eta, mu, np.zeros(30), np.full(30, sig))
+    t = -1.0
+    qs = [2 * np.pi * np.arange(n) / n for n in L]
+    eps = -2 * t * (np.cos(qs[0])[:, None] + np.cos(qs[1])[None, :])
+    ref = np.mean(1.0 / (w + 1j * eta + mu - sig - eps))
+    got = O.dense_diag_inverse(L, (True, True, False), t, z)
+    assert np.max(np.abs(got - ref) / abs(ref)) < 1e-12
+
+
+def test_real_axis_spectral_weight():
+    """Retarded G on the real axis: A_i(w) = -Im G_ii(w) / pi >= 0 and, for an open
+    lattice with Sigma = 0, integrates to 1 up to the Lorentzian tails outside the
+    window: for a level e the weight in [-W, W] is (atan((W-e)/eta) + atan((W+e)/eta)) / pi."""
+    L = (5, 4)
+    eta, W = 0.05, 30.0
+    ws = np.linspace(-W, W, 20001)
+    N = O.site_count(L)
+    A = np.zeros((ws.size, N))
+    for n, w in enumerate(ws):
+        z = O.dyson_diagonal_real(w, eta, 0.0, np.zeros(N), np.zeros(N))
+        A[n] = -O.exact_diag(L, (False, False, False), -1.0, z).imag / np.pi
+    assert A.min() >= 0.0
+    weight = np.trapezoid(A, ws, axis=0)
+    # eigenvalues of the open-lattice hopping matrix: every site sees all levels
+    ks = [np.pi * np.arange(1, n + 1) / (n + 1) for n in L]
+    lv = (-2.0 * (np.cos(ks[0])[:, None] + np.cos(ks[1])[None, :])).ravel()
+    tails = (np.arctan((W - lv) / eta) + np.arctan((W + lv) / eta)) / np.pi
+    lo, hi = tails.min(), tails.max()
+    assert np.all(weight > lo - 1e-4) and np.all(weight < hi + 1e-4)
+
+
+def test_real_axis_lowrank_terminated_is_exact():
+    """The low-rank method on the real axis: with k past closure it returns the exact diagonal."""
+    w = I.Workload("r", (10, 9), -1.0, 0.0, 0.01, 0.5, 10.0, 2, 2, 12, 5)
+    omega, V, sigma, q1 = I.make_inputs(w, axis="real")
+    for k in range(2):
+        z = O.dyson_diagonal_real(omega[k], 0.1, w.mu, V, sigma[k])
+        ex = O.exact_diag(w.L, (False, False, False), w.t, z)
+        lr = O.lowrank_diag(w.L, (False, False, False), w.t, w.mu, V, sigma[k], omega[k], q1,
+                            w.p, w.k, eta=0.1)
+        assert np.max(np.abs(lr - ex) / np.abs(ex)) < 1e-10
