@@ -93,6 +93,42 @@ __host__ __device__ __forceinline__ cxd csqrt_principal(cxd z) {
 template <typename R, typename S>
 __host__ __device__ __forceinline__ cx<R> cconv(cx<S> a) { return {(R)a.x, (R)a.y}; }
 
+// Precision conversions by integer operations on the IEEE-754 bit patterns.
+// The hardware conversions between binary64 and binary32 issue on the FP64
+// pipe, which on this part runs at ~1/64 of the FP32 rate (ncu: FP64 pipe 92 %
+// busy in the complex64 stencil with hardware conversions).
+//   d2f_bits: binary64 -> binary32, round to nearest even; results below the
+//             binary32 normal range flush to a signed zero, overflow gives inf,
+//             NaN stays NaN.
+//   f2d_bits: binary32 -> binary64, exact for normal numbers; binary32
+//             subnormals flush to a signed zero.
+__device__ __forceinline__ float d2f_bits(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned sign = hi & 0x80000000u;
+  const int ed = (int)((hi >> 20) & 0x7ffu);
+  const int e = ed - 1023 + 127;
+  unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);      // top 23 of the 52 mantissa bits
+  const unsigned rest = lo & 0x1fffffffu;                  // the 29 bits dropped
+  unsigned out = ((unsigned)e << 23) | m;
+  out += (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) ? 1u : 0u;   // carry may reach inf
+  if (e >= 255) out = 0x7f800000u;
+  if (e <= 0) out = 0u;
+  if (ed == 0x7ff) out = 0x7f800000u | (((hi & 0xfffffu) | lo) ? 0x400000u : 0u);
+  return __uint_as_float(sign | out);
+}
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned sign = u & 0x80000000u;
+  const unsigned ef = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+  unsigned hi = sign | ((ef + (1023u - 127u)) << 20) | (m >> 3), lo = m << 29;
+  if (ef == 0u) hi = sign, lo = 0u;
+  if (ef == 0xffu) hi = sign | 0x7ff00000u | (m >> 3), lo = m << 29;
+  return __longlong_as_double((long long)(((unsigned long long)hi << 32) | lo));
+}
+__device__ __forceinline__ cxf c2f_bits(cxd a) { return {d2f_bits(a.x), d2f_bits(a.y)}; }
+__device__ __forceinline__ cxd c2d_bits(cxf a) { return {f2d_bits(a.x), f2d_bits(a.y)}; }
+
 // ---------------------------------------------------------------- geometry
 struct Geo {
   int dim;        // 2 or 3

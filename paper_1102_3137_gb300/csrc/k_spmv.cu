@@ -8,8 +8,8 @@
 // row and one plane away are 16-byte or 8-byte loads, coalesced over tx, and
 // the grid (x pairs, rows, frequencies) needs no per-site division.  The
 // FP64 inputs (Sigma, V) are converted first and the diagonal is formed in
-// R: in the complex64 form the only FP64 work is those conversions (FP64
-// arithmetic runs at 1/64 of FP32 here).
+// R; in the complex64 form the conversions are integer operations on the bit
+// patterns (d2f_bits), so nothing runs on the FP64 pipe (1/64 of FP32 here).
 #include "dyson_common.cuh"
 
 namespace {
@@ -64,9 +64,13 @@ __global__ void __launch_bounds__(256) k_spmv(Geo g, const double* __restrict__ 
   if (yi < Ly - 1) pair(n + Lx);
   if (zi > 0) pair(n - LxLy);
   if (zi < Lz - 1) pair(n + LxLy);
+  auto cvt = [](double v) -> R {
+    if constexpr (sizeof(R) == 4) return d2f_bits(v);   // integer unit, not the FP64 pipe
+    else return v;
+  };
   auto diag = [&](int m) {
     const cxd s = sk[m];
-    const R vr = (R)V[m], sr = (R)s.x, si = (R)s.y;
+    const R vr = cvt(V[m]), sr = cvt(s.x), si = cvt(s.y);
     return real_axis ? C{wr + mur - vr - sr, er - si} : C{mur - vr - sr, wr - si};
   };
   C* yk = y + (size_t)kf * N;

@@ -235,15 +235,25 @@ __device__ void sweep_chunked(const Geo& g, int i, const SweepArgs<R>& a, cx<R>*
 
 // Pre-pass of a sweep (all threads): the right-hand side rows in precision R
 // into the row buffer yb [Lx][W] (zero on padding columns).
+// In complex64 the FP64 right-hand side is converted by integer operations
+// (d2f_bits) and scaled in FP32, so the pass issues nothing on the FP64 pipe;
+// the scale only keeps the values inside the FP32 range, so its product is
+// taken in FP32 whenever it is itself well inside that range.
 template <typename R>
 __device__ __forceinline__ void sweep_prepass(const Geo& g, int i, const SweepArgs<R>& a, cx<R>* yb) {
   const int W = g.W, Lx = g.Lx, T = g.T, w = T * g.h[i], nrow = Lx * W;
   const R t = (R)g.t;
+  const double as = fabs(a.in_scale);
+  const bool fast = sizeof(R) == 4 && as > 1e-30 && as < 1e30;
+  const R scf = (R)a.in_scale;
   for (int e = threadIdx.x; e < nrow; e += DY_THREADS) {
     const int s = e / W, j = e - s * W;
     cxd v = {0, 0};
     if (j < w) {
-      if (a.src) {
+      if (a.src && fast) {
+        if constexpr (sizeof(R) == 4) yb[e] = scf * c2f_bits(a.src[e]);
+        continue;
+      } else if (a.src) {
         v = a.in_scale * a.src[e];
       } else {
         cx<R> u = {0, 0};
@@ -259,16 +269,28 @@ __device__ __forceinline__ void sweep_prepass(const Geo& g, int i, const SweepAr
 
 // Post-pass of a sweep (all threads): the solution rows x_s in yb to the FP64
 // outputs and the boundary-row copies.
+// In complex64 the scale is applied in FP32 and the value widened by integer
+// operations (f2d_bits); only the accumulating add/subtract into the FP64
+// output runs on the FP64 pipe.
 template <typename R>
 __device__ __forceinline__ void sweep_postpass(const Geo& g, int i, const SweepArgs<R>& a,
                                                const cx<R>* yb) {
   const int W = g.W, Lx = g.Lx, T = g.T, w = T * g.h[i], nrow = Lx * W;
+  const double os = fabs(a.out_scale);
+  const bool fast = sizeof(R) == 4 && os > 1e-30 && os < 1e30;
+  const R scf = (R)a.out_scale;
   for (int e = threadIdx.x; e < nrow; e += DY_THREADS) {
     const int s = e / W, j = e - s * W;
     if (j >= w) continue;
     const cx<R> xr = yb[e];
     if (a.dst) {
-      const cxd xd = a.out_scale * cconv<double>(xr);
+      cxd xd;
+      if constexpr (sizeof(R) == 4) {
+        if (fast) xd = c2d_bits(scf * xr);
+        else xd = a.out_scale * cconv<double>(xr);
+      } else {
+        xd = a.out_scale * cconv<double>(xr);
+      }
       cxd* d = a.dst + e;
       if (a.dst_op == 0) *d = xd;
       else if (a.dst_op == 1) *d = *d + xd;
