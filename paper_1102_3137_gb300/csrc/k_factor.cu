@@ -23,11 +23,16 @@ __device__ __forceinline__ bool slice_adjacent(int r, int c, int T) {
   return tr_r == tr_c && abs(sl_r - sl_c) == 1;
 }
 
-// In-place Gauss-Jordan inverse of the W x W matrix A (row-major, shared).
-// Step k: W threads cache the pivot row scaled by the pivot inverse in prow
-// (with the pivot inverse itself at prow[k]) and the pivot column in fcol;
-// every other entry then has one owner thread and needs one complex FMA, so
-// a step is W^2 FMAs and W reciprocals (not one reciprocal per thread).
+// In-place inverse of the complex symmetric W x W matrix A (row-major, shared)
+// by the symmetric sweep operator (symmetric Gauss-Jordan): sweeping pivot k
+// maps a_kk -> -1/a_kk, a_rk, a_kr -> a_rk / a_kk and the rest to
+// a_rc - a_rk a_kc / a_kk, which keeps the matrix symmetric, so only the upper
+// triangle is updated (W^2/2 complex FMAs per step, half of plain
+// Gauss-Jordan); after all W pivots it holds -A^-1.  Step k: W threads cache
+// column k unscaled in prow and scaled by the pivot inverse in fcol (with
+// -1/a_kk at fcol[k]); every other entry has one owner thread.  Every block
+// inverted here is complex symmetric (D_s and the g_s are), without pivoting
+// because Im A is positive definite (leading minors never vanish).
 template <typename R>
 __device__ void gj_invert(cx<R>* A, int W, cx<R>* prow, cx<R>* fcol) {
   const int n = W * W;
@@ -35,18 +40,27 @@ __device__ void gj_invert(cx<R>* A, int W, cx<R>* prow, cx<R>* fcol) {
     __syncthreads();                         // step k-1 finished by every thread
     for (int e = threadIdx.x; e < W; e += DY_THREADS) {
       const cx<R> piv = cinv(A[k * W + k]);
-      prow[e] = (e == k) ? piv : A[k * W + e] * piv;
-      fcol[e] = A[e * W + k];
+      const cx<R> a = (e < k) ? A[e * W + k] : A[k * W + e];   // a_ek from the upper triangle
+      prow[e] = a;
+      fcol[e] = (e == k) ? -piv : a * piv;
     }
     __syncthreads();
     for (int e = threadIdx.x; e < n; e += DY_THREADS) {
       const int r = e / W, c = e - r * W;
-      cx<R> v;
-      if (r == k) v = prow[c];                        // scaled pivot row; piv at c = k
-      else if (c == k) v = -(fcol[r] * prow[k]);
-      else v = cfma(-fcol[r], prow[c], A[e]);   // 4 FP64 FMAs, not a product and a difference
-      A[e] = v;
+      if (c < r) continue;
+      if (r == k || c == k) A[e] = fcol[r == k ? c : r];
+      else A[e] = cfma(-fcol[r], prow[c], A[e]);
     }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < n; e += DY_THREADS) {   // -(-A^-1), upper triangle
+    const int r = e / W, c = e - r * W;
+    if (c >= r) A[e] = -A[e];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < n; e += DY_THREADS) {   // mirror to the lower triangle
+    const int r = e / W, c = e - r * W;
+    if (c < r) A[e] = A[c * W + r];
   }
   __syncthreads();
 }
@@ -239,27 +253,37 @@ __global__ void __launch_bounds__(DY_THREADS) k_factor(Geo g, Bufs b) {
 // DY_FACTOR_CTAS CTAs walks the (subdomain, frequency) units, so the workspace
 // is bounded by the grid, not by K.
 
-// In-place Gauss-Jordan on a global W x W matrix.  Step k caches pivot row k
-// and the column multipliers A[r][k] / A[k][k] on chip; every other element is
-// then owned by exactly one thread, so one barrier per phase suffices.
+// In-place inverse of a complex symmetric global W x W matrix by the
+// symmetric sweep operator (see gj_invert): the upper triangle only, then
+// negation and mirror.  Step k caches column k (unscaled in prow, scaled by
+// the pivot inverse in fcol, -1/a_kk at fcol[k]) on chip.
 __device__ void gj_invert_global(cxd* A, int W, cxd* prow, cxd* fcol) {
   const int n = W * W;
   for (int k = 0; k < W; ++k) {
     __syncthreads();                         // step k-1 finished by every thread
-    const cxd piv = cinv(A[(size_t)k * W + k]);
     for (int e = threadIdx.x; e < W; e += DY_THREADS) {
-      prow[e] = A[(size_t)k * W + e];
-      fcol[e] = A[(size_t)e * W + k] * piv;
+      const cxd piv = cinv(A[(size_t)k * W + k]);
+      const cxd a = (e < k) ? A[(size_t)e * W + k] : A[(size_t)k * W + e];
+      prow[e] = a;
+      fcol[e] = (e == k) ? -piv : a * piv;
     }
     __syncthreads();
     for (int e = threadIdx.x; e < n; e += DY_THREADS) {
       const int r = e / W, c = e - r * W;
-      cxd v;
-      if (r == k) v = (c == k) ? piv : prow[c] * piv;
-      else if (c == k) v = -fcol[r];
-      else v = cfma(-fcol[r], prow[c], A[e]);   // 4 FP64 FMAs, not a product and a difference
-      A[e] = v;
+      if (c < r) continue;
+      if (r == k || c == k) A[e] = fcol[r == k ? c : r];
+      else A[e] = cfma(-fcol[r], prow[c], A[e]);
     }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < n; e += DY_THREADS) {
+    const int r = e / W, c = e - r * W;
+    if (c >= r) A[e] = -A[e];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < n; e += DY_THREADS) {
+    const int r = e / W, c = e - r * W;
+    if (c < r) A[e] = A[(size_t)c * W + r];
   }
   __syncthreads();
 }
