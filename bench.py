@@ -410,14 +410,18 @@ def run_reference(a, rank, world):
 
 
 # ----------------------------------------------------------------- serving stream
-SERVE_SIZES = [((64, 64), 4, 32), ((128, 128), 4, 32)]
+# lattices of the serving stream with their (p, k); 48^3 (p = 8 gives slice width 288 > 256)
+# is not taken
+SERVE_SIZES = [((64, 64), 4, 32), ((128, 128), 4, 32), ((256, 256), 8, 48), ((24, 24, 24), 4, 48)]
+SERVE_KMAX = 128
 
 
 def run_serving(a):
     """Open-loop Poisson arrivals of Dyson solves from simulated IDMFT loops.
 
-    Lattices drawn from 64^2 (p=4, k=32) and 128^2 (p=4, k=32), K uniform in
-    [8, 32], a fresh seeded self-energy per request.  The plain-FP64 capacity
+    Lattices drawn uniformly from 64^2 (p=4, k=32), 128^2 (p=4, k=32), 256^2 (p=8,
+    k=48) and 24^3 (p=4, k=48), K uniform in [16, 128], a fresh seeded self-energy
+    per request; every geometry's plan holds 128 frequencies.  The plain-FP64 capacity
     is measured first by solving every request alone, one after the other;
     the stream then arrives at rate_frac x that capacity and is served by the
     continuous-batching server (mixed form, plans resident and reused).
@@ -434,7 +438,7 @@ def run_serving(a):
     reqs = []
     for n in range(a.requests):
         L, p, k = SERVE_SIZES[int(rng.integers(len(SERVE_SIZES)))]
-        K = int(rng.integers(8, 33))
+        K = int(rng.integers(16, SERVE_KMAX + 1))
         w = I.Workload("serve", L, -1.0, 0.0, 0.01, 0.5, 20.0, K, p, k, 1000 + n)
         omega, V, sigma, q1 = I.make_inputs(w)
         pin = lambda x: torch.from_numpy(x).pin_memory().numpy()
@@ -443,7 +447,7 @@ def run_serving(a):
     work = sum(r["w"].N * r["w"].K for r in reqs)
 
     def serve(prec, arrivals, inflight):
-        srv = D.dyson_server_create(64 << 30, max_inflight=inflight)
+        srv = D.dyson_server_create(96 << 30, max_inflight=inflight)
         t0 = time.perf_counter()
         tickets = []
         for r, ta in zip(reqs, arrivals):
@@ -451,7 +455,7 @@ def run_serving(a):
             if dt > 0:
                 time.sleep(dt)
             w = r["w"]
-            geom = D.make_geometry(w.L, w.t, w.mu, w.p, w.k, prec, max_freqs=32)
+            geom = D.make_geometry(w.L, w.t, w.mu, w.p, w.k, prec, max_freqs=SERVE_KMAX)
             tickets.append(D.dyson_submit(srv, geom, w.K, r["omega"], r["V"], r["sigma"], r["q1"], r["out"]))
         lat = [D.dyson_wait(srv, t)[0] for t in tickets]
         wall = time.perf_counter() - t0
@@ -466,7 +470,8 @@ def run_serving(a):
     mean_work = work / len(reqs)
     out = dict(metric="serving: site-frequencies/s and p50/p99 request latency (continuous batching)",
                unit="site-frequencies/s", requests=len(reqs),
-               config=dict(lattices="64x64 p=4 k=32 | 128x128 p=4 k=32", K="uniform 8..32",
+               config=dict(lattices="64x64 p=4 k=32 | 128x128 p=4 k=32 | 256x256 p=8 k=48 | 24^3 p=4 k=48",
+                           K="uniform 16..128",
                            arrivals="open-loop Poisson, seed 5", served_form="mixed",
                            max_inflight=a.inflight),
                plain_fp64_capacity=capacity, plain_fp64_sequential_wall_s=wall_plain, rates=[])
