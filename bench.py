@@ -251,6 +251,7 @@ def run_ours(a, rank, world, local_rank):
                     per_launch_algorithmic_flops=sw_flops / n_xm)
     roof["share_of_step"] = float(xm.sum() / kms.sum()) if len(kms) else None
     phases = {D.KERNEL_NAMES[int(k)]: round(float(kms[kinds == k].sum()), 3) for k in sorted(set(kinds))}
+    tuning = D.dyson_plan_tuning(plan.handle)
 
     extra = {}
     if rank == 0 and world == 1 and not a.quick:
@@ -272,7 +273,8 @@ def run_ours(a, rank, world, local_rank):
         plain = outf.cpu().numpy()
         rel = np.abs(res - plain) / np.abs(plain)
         extra["err_vs_plain"] = dict(max=float(rel.max()), median=float(np.median(rel)))
-        extra["fp64_plain"] = dict(value=w.K * w.N / (ms_f / 1e3), ms_per_step=ms_f)
+        extra["fp64_plain"] = dict(value=w.K * w.N / (ms_f / 1e3), ms_per_step=ms_f,
+                                   autotuner=D.dyson_plan_tuning(pf.handle))
         pf.close()
         # one frequency per launch vs all frequencies in one batch (same form)
         p1 = D.Plan(w.L, w.t, w.mu, w.p, w.k, prec, max_freqs=1)
@@ -373,7 +375,7 @@ def run_ours(a, rank, world, local_rank):
                     l2="per-step working set > L2: factors + Lanczos basis ~1 GB, no flush",
                     parallelism=f"replicas x{world}"),
         latency_ms=dict(p50=pct(0.50), p99=pct(0.99)),
-        roofline=roof, phases_ms_last_step=phases,
+        roofline=roof, phases_ms_last_step=phases, autotuner=tuning,
         inner_iterations_per_solve=float(np.mean(info["iters"]) / max(1, w.k)),
         status_flags=sorted({int(x) for x in status}),
         cpu_baseline=({k: v for k, v in cpu.items() if k != "wall_s"} if cpu else None),

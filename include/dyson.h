@@ -136,6 +136,19 @@ int dyson_plan_create(const dyson_geometry* geom, dyson_plan* out);
 int dyson_plan_destroy(dyson_plan plan);
 
 /*
+ * Autotuner result (batched kernels' tile choice).  At a plan's first
+ * dyson_solve with p > 1, before its graph is captured, the library times one
+ * X-matvec launch for each copy-ring configuration the geometry admits (ring
+ * slots; rows per streamed chunk when W > 64) on the caller's inputs and keeps
+ * the fastest.  Reports the configuration in use (*ring_slots, *chunk_rows),
+ * how many were timed (*candidates, 0 before the first solve) and the launch
+ * times of the shared-memory heuristic's choice and of the kept one (ms).
+ * Any output pointer may be NULL.  The paper has no counterpart.
+ */
+int dyson_plan_tuning(dyson_plan plan, int* ring_slots, int* chunk_rows, int* candidates,
+                      float* ms_heuristic, float* ms_best);
+
+/*
  * diag(G(i w_k)) for K frequencies (Eq. 1 solved by the method of Sec. 2.3):
  *   omega  [K]         real Matsubara frequencies w_k
  *   V      [N]         real local potential V_i

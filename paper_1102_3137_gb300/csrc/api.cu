@@ -187,6 +187,9 @@ struct dyson_plan_s {
   std::map<int, cudaGraphExec_t> graphs;
   bool use_graph;
   bool profile;                    // bracket every kernel with timing events
+  bool tuned;                      // the copy-ring configuration has been timed
+  int tune_candidates;             // configurations timed
+  float tune_ms_heuristic, tune_ms_best;   // one X-matvec launch with each
   std::vector<cudaEvent_t> evs;    // 2 per profiled kernel
   std::vector<int> ev_kind;        // DYSON_KERNEL_* of each profiled kernel
   int n_prof;                      // profiled kernels in the last enqueued sequence
@@ -315,6 +318,59 @@ int enqueue_solve(dyson_plan p, int K, cudaStream_t s, bool cap) {
   return DYSON_OK;
 }
 
+// Autotuner (batched kernels' tile choice): at the first solve of a plan with
+// an interface, on the caller's staged inputs, run init, factorization and
+// preconditioner once, then time one X-matvec launch (after one untimed) for
+// each copy-ring configuration the geometry admits (ring slots; chunk height
+// for W > 64) and keep the fastest for every later launch and captured graph.
+int autotune(dyson_plan p, int K, cudaStream_t s) {
+  p->tuned = true;
+  if (p->g.p < 2) return DYSON_OK;
+  int S[16], CR[16];
+  const int n = dyson_internal_ring_candidates(p->g, p->mixed, S, CR, 16);
+  p->tune_candidates = n;
+  if (n < 2) return DYSON_OK;
+  Geo& g = p->g;
+  LK(launch_init(g, p->b, K, s));
+  if (p->mixed) LK((launch_factor<double, float>(g, p->b, K, s)));
+  else LK((launch_factor<double, double>(g, p->b, K, s)));
+  if (p->mixed) LK(launch_precond<float>(g, p->b, K, s));
+  else LK(launch_precond<double>(g, p->b, K, s));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  int best = 0;
+  float best_ms = 0.f;
+  int rc = DYSON_OK;
+  for (int c = 0; c < n && rc == DYSON_OK; ++c) {
+    g.ring_S = S[c];
+    g.ring_CR = CR[c];
+    cudaError_t e = p->mixed ? launch_xmatvec<float>(g, p->b, K, 0, 1, s) : launch_xmatvec<double>(g, p->b, K, 0, 0, s);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+    if (e == cudaSuccess)
+      e = p->mixed ? launch_xmatvec<float>(g, p->b, K, 0, 1, s) : launch_xmatvec<double>(g, p->b, K, 0, 0, s);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) {
+      rc = fail(DYSON_E_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+      break;
+    }
+    if (c == 0) p->tune_ms_heuristic = ms;
+    if (c == 0 || ms < best_ms) {
+      best_ms = ms;
+      best = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  g.ring_S = S[best];
+  g.ring_CR = CR[best];
+  p->tune_ms_best = best_ms;
+  return rc;
+}
+
 int get_graph(dyson_plan p, int K, cudaGraphExec_t* out) {
   auto it = p->graphs.find(K);
   if (it != p->graphs.end()) {
@@ -429,6 +485,9 @@ int dyson_plan_create(const dyson_geometry* geom, dyson_plan* out) {
   b.off2 = p->g.penta ? at<cxd>(p, B_OFF2) : nullptr;
   p->status_d = at<int>(p, B_STATUS);
   p->profile = false;
+  p->tuned = false;
+  p->tune_candidates = 0;
+  p->tune_ms_heuristic = p->tune_ms_best = 0.f;
   p->n_prof = 0;
   *out = p;
   return DYSON_OK;
@@ -458,6 +517,7 @@ int dyson_internal_solve_enqueue(dyson_plan p, int K, const double* omega, const
   if (!q1 || !diagG) return fail(DYSON_E_BAD_ARG, "q1 and diagG must not be NULL");
   cudaStream_t s = (cudaStream_t)stream;
   if ((rc = stage_inputs(p, K, omega, V, sigma, q1, s))) return rc;
+  if (!p->tuned && (rc = autotune(p, K, s))) return rc;
   if (p->use_graph) {
     cudaGraphExec_t ex;
     if ((rc = get_graph(p, K, &ex))) return rc;
@@ -479,6 +539,20 @@ int dyson_solve(dyson_plan p, int K, const double* omega, const double* V, const
   int rc = dyson_internal_solve_enqueue(p, K, omega, V, sigma, q1, diagG, status, mem_kind, stream);
   if (rc) return rc;
   return finish(mem_kind, (cudaStream_t)stream);
+}
+
+int dyson_plan_tuning(dyson_plan p, int* ring_slots, int* chunk_rows, int* candidates,
+                      float* ms_heuristic, float* ms_best) {
+  int rc;
+  if ((rc = check_plan(p))) return rc;
+  int S = 0, CR = 0;
+  dyson_internal_ring_plan(p->g, p->mixed, &S, &CR);
+  if (ring_slots) *ring_slots = S;
+  if (chunk_rows) *chunk_rows = CR;
+  if (candidates) *candidates = p->tuned ? p->tune_candidates : 0;
+  if (ms_heuristic) *ms_heuristic = p->tune_ms_heuristic;
+  if (ms_best) *ms_best = p->tune_ms_best;
+  return DYSON_OK;
 }
 
 int dyson_solve_info(dyson_plan p, int K, double* alpha_beta, int* steps, int* iters, int* refines) {

@@ -152,6 +152,8 @@ struct Geo {
   int ylayer[DY_MAXP]; // slow coordinate of interface layer l
   int penta;           // interface preconditioner keeps the distance-2 coupling (2D strips, W <= 64)
   double eta;          // 0: Matsubara axis; > 0: real axis w + i eta
+  int ring_S;          // copy-ring slots chosen by the autotuner (0: shared-memory heuristic)
+  int ring_CR;         // rows per streamed chunk chosen by the autotuner (W > 64; 0: heuristic)
 };
 
 // Device buffers of one plan; every per-frequency array is [K_cap][...].
@@ -221,6 +223,11 @@ size_t dyson_internal_plan_bytes(dyson_plan_s* p);
 // Dynamic shared memory of the sweep-based solver kernels for this geometry in
 // the given form; 0 when the slice width and x extent do not fit on chip.
 size_t dyson_internal_sweep_smem(const Geo& g, bool mixed);
+// Copy-ring configurations the autotuner times for this geometry and form:
+// up to max pairs (slots, chunk rows), the shared-memory heuristic's first.
+int dyson_internal_ring_candidates(const Geo& g, bool mixed, int* S, int* CR, int max);
+// The copy-ring configuration the kernels use for this geometry (slots, chunk rows).
+void dyson_internal_ring_plan(const Geo& g, bool mixed, int* S, int* CR);
 
 // ---------------------------------------------------------------- host launchers
 template <typename R, typename S>

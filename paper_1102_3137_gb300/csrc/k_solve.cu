@@ -190,6 +190,16 @@ size_t dyson_internal_sweep_smem(const Geo& g, bool mixed) {
   return mixed ? sweep_smem<float>(g) : sweep_smem<double>(g);
 }
 
+void dyson_internal_ring_plan(const Geo& g, bool mixed, int* S, int* CR) {
+  const RingPlan rp = mixed ? ring_plan<float>(g) : ring_plan<double>(g);
+  *S = rp.S;
+  *CR = rp.CR;
+}
+
+int dyson_internal_ring_candidates(const Geo& g, bool mixed, int* S, int* CR, int max) {
+  return mixed ? ring_candidates<float>(g, S, CR, max) : ring_candidates<double>(g, S, CR, max);
+}
+
 
 
 cudaError_t launch_lanczos(const Geo& g, const Bufs& b, int K, int j, cudaStream_t st) {

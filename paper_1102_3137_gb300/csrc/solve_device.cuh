@@ -1363,12 +1363,59 @@ __host__ __device__ inline RingPlan ring_plan(int W, int Lx) {
   rp.smem = rp.CR ? (size_t)rp.S * rp.CR * W * cs + (size_t)rp.zw * cs + rp.ybuf : 0;
   return rp;
 }
+// The plan of a geometry: the heuristic above, or the autotuner's choice of
+// slots (and chunk rows for W > 64) with the same row buffer and z area.
+constexpr size_t SMEM_LIMIT = 225 * 1024;   // dynamic shared memory per CTA, below the 227 KB cap
 template <typename R>
-__host__ __device__ inline size_t ybuf_bytes(int W, int Lx) { return ring_plan<R>(W, Lx).ybuf; }
+__host__ __device__ inline RingPlan ring_plan(const Geo& g) {
+  RingPlan rp = ring_plan<R>(g.W, g.Lx);
+  if (g.ring_S > 0 && rp.CR > 0) {
+    rp.S = g.ring_S;
+    if (g.W > DY_MAXW_SMEM && g.ring_CR > 0) rp.CR = g.ring_CR;
+    rp.smem = (size_t)rp.S * rp.CR * g.W * sizeof(cx<R>) + (size_t)rp.zw * sizeof(cx<R>) + rp.ybuf;
+  }
+  return rp;
+}
+// Configurations the autotuner times: the heuristic's first, then every slot
+// count 2..MAX_STAGES (even in the two-chain complex64 form) that fits, and
+// for W > 64 the chunk heights (divisors of W) with the most slots that fit.
 template <typename R>
-__host__ __device__ inline int ring_stages(int W, int Lx) { return ring_plan<R>(W, Lx).S; }
-template <typename R>
-__host__ __device__ inline size_t solver_smem(int W, int Lx) { return ring_plan<R>(W, Lx).smem; }
+inline int ring_candidates(const Geo& g, int* S, int* CR, int max) {
+  const RingPlan h = ring_plan<R>(g.W, g.Lx);
+  if (h.CR == 0 || max < 1) return 0;
+  int n = 0;
+  S[n] = h.S;
+  CR[n] = h.CR;
+  ++n;
+  const size_t cs = sizeof(cx<R>), fixed = (size_t)h.zw * cs + h.ybuf;
+  auto fits = [&](int s, int cr) { return (size_t)s * cr * g.W * cs + fixed <= SMEM_LIMIT; };
+  auto add = [&](int s, int cr) {
+    for (int k = 0; k < n; ++k)
+      if (S[k] == s && CR[k] == cr) return;
+    if (n < max && fits(s, cr)) {
+      S[n] = s;
+      CR[n] = cr;
+      ++n;
+    }
+  };
+  if (g.W <= DY_MAXW_SMEM) {
+    const int step = sizeof(R) == 4 ? 2 : 1;        // two chains split the ring evenly
+    for (int s = 2; s <= MAX_STAGES; s += step) add(s, g.W);
+  } else {
+    for (int cr = g.W; cr >= 1; --cr) {
+      if (g.W % cr) continue;
+      int best = 0;
+      for (int s = MAX_STAGES; s >= 2; --s)
+        if (fits(s, cr)) {
+          best = s;
+          break;
+        }
+      if (best >= 3) add(best, cr);
+      if (n >= max) break;
+    }
+  }
+  return n;
+}
 
 // ---------------------------------------------------------------- kernels
 // u = X q_j  (Sec. 2.3 Eqs. 6-8), with u = v - w computed as the solution of
@@ -1390,7 +1437,7 @@ __global__ void __launch_bounds__(DY_THREADS, 2) k_xmatvec(Geo g, Bufs b, int j,
   if (st[ST_DONE]) return;                 // same value in every CTA of the cluster
   Pipe pp;
   pp.bar = bars;
-  const RingPlan rp = ring_plan<R>(g.W, g.Lx);
+  const RingPlan rp = ring_plan<R>(g);
   pp.S = rp.S;
   pp.CR = rp.CR;
   pp.ring = smem_raw;
@@ -1540,7 +1587,7 @@ __global__ void __launch_bounds__(DY_THREADS, 2) k_bsolve(Geo g, Bufs b, const c
   const size_t nsub = (size_t)g.Lx * g.W;
   Pipe pp;
   pp.bar = bars;
-  const RingPlan rp = ring_plan<R>(g.W, g.Lx);
+  const RingPlan rp = ring_plan<R>(g);
   pp.S = rp.S;
   pp.CR = rp.CR;
   pp.ring = smem_raw;
@@ -1587,7 +1634,7 @@ cudaError_t launch_cluster(Kern kern, dim3 grid, int cx_, size_t smem, cudaStrea
 }
 
 template <typename R>
-size_t sweep_smem(const Geo& g) { return solver_smem<R>(g.W, g.Lx); }
+size_t sweep_smem(const Geo& g) { return ring_plan<R>(g).smem; }
 // the WF of the kernels for this geometry: every slice wider than 64 takes the
 // streamed form (CR may equal W there); the complex64 two-chain form is
 // compiled for W <= 16, 32 and 64 (fully unrolled block products); the FP64

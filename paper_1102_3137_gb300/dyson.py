@@ -77,6 +77,7 @@ def load(path: str = LIB_PATH):
         "dyson_plan_footprint": ([C.POINTER(dyson_geometry), C.POINTER(C.c_size_t)], I),
         "dyson_plan_create": ([C.POINTER(dyson_geometry), C.POINTER(P)], I),
         "dyson_plan_destroy": ([P], I),
+        "dyson_plan_tuning": ([P, P, P, P, P, P], I),
         "dyson_solve": ([P, I, P, P, P, P, P, P, I, P], I),
         "dyson_solve_info": ([P, I, P, P, P, P], I),
         "dyson_apply_H": ([P, I, P, P, P, P, P, I, P], I),
@@ -193,6 +194,16 @@ def dyson_partition(geom):
     dd2nat = np.zeros(ndd.value, dtype=np.int32)
     _check(lib.dyson_partition(C.byref(geom), None, None, None, dd2nat.ctypes.data))
     return heights[:geom.p].copy(), m.value, dd2nat
+
+
+def dyson_plan_tuning(plan):
+    """(ring slots, chunk rows, configurations timed, heuristic ms, kept ms) of a plan."""
+    s, cr, n = C.c_int(), C.c_int(), C.c_int()
+    mh, mb = C.c_float(), C.c_float()
+    _check(load().dyson_plan_tuning(plan, C.addressof(s), C.addressof(cr), C.addressof(n),
+                                    C.addressof(mh), C.addressof(mb)))
+    return dict(ring_slots=s.value, chunk_rows=cr.value, candidates=n.value,
+                ms_heuristic=mh.value, ms_best=mb.value)
 
 
 def dyson_plan_footprint(geom):

@@ -255,3 +255,22 @@ def test_square128_full_batch_sampled(precision, tol):
         eps = max(float(np.linalg.norm(u[0] - ux) / np.linalg.norm(ux)), 1e-15)
         base, sens = oracle_sensitivity(w, subs, X, q1, eps)
         assert relerr(out[k], base) <= max(tol, 10 * sens), (k, eps, sens)
+
+
+@pytest.mark.parametrize("precision", [D.DYSON_FP64, D.DYSON_MIXED])
+def test_autotuner_times_candidates_and_keeps_results(precision):
+    """The first solve times the copy-ring configurations; the ring depth does not
+    change the arithmetic, so every configuration gives the same bits."""
+    w = wl((40, 64), 4, 8, K=4, seed=31)
+    omega, V, sigma, q1 = I.make_inputs(w)
+    pl = plan_for(w, precision)
+    assert D.dyson_plan_tuning(pl.handle)["candidates"] == 0
+    ref = pl.solve(omega, V, sigma, q1)
+    t = D.dyson_plan_tuning(pl.handle)
+    assert t["candidates"] >= 2 and t["ring_slots"] >= 2
+    assert 0 < t["ms_best"] <= t["ms_heuristic"]
+    # the subdomain solve path runs with the tuned configuration too
+    for _ in range(2):
+        assert np.array_equal(pl.solve(omega, V, sigma, q1), ref)
+    other = plan_for(w, precision)
+    assert np.array_equal(other.solve(omega, V, sigma, q1), ref)
