@@ -29,6 +29,10 @@ Readings of the paper taken here (the paper is silent or garbled there):
     breakdown when |r^T r| <= 1e-14 ||r||_2^2                 (Sec. 2.1, 2.3)
   * the H solve of Eq. 6 is a direct block-LU solve of the full lattice
     (the paper does not say which solver it used).
+  * block Lanczos (not in the paper; for degenerate spectra of X): blocks are
+    split by a column-by-column bilinear Gram-Schmidt QR (applied twice);
+    a column whose pivot falls to 1e-12 max|T| is deflated to zero; the run
+    terminates when a whole new block deflates; k_max counts columns.
 """
 from __future__ import annotations
 
@@ -372,6 +376,101 @@ def cs_lanczos(matvec, q1, k_max: int, term_tol: float = 1e-12, brk_tol: float =
     return acc, np.array(alphas), np.array(betas), Q[:, :steps], status
 
 
+def _bilinear_qr(R, maxT: float, term_tol: float, brk_tol: float):
+    """R = Q B in the bilinear form, column by column (Gram-Schmidt twice).
+
+    Q^T Q = I on the kept columns; a column whose pivot |B_cc| falls to
+    term_tol * maxT is deflated (q_c = 0, B_cc = 0) and takes no further
+    part.  Returns (Q, B, deflated[b], breakdown) where breakdown means
+    (r, r)_C vanished for a column that is not small.
+    """
+    N, nb = R.shape
+    Q = np.zeros((N, nb), dtype=np.complex128)
+    B = np.zeros((nb, nb), dtype=np.complex128)
+    defl = np.zeros(nb, dtype=bool)
+    for c in range(nb):
+        r = R[:, c].copy()
+        for _ in range(2):
+            h = Q[:, :c].T @ r
+            r = r - Q[:, :c] @ h
+            B[:c, c] += h
+        rr = r @ r
+        b = np.sqrt(rr)
+        if abs(b) <= term_tol * maxT:
+            defl[c] = True
+            continue
+        if abs(rr) <= brk_tol * np.vdot(r, r).real:
+            return Q, B, defl, True
+        B[c, c] = b
+        Q[:, c] = r / b
+    return Q, B, defl, False
+
+
+def cs_block_lanczos(matvec, Q1, k_max: int, term_tol: float = 1e-12, brk_tol: float = 1e-14):
+    """Block complex-symmetric Lanczos with (q, u)_C = q^T u.
+
+    Not in the paper: the block form of Sec. 2.1's recurrence, for X whose
+    eigenvalues are degenerate (a single start vector spans only one
+    direction of each eigenspace).  With block size nb = Q1.shape[1]:
+
+        X Q_j = Q_{j-1} B_j^T + Q_j A_j + Q_{j+1} B_{j+1},
+        A_j = Q_j^T X Q_j,   R_j = X Q_j - Q_j A_j - Q_{j-1} B_j^T = Q_{j+1} B_{j+1}
+
+    with R_j re-orthogonalised against every earlier block (CGS2) and split
+    by the bilinear QR above.  T is block tridiagonal (A_j on the diagonal,
+    B_{j+1} below, B_{j+1}^T above), so the diagonal of Q T Q^T takes, per
+    block step, diag(Q_j A_j Q_j^T) + 2 diag(Q_j B_j Q_{j-1}^T) (Eq. 9 per
+    block).  k_max is the rank cap: k_max / nb block steps.  Stops when every
+    column of the next block deflated (invariant subspace: terminated) or on a
+    bilinear breakdown.  The start block is split by the same QR first.
+
+    Returns (diag_QTQ, A[steps], B[steps], Q, status); B[j] couples block j
+    to block j - 1 (B[0] = the start block's factor).
+    """
+    Q1 = np.asarray(Q1, dtype=np.complex128)
+    N, nb = Q1.shape
+    if k_max % nb:
+        raise ValueError("k_max must be a multiple of the block size")
+    nsteps = k_max // nb
+    acc = np.zeros(N, dtype=np.complex128)
+    Qj, B0, defl, brk = _bilinear_qr(Q1, 1.0, 0.0, brk_tol)
+    if brk or defl.any():
+        raise ValueError("start block is not of full rank in the bilinear form")
+    blocks = [Qj]
+    As, Bs = [], [B0]
+    status = STATUS_OK
+    maxT = 0.0
+    for j in range(nsteps):
+        Qj = blocks[j]
+        U = matvec(Qj)
+        A = Qj.T @ U
+        Rj = U - Qj @ A
+        if j > 0:
+            Rj = Rj - blocks[j - 1] @ Bs[j].T
+        Qall = np.concatenate(blocks, axis=1)
+        for _ in range(2):                       # CGS2 in the bilinear form
+            Rj = Rj - Qall @ (Qall.T @ Rj)
+        acc += np.einsum("ic,cd,id->i", Qj, A, Qj)
+        if j > 0:
+            acc += 2.0 * np.einsum("ic,cd,id->i", Qj, Bs[j], blocks[j - 1])
+        As.append(A)
+        maxT = max(maxT, np.abs(A).max())
+        if j == nsteps - 1:
+            break
+        Qn, Bn, defl, brk = _bilinear_qr(Rj, maxT, term_tol, brk_tol)
+        if brk:
+            status = STATUS_BREAKDOWN
+            break
+        if defl.all():
+            status = STATUS_TERMINATED
+            break
+        maxT = max(maxT, np.abs(Bn).max())
+        blocks.append(Qn)
+        Bs.append(Bn)
+    Q = np.concatenate(blocks[:len(As)], axis=1)
+    return acc, np.array(As), np.array(Bs[:len(As)]), Q, status
+
+
 # --------------------------------------------------------------------------
 # The low-rank correction method (Sec. 2.3, Eqs. 4-9)
 # --------------------------------------------------------------------------
@@ -411,6 +510,24 @@ def lowrank_diag(L, periodic, t, mu, V, sigma_k, omega_k, q1, p: int, k_max: int
     if return_info:
         return res, dict(alphas=al, betas=be, steps=len(al), status=status,
                          diagB=subs.diagB, Q=Q)
+    return res
+
+
+def lowrank_diag_block(L, periodic, t, mu, V, sigma_k, omega_k, Q1, p: int, k_max: int,
+                       return_info: bool = False, eta: float = 0.0):
+    """Eq. 9 with the block Lanczos approximation of X (start block Q1, N x nb)."""
+    z = axis_diagonal(omega_k, mu, V, sigma_k, eta)
+    subs = Subdomains(L, periodic, t, z, p)
+    full = FullLattice(L, periodic, t, z)
+
+    def xmatvec_block(Qb):
+        return np.stack([full.solve(Qb[:, c]) - subs.solve(Qb[:, c])
+                         for c in range(Qb.shape[1])], axis=1)   # Eqs. 6-8 per column
+
+    acc, As, Bs, Q, status = cs_block_lanczos(xmatvec_block, Q1, k_max)
+    res = subs.diagB + acc
+    if return_info:
+        return res, dict(A=As, B=Bs, steps=len(As), status=status, diagB=subs.diagB, Q=Q)
     return res
 
 

@@ -437,3 +437,110 @@ def test_real_axis_lowrank_terminated_is_exact():
         lr = O.lowrank_diag(w.L, (False, False, False), w.t, w.mu, V, sigma[k], omega[k], q1,
                             w.p, w.k, eta=0.1)
         assert np.max(np.abs(lr - ex) / np.abs(ex)) < 1e-10
+
+
+# --------------------------------------------------------------------------- block Lanczos
+
+
+def _homogeneous_cube():
+    """3 x 3 x 7 open lattice, constant Sigma, no trap, p = 2: the 3 x 3 interface
+    plane has degenerate eigenvalues of X (the x <-> y swap and the accidental
+    degeneracy of the plane modes cos(pi n1/4) + cos(pi n2/4) = 0 for
+    (1,3), (3,1), (2,2) give an eigenvalue of multiplicity 3)."""
+    L = (3, 3, 7)
+    N = O.site_count(L)
+    V = np.zeros(N)
+    sigma = np.full(N, 0.3 + 0.2j)
+    return L, N, V, sigma, math.pi / 10
+
+
+def _dense_X(L, per, t, z, p):
+    N = z.shape[0]
+    Hinv = np.linalg.inv(O.dense_H(L, per, t, z))
+    subs = O.Subdomains(L, per, t, z, p)
+    return Hinv - np.stack([subs.solve(e) for e in np.eye(N)], 1), Hinv
+
+
+def test_block_lanczos_exact_on_degenerate_spectrum():
+    """A single start vector spans one direction per eigenspace of X, so on a
+    degenerate spectrum the scalar method terminates early and misses part of
+    diag(X); a block of size >= the largest multiplicity reaches the exact
+    diagonal (dense library inverse) at any start block."""
+    L, N, V, sigma, w = _homogeneous_cube()
+    per = [False] * 3
+    z = O.dyson_diagonal(w, 0.0, V, sigma)
+    X, Hinv = _dense_X(L, per, -1.0, z, 2)
+    ev = np.linalg.eigvals(X)
+    ev = ev[np.abs(ev) > 1e-10]
+    assert len(ev) == 9
+    mult = max(int(np.sum(np.abs(ev - e) < 1e-8)) for e in ev)
+    assert mult == 3
+    exact = np.diag(Hinv)
+    rng = np.random.default_rng(11)
+    Q1 = rng.uniform(-1, 1, (N, 3))
+    r1, info1 = O.lowrank_diag(L, per, -1.0, 0.0, V, sigma, w, Q1[:, 0], 2, 12, return_info=True)
+    assert info1["status"] == O.STATUS_TERMINATED and info1["steps"] < 9
+    assert np.max(np.abs(r1 - exact)) / np.max(np.abs(exact)) > 1e-2
+    for seed in (11, 12):
+        Q1 = np.random.default_rng(seed).uniform(-1, 1, (N, 3))
+        rb, info = O.lowrank_diag_block(L, per, -1.0, 0.0, V, sigma, w, Q1, 2, 12, return_info=True)
+        assert np.max(np.abs(rb - exact)) / np.max(np.abs(exact)) < 1e-11
+
+
+def test_block_lanczos_recurrence_and_orthogonality():
+    """X Q_k = Q_k T_k + (last block residual), Q_k^T Q_k = I, A_j = A_j^T,
+    and diag(Q T Q^T) from the recurrence equals the product formed densely."""
+    L, per, p, nb, k = (6, 11), [False, False], 3, 2, 8
+    N = 66
+    rng = np.random.default_rng(5)
+    V = rng.uniform(0, 0.5, N)
+    sigma = rng.uniform(0, 1, N) + 1j * rng.uniform(0.1, 1, N)
+    w, mu = math.pi / 10, 0.2
+    Q1 = rng.uniform(-1, 1, (N, nb))
+    res, info = O.lowrank_diag_block(L, per, -1.0, mu, V, sigma, w, Q1, p, k, return_info=True)
+    assert info["status"] == O.STATUS_OK and info["steps"] == k // nb
+    z = O.dyson_diagonal(w, mu, V, sigma)
+    X, _ = _dense_X(L, per, -1.0, z, p)
+    Q, A, B = info["Q"], info["A"], info["B"]
+    assert np.max(np.abs(Q.T @ Q - np.eye(k))) < 1e-12
+    T = np.zeros((k, k), dtype=complex)
+    for j in range(k // nb):
+        s = slice(nb * j, nb * j + nb)
+        T[s, s] = A[j]
+        assert np.max(np.abs(A[j] - A[j].T)) < 1e-12 * np.max(np.abs(A[j]))
+        if j > 0:
+            sp = slice(nb * (j - 1), nb * j)
+            T[s, sp] = B[j]
+            T[sp, s] = B[j].T
+            assert np.max(np.abs(np.tril(B[j], -1))) == 0.0
+    R = X @ Q - Q @ T
+    assert np.max(np.abs(R[:, :k - nb])) < 1e-12 * np.max(np.abs(X))
+    assert np.max(np.abs(np.diag(Q @ T @ Q.T) + info["diagB"] - res)) < 1e-12
+
+
+def test_block_lanczos_depends_only_on_start_span():
+    """Truncated block runs depend on the start block only through its span:
+    Q1 -> Q1 M (M invertible) leaves every block Krylov space, hence the
+    rank-k result, unchanged."""
+    L, per, p = (6, 11), [False, False], 3
+    N = 66
+    rng = np.random.default_rng(7)
+    V = rng.uniform(0, 0.5, N)
+    sigma = rng.uniform(0, 1, N) + 1j * rng.uniform(0.1, 1, N)
+    Q1 = rng.uniform(-1, 1, (N, 2))
+    M = np.array([[0.7, -1.3], [0.4, 0.9]])
+    for k in (4, 8):
+        r1 = O.lowrank_diag_block(L, per, -1.0, 0.0, V, sigma, math.pi / 10, Q1, p, k)
+        r2 = O.lowrank_diag_block(L, per, -1.0, 0.0, V, sigma, math.pi / 10, Q1 @ M, p, k)
+        assert np.max(np.abs(r1 - r2)) / np.max(np.abs(r1)) < 1e-11
+
+
+def test_block_of_one_is_the_scalar_recurrence():
+    L, per, p, N = (6, 11), [False, False], 3, 66
+    rng = np.random.default_rng(8)
+    V = rng.uniform(0, 0.5, N)
+    sigma = rng.uniform(0, 1, N) + 1j * rng.uniform(0.1, 1, N)
+    q1 = rng.uniform(-1, 1, N)
+    r1 = O.lowrank_diag(L, per, -1.0, 0.0, V, sigma, math.pi / 10, q1, p, 7)
+    r2 = O.lowrank_diag_block(L, per, -1.0, 0.0, V, sigma, math.pi / 10, q1[:, None], p, 7)
+    assert np.max(np.abs(r1 - r2)) / np.max(np.abs(r1)) < 1e-12
