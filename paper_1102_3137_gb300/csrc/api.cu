@@ -88,6 +88,7 @@ int build_part(const dyson_geometry* in, Part* out, bool gpu) {
   g.mu = in->mu;
   if (!(in->eta >= 0.0)) return fail(DYSON_E_BAD_ARG, "eta must be >= 0 (0: Matsubara axis)");
   g.eta = in->eta;
+  g.real_axis = in->eta > 0.0 ? 1 : 0;
   g.krylov_tol = in->krylov_tol > 0 ? in->krylov_tol : (mixed ? 1e-5 : 1e-13);
   g.krylov_maxit = in->krylov_maxit > 0 ? in->krylov_maxit : 1000;
   g.refine_tol = in->refine_tol > 0 ? in->refine_tol : 1e-13;

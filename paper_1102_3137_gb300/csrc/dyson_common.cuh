@@ -152,6 +152,7 @@ struct Geo {
   int ylayer[DY_MAXP]; // slow coordinate of interface layer l
   int penta;           // interface preconditioner keeps the distance-2 coupling (2D strips, W <= 64)
   double eta;          // 0: Matsubara axis; > 0: real axis w + i eta
+  int real_axis;       // eta > 0 (an integer test on the device)
   int ring_S;          // copy-ring slots chosen by the autotuner (0: shared-memory heuristic)
   int ring_CR;         // rows per streamed chunk chosen by the autotuner (W > 64; 0: heuristic)
 };
@@ -196,7 +197,7 @@ __host__ __device__ __forceinline__ size_t nifc(const Geo& g) { return (size_t)(
 __device__ __forceinline__ cxd dyson_diag(const Geo& g, const Bufs& b, int kf, int nat) {
   cxd s = b.sigma[(size_t)kf * g.N + nat];
   const double w = b.omega[kf];
-  return g.eta > 0.0 ? cxd{w + g.mu - b.V[nat] - s.x, g.eta - s.y}
+  return g.real_axis ? cxd{w + g.mu - b.V[nat] - s.x, g.eta - s.y}
                      : cxd{g.mu - b.V[nat] - s.x, w - s.y};
 }
 

@@ -31,10 +31,12 @@ __global__ void __launch_bounds__(256) k_spmv(Geo g, const double* __restrict__ 
   const bool two = xs + 1 < Lx;
   const C* xk = x + (size_t)kf * N;
   const cxd* sk = sigma + (size_t)kf * N;
-  const R t = (R)g.t;
-  const double w = omega[kf];
-  const R wr = (R)w, er = (R)g.eta, mur = (R)g.mu;
-  const bool real_axis = g.eta > 0.0;
+  auto cvt = [](double v) -> R {
+    if constexpr (sizeof(R) == 4) return d2f_bits(v);   // integer unit, not the FP64 pipe
+    else return v;
+  };
+  const R t = cvt(g.t), wr = cvt(omega[kf]), er = cvt(g.eta), mur = cvt(g.mu);
+  const bool real_axis = g.real_axis != 0;
   // vec (complex64, Lx even, x and y 16-byte aligned): every pair starts on a
   // 16-byte boundary (n is even)
   auto ld2 = [&](int m, C& p0, C& p1) {
@@ -64,10 +66,6 @@ __global__ void __launch_bounds__(256) k_spmv(Geo g, const double* __restrict__ 
   if (yi < Ly - 1) pair(n + Lx);
   if (zi > 0) pair(n - LxLy);
   if (zi < Lz - 1) pair(n + LxLy);
-  auto cvt = [](double v) -> R {
-    if constexpr (sizeof(R) == 4) return d2f_bits(v);   // integer unit, not the FP64 pipe
-    else return v;
-  };
   auto diag = [&](int m) {
     const cxd s = sk[m];
     const R vr = cvt(V[m]), sr = cvt(s.x), si = cvt(s.y);

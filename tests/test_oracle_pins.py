@@ -454,7 +454,7 @@ def _homogeneous_cube():
     return L, N, V, sigma, math.pi / 10
 
 
-def _dense_X(L, per, t, z, p):
+def _dense_X_and_inverse(L, per, t, z, p):
     N = z.shape[0]
     Hinv = np.linalg.inv(O.dense_H(L, per, t, z))
     subs = O.Subdomains(L, per, t, z, p)
@@ -469,7 +469,7 @@ def test_block_lanczos_exact_on_degenerate_spectrum():
     L, N, V, sigma, w = _homogeneous_cube()
     per = [False] * 3
     z = O.dyson_diagonal(w, 0.0, V, sigma)
-    X, Hinv = _dense_X(L, per, -1.0, z, 2)
+    X, Hinv = _dense_X_and_inverse(L, per, -1.0, z, 2)
     ev = np.linalg.eigvals(X)
     ev = ev[np.abs(ev) > 1e-10]
     assert len(ev) == 9
@@ -500,7 +500,7 @@ def test_block_lanczos_recurrence_and_orthogonality():
     res, info = O.lowrank_diag_block(L, per, -1.0, mu, V, sigma, w, Q1, p, k, return_info=True)
     assert info["status"] == O.STATUS_OK and info["steps"] == k // nb
     z = O.dyson_diagonal(w, mu, V, sigma)
-    X, _ = _dense_X(L, per, -1.0, z, p)
+    X, _ = _dense_X_and_inverse(L, per, -1.0, z, p)
     Q, A, B = info["Q"], info["A"], info["B"]
     assert np.max(np.abs(Q.T @ Q - np.eye(k))) < 1e-12
     T = np.zeros((k, k), dtype=complex)
