@@ -97,6 +97,13 @@ typedef struct {
                          Sec. 2 notes after Eq. 1); omega[] then holds real frequencies w
                          and Sigma the retarded self-energy (Im Sigma <= 0 keeps Im H_ii >=
                          eta > 0, which the factorization relies on).  Must be >= 0. */
+  int block_size;     /* Lanczos block size nb.  0 or 1: the scalar recurrence of Sec. 2.1.
+                         2..4: block Lanczos on X (not in the paper): nb start vectors, A_j =
+                         Q_j^T X Q_j and B_j in the bilinear form, deflation of vanishing
+                         columns; reaches the exact diagonal when X has eigenvalues of
+                         multiplicity up to nb, which the scalar method cannot.  k_max counts
+                         columns (k_max / nb block steps) and must be a multiple of nb with
+                         k_max * nb <= 1024; max_freqs * nb <= 65535. */
 } dyson_geometry;
 
 /* Library version string. */
@@ -153,8 +160,10 @@ int dyson_plan_tuning(dyson_plan plan, int* ring_slots, int* chunk_rows, int* ca
  *   omega  [K]         real Matsubara frequencies w_k
  *   V      [N]         real local potential V_i
  *   sigma  complex[K][N]  self-energy Sigma_i(i w_k)
- *   q1     [N]         real Lanczos start vector (normalised internally in the
- *                      bilinear form); the paper leaves it open
+ *   q1     [nb][N]     real Lanczos start vector(s), nb = block_size (normalised
+ *                      internally in the bilinear form; the nb columns of a
+ *                      block must be independent in it, else the frequency
+ *                      reports DYSON_ST_BREAKDOWN); the paper leaves it open
  *   diagG  complex[K][N]  output G_ii(i w_k)
  *   status [K]         output DYSON_ST_* flags per frequency (may be NULL)
  * All frequencies run in one batch: one thread-block cluster per frequency
@@ -175,6 +184,16 @@ int dyson_solve(dyson_plan plan, int K, const double* omega, const double* V,
  */
 int dyson_solve_info(dyson_plan plan, int K, double* alpha_beta, int* steps, int* iters,
                      int* refines);
+
+/*
+ * Block plans (block_size nb >= 2): the block tridiagonal T of the last
+ * dyson_solve.  AB complex[K][k_max/nb][2][nb][nb] (host) receives per block
+ * step j the diagonal block A_j (row-major, A_j[d][c] = q_{j,d}^T X q_{j,c})
+ * and the coupling B_j (upper triangular, R_{j-1} = Q_j B_j; B_0 = 0);
+ * steps[K] the block steps taken.  dyson_solve_info's alpha_beta must be NULL
+ * for block plans (its steps count block steps).  Either pointer may be NULL.
+ */
+int dyson_block_info(dyson_plan plan, int K, double* AB, int* steps);
 
 /*
  * y = H(i w_k) x for K frequencies by the nearest-neighbour stencil (Eq. 1),
@@ -234,7 +253,7 @@ typedef struct {
   const double* omega;   /* [K] host (pinned host memory lets the copies overlap) */
   const double* V;       /* [N] host */
   const double* sigma;   /* complex[K][N] host */
-  const double* q1;      /* [N] host, real Lanczos start vector */
+  const double* q1;      /* [nb][N] host, real Lanczos start vector(s) (nb = geom.block_size) */
   double* diagG;         /* complex[K][N] host, written before the request completes */
   int* status;           /* [K] host, DYSON_ST_* flags, or NULL */
 } dyson_request;
@@ -283,7 +302,8 @@ int dyson_profile_read(dyson_plan plan, int max_kernels, int* kinds, float* ms, 
 /*
  * Work accounting of the last dyson_solve: sweeps[K][p] receives the number
  * of block forward/back substitutions (each reads the subdomain's stored
- * g_s twice) that the CTA of subdomain i performed for frequency k.
+ * g_s twice) that the CTA of subdomain i performed for frequency k (summed
+ * over the columns of a block plan).
  * Waits for the device.
  */
 int dyson_work_counters(dyson_plan plan, int K, unsigned long long* sweeps);
@@ -291,7 +311,8 @@ int dyson_work_counters(dyson_plan plan, int K, unsigned long long* sweeps);
 /*
  * Lanczos basis of frequency k (0-based) from the last dyson_solve, for
  * checking the run step by step: Q complex[nvec][N] (host) receives q_1 ..
- * q_nvec in natural order (bilinear-normalised, Sec. 2.1), nvec <= k_max+1;
+ * q_nvec in natural order (bilinear-normalised, Sec. 2.1), nvec <= k_max+nb
+ * (block plans: column j*nb + c is column c of block j; deflated columns are 0);
  * vectors past the last step taken are left over from earlier work.  Waits for
  * the device; allocates a temporary device buffer.
  */

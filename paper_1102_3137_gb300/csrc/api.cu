@@ -76,6 +76,12 @@ int build_part(const dyson_geometry* in, Part* out, bool gpu) {
   g.penta = (g.T == 1 && g.W <= DY_MAXW_SMEM) ? 1 : 0;
   g.k_max = in->k_max;
   if (g.k_max < 1 || g.k_max > 256) return fail(DYSON_E_BAD_ARG, "k_max must be in 1..256");
+  g.nb = in->block_size > 1 ? in->block_size : 1;
+  if (in->block_size < 0 || g.nb > DY_MAXNB)
+    return fail(DYSON_E_BAD_ARG, "block_size must be in 0.." + std::to_string(DY_MAXNB));
+  if (g.nb > 1 && (g.k_max % g.nb || g.k_max * g.nb > DY_BLOCK_H))
+    return fail(DYSON_E_BAD_ARG, "block plans need k_max a multiple of block_size and k_max * block_size <= " +
+                                     std::to_string(DY_BLOCK_H));
   if (in->precision != DYSON_FP64 && in->precision != DYSON_MIXED)
     return fail(DYSON_E_BAD_ARG, "precision must be DYSON_FP64 or DYSON_MIXED");
   const bool mixed = in->precision == DYSON_MIXED;
@@ -93,8 +99,8 @@ int build_part(const dyson_geometry* in, Part* out, bool gpu) {
   g.krylov_maxit = in->krylov_maxit > 0 ? in->krylov_maxit : 1000;
   g.refine_tol = in->refine_tol > 0 ? in->refine_tol : 1e-13;
   g.refine_max = in->refine_max > 0 ? in->refine_max : 6;
-  if (in->max_freqs < 1 || in->max_freqs > 65535)
-    return fail(DYSON_E_BAD_ARG, "max_freqs must be in 1..65535");
+  if (in->max_freqs < 1 || (long long)in->max_freqs * g.nb > 65535)
+    return fail(DYSON_E_BAD_ARG, "max_freqs (times block_size) must be in 1..65535");
   out->dd2nat.assign(g.Ndd, -1);
   for (int i = 0; i < g.p; ++i) {
     const int w = g.T * g.h[i];
@@ -120,31 +126,32 @@ enum {
 size_t layout(const Geo& g, int K, bool mixed, size_t off[B_COUNT]) {
   const size_t cs = mixed ? sizeof(cxf) : sizeof(cxd);
   const size_t Kz = (size_t)K, Ndd = g.Ndd, nsub = (size_t)g.Lx * g.W;
+  const size_t Ks = Kz * g.nb;     // work slots: one per (frequency, block column)
   size_t sz[B_COUNT];
   sz[B_V] = g.N * sizeof(double);
   sz[B_OMEGA] = Kz * sizeof(double);
   sz[B_SIGMA] = Kz * g.N * sizeof(cxd);
-  sz[B_Q1] = g.N * sizeof(double);
+  sz[B_Q1] = (size_t)g.nb * g.N * sizeof(double);
   sz[B_DD2NAT] = Ndd * sizeof(int);
   sz[B_G] = Kz * g.p * nsub * g.W * cs;
   sz[B_G64] = mixed ? Kz * g.p * nsub * g.W * sizeof(cxd) : 0;
   sz[B_DIAGB] = Kz * Ndd * sizeof(cxd);
-  sz[B_Q] = Kz * (g.k_max + 1) * Ndd * sizeof(cxd);
+  sz[B_Q] = Kz * (g.k_max + g.nb) * Ndd * sizeof(cxd);
   sz[B_ACC] = Kz * Ndd * sizeof(cxd);
-  sz[B_U] = Kz * Ndd * sizeof(cxd);
-  sz[B_V1] = mixed ? Kz * Ndd * sizeof(cxd) : 0;
+  sz[B_U] = Ks * Ndd * sizeof(cxd);
+  sz[B_V1] = mixed ? Ks * Ndd * sizeof(cxd) : 0;
   sz[B_V2] = sz[B_V1];
   sz[B_V3] = sz[B_V1];
-  sz[B_YSCR] = Kz * g.p * nsub * cs;
-  sz[B_BND] = Kz * g.p * 2 * g.A * sizeof(cxd);
-  sz[B_IFV] = Kz * IF_N * nifc(g) * sizeof(cxd);
+  sz[B_YSCR] = Ks * g.p * nsub * cs;
+  sz[B_BND] = Ks * g.p * 2 * g.A * sizeof(cxd);
+  sz[B_IFV] = Ks * IF_N * nifc(g) * sizeof(cxd);
   sz[B_PRE] = Kz * nifc(g) * 3 * sizeof(cxd);
-  sz[B_LAN] = Kz * (g.k_max + 1) * 2 * sizeof(cxd);
+  sz[B_LAN] = Kz * (g.k_max + g.nb) * 2 * g.nb * sizeof(cxd);
   sz[B_MAXT] = Kz * sizeof(double);
   sz[B_ST] = Kz * ST_N * sizeof(int);
   sz[B_OUT] = Kz * g.N * sizeof(cxd);
   sz[B_STATUS] = Kz * sizeof(int);
-  sz[B_SWEEPS] = Kz * g.p * sizeof(unsigned long long);
+  sz[B_SWEEPS] = Ks * g.p * sizeof(unsigned long long);
   sz[B_FWORK] = g.W > DY_MAXW_SMEM ? (size_t)DY_FACTOR_CTAS * 2 * g.W * g.W * sizeof(cxd) : 0;
   sz[B_OFFB] = Kz * g.p * nsub * sizeof(cxd);
   sz[B_OFF2] = g.penta ? Kz * g.p * nsub * sizeof(cxd) : 0;
@@ -238,7 +245,8 @@ int stage_inputs(dyson_plan p, int K, const double* omega, const double* V, cons
   CK(cudaMemcpyAsync(at<double>(p, B_OMEGA), omega, K * sizeof(double), cudaMemcpyDefault, s));
   CK(cudaMemcpyAsync(at<double>(p, B_V), V, g.N * sizeof(double), cudaMemcpyDefault, s));
   CK(cudaMemcpyAsync(at<cxd>(p, B_SIGMA), sigma, (size_t)K * g.N * sizeof(cxd), cudaMemcpyDefault, s));
-  if (q1) CK(cudaMemcpyAsync(at<double>(p, B_Q1), q1, g.N * sizeof(double), cudaMemcpyDefault, s));
+  if (q1)
+    CK(cudaMemcpyAsync(at<double>(p, B_Q1), q1, (size_t)g.nb * g.N * sizeof(double), cudaMemcpyDefault, s));
   return DYSON_OK;
 }
 
@@ -300,7 +308,8 @@ int run_kernel(dyson_plan p, int kind, cudaStream_t s, bool cap, const char* wha
 int enqueue_solve(dyson_plan p, int K, cudaStream_t s, bool cap) {
   const Geo& g = p->g;
   p->n_prof = 0;
-  RUN(DYSON_KERNEL_INIT, "init", launch_init(g, p->b, K, s));
+  if (g.nb > 1) RUN(DYSON_KERNEL_INIT, "init", launch_init_block(g, p->b, K, s));
+  else RUN(DYSON_KERNEL_INIT, "init", launch_init(g, p->b, K, s));
   if (p->mixed) RUN(DYSON_KERNEL_FACTOR, "factor", (launch_factor<double, float>(g, p->b, K, s)));
   else RUN(DYSON_KERNEL_FACTOR, "factor", (launch_factor<double, double>(g, p->b, K, s)));
   if (g.p > 1) {
@@ -308,10 +317,11 @@ int enqueue_solve(dyson_plan p, int K, cudaStream_t s, bool cap) {
     else RUN(DYSON_KERNEL_PRECOND, "precond", launch_precond<double>(g, p->b, K, s));
   }
   if (g.p > 1) {
-    for (int j = 0; j < g.k_max; ++j) {
-      if (p->mixed) RUN(DYSON_KERNEL_XMATVEC, "xmatvec", launch_xmatvec<float>(g, p->b, K, j, 1, s));
-      else RUN(DYSON_KERNEL_XMATVEC, "xmatvec", launch_xmatvec<double>(g, p->b, K, j, 0, s));
-      RUN(DYSON_KERNEL_LANCZOS, "lanczos", launch_lanczos(g, p->b, K, j, s));
+    for (int j = 0; j < g.k_max / g.nb; ++j) {      // (block) Lanczos steps
+      if (p->mixed) RUN(DYSON_KERNEL_XMATVEC, "xmatvec", launch_xmatvec<float>(g, p->b, K, j, 1, g.nb, s));
+      else RUN(DYSON_KERNEL_XMATVEC, "xmatvec", launch_xmatvec<double>(g, p->b, K, j, 0, g.nb, s));
+      if (g.nb > 1) RUN(DYSON_KERNEL_LANCZOS, "lanczos", launch_block_lanczos(g, p->b, K, j, s));
+      else RUN(DYSON_KERNEL_LANCZOS, "lanczos", launch_lanczos(g, p->b, K, j, s));
     }
   }
   RUN(DYSON_KERNEL_FINALIZE, "finalize", launch_finalize(g, p->b, K, s));
@@ -332,7 +342,8 @@ int autotune(dyson_plan p, int K, cudaStream_t s) {
   p->tune_candidates = n;
   if (n < 2) return DYSON_OK;
   Geo& g = p->g;
-  LK(launch_init(g, p->b, K, s));
+  if (g.nb > 1) LK(launch_init_block(g, p->b, K, s));
+  else LK(launch_init(g, p->b, K, s));
   if (p->mixed) LK((launch_factor<double, float>(g, p->b, K, s)));
   else LK((launch_factor<double, double>(g, p->b, K, s)));
   if (p->mixed) LK(launch_precond<float>(g, p->b, K, s));
@@ -346,10 +357,12 @@ int autotune(dyson_plan p, int K, cudaStream_t s) {
   for (int c = 0; c < n && rc == DYSON_OK; ++c) {
     g.ring_S = S[c];
     g.ring_CR = CR[c];
-    cudaError_t e = p->mixed ? launch_xmatvec<float>(g, p->b, K, 0, 1, s) : launch_xmatvec<double>(g, p->b, K, 0, 0, s);
+    cudaError_t e = p->mixed ? launch_xmatvec<float>(g, p->b, K, 0, 1, g.nb, s)
+                             : launch_xmatvec<double>(g, p->b, K, 0, 0, g.nb, s);
     if (e == cudaSuccess) e = cudaEventRecord(e0, s);
     if (e == cudaSuccess)
-      e = p->mixed ? launch_xmatvec<float>(g, p->b, K, 0, 1, s) : launch_xmatvec<double>(g, p->b, K, 0, 0, s);
+      e = p->mixed ? launch_xmatvec<float>(g, p->b, K, 0, 1, g.nb, s)
+                   : launch_xmatvec<double>(g, p->b, K, 0, 0, g.nb, s);
     if (e == cudaSuccess) e = cudaEventRecord(e1, s);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
     float ms = 0.f;
@@ -568,6 +581,8 @@ int dyson_solve_info(dyson_plan p, int K, double* alpha_beta, int* steps, int* i
     if (iters) iters[k] = st[(size_t)k * ST_N + ST_ITERS];
     if (refines) refines[k] = st[(size_t)k * ST_N + ST_REFINE];
   }
+  if (alpha_beta && g.nb > 1)
+    return fail(DYSON_E_BAD_ARG, "block plan: alpha_beta must be NULL (dyson_block_info has T)");
   if (alpha_beta) {
     std::vector<cxd> lan((size_t)K * (g.k_max + 1) * 2);
     CK(cudaMemcpy(lan.data(), p->b.lan, lan.size() * sizeof(cxd), cudaMemcpyDeviceToHost));
@@ -579,6 +594,28 @@ int dyson_solve_info(dyson_plan p, int K, double* alpha_beta, int* steps, int* i
           o[0] = v.x;
           o[1] = v.y;
         }
+  }
+  return DYSON_OK;
+}
+
+int dyson_block_info(dyson_plan p, int K, double* AB, int* steps) {
+  int rc;
+  if ((rc = check_plan(p)) || (rc = check_K(p, K))) return rc;
+  const Geo& g = p->g;
+  if (g.nb < 2) return fail(DYSON_E_BAD_ARG, "not a block plan (block_size < 2)");
+  CK(cudaDeviceSynchronize());
+  if (steps) {
+    std::vector<int> st((size_t)K * ST_N);
+    CK(cudaMemcpy(st.data(), p->b.st, st.size() * sizeof(int), cudaMemcpyDeviceToHost));
+    for (int k = 0; k < K; ++k) steps[k] = st[(size_t)k * ST_N + ST_STEPS];
+  }
+  if (AB) {
+    // device: [K][k_max/nb + 1][2][nb][nb]; caller: [K][k_max/nb][2][nb][nb]
+    const size_t per = (size_t)(g.k_max + g.nb) * 2 * g.nb, keep = (size_t)g.k_max * 2 * g.nb;
+    std::vector<cxd> lan((size_t)K * per);
+    CK(cudaMemcpy(lan.data(), p->b.lan, lan.size() * sizeof(cxd), cudaMemcpyDeviceToHost));
+    for (int k = 0; k < K; ++k)
+      std::memcpy(AB + (size_t)k * keep * 2, lan.data() + (size_t)k * per, keep * sizeof(cxd));
   }
   return DYSON_OK;
 }
@@ -614,13 +651,13 @@ int dyson_lanczos_basis(dyson_plan p, int k, int nvec, double* Q) {
   if ((rc = check_plan(p))) return rc;
   const Geo& g = p->g;
   if (k < 0 || k >= p->Kcap) return fail(DYSON_E_BAD_ARG, "frequency index out of range");
-  if (nvec < 1 || nvec > g.k_max + 1) return fail(DYSON_E_BAD_ARG, "nvec must be in 1..k_max+1");
+  if (nvec < 1 || nvec > g.k_max + g.nb) return fail(DYSON_E_BAD_ARG, "nvec must be in 1..k_max+block_size");
   if (!Q) return fail(DYSON_E_BAD_ARG, "Q is NULL");
   CK(cudaDeviceSynchronize());
   const size_t bytes = (size_t)nvec * g.N * sizeof(cxd);
   cxd* tmp = nullptr;
   CK(cudaMalloc(&tmp, bytes));
-  const cxd* src = p->b.Q + (size_t)k * (g.k_max + 1) * g.Ndd;
+  const cxd* src = p->b.Q + (size_t)k * (g.k_max + g.nb) * g.Ndd;
   cudaError_t e = launch_scatter(g, p->b, nvec, src, tmp, g.Ndd, 0);
   if (e == cudaSuccess) e = cudaMemcpy(Q, tmp, bytes, cudaMemcpyDeviceToHost);
   cudaFree(tmp);
@@ -633,8 +670,15 @@ int dyson_work_counters(dyson_plan p, int K, unsigned long long* sweeps) {
   if ((rc = check_plan(p)) || (rc = check_K(p, K))) return rc;
   if (!sweeps) return fail(DYSON_E_BAD_ARG, "sweeps is NULL");
   CK(cudaDeviceSynchronize());
-  CK(cudaMemcpy(sweeps, p->b.sweeps, (size_t)K * p->g.p * sizeof(unsigned long long),
-                cudaMemcpyDeviceToHost));
+  const int nb = p->g.nb, P = p->g.p;
+  std::vector<unsigned long long> per((size_t)K * nb * P);
+  CK(cudaMemcpy(per.data(), p->b.sweeps, per.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+  for (int k = 0; k < K; ++k)
+    for (int i = 0; i < P; ++i) {
+      unsigned long long t = 0;
+      for (int c = 0; c < nb; ++c) t += per[((size_t)k * nb + c) * P + i];
+      sweeps[(size_t)k * P + i] = t;
+    }
   return DYSON_OK;
 }
 
@@ -756,16 +800,17 @@ int dyson_xmatvec(dyson_plan p, int K, const double* omega, const double* V, con
   if ((rc = enqueue_factor(p, K, s))) return rc;
   if (p->mixed) LK(launch_precond<float>(g, p->b, K, s));
   else LK(launch_precond<double>(g, p->b, K, s));
-  LK(launch_gather(g, p->b, K, qn, p->b.Q, (size_t)(g.k_max + 1) * g.Ndd, s));
+  // one vector per frequency: column 0 of block 0, result in the frequency's first slot
+  LK(launch_gather(g, p->b, K, qn, p->b.Q, (size_t)(g.k_max + g.nb) * g.Ndd, s));
   CK(cudaMemsetAsync(p->b.st, 0, (size_t)K * ST_N * sizeof(int), s));
   if (g.p > 1) {
-    if (p->mixed) LK(launch_xmatvec<float>(g, p->b, K, 0, 1, s));
-    else LK(launch_xmatvec<double>(g, p->b, K, 0, 0, s));
+    if (p->mixed) LK(launch_xmatvec<float>(g, p->b, K, 0, 1, 1, s));
+    else LK(launch_xmatvec<double>(g, p->b, K, 0, 0, 1, s));
   } else {
-    CK(cudaMemsetAsync(p->b.u, 0, (size_t)K * g.Ndd * sizeof(cxd), s));
+    CK(cudaMemsetAsync(p->b.u, 0, (size_t)K * g.nb * g.Ndd * sizeof(cxd), s));
   }
   cxd* dst = mem_kind == DYSON_MEM_HOST ? p->b.out : reinterpret_cast<cxd*>(u);
-  LK(launch_scatter(g, p->b, K, p->b.u, dst, g.Ndd, s));
+  LK(launch_scatter(g, p->b, K, p->b.u, dst, (size_t)g.nb * g.Ndd, s));
   if (mem_kind == DYSON_MEM_HOST) CK(cudaMemcpyAsync(u, dst, bytes, cudaMemcpyDeviceToHost, s));
   return finish(mem_kind, s);
 }

@@ -24,6 +24,8 @@
 #define DY_WARPS (DY_THREADS / 32)
 #define DY_MAXW 256         // widest slice the sweep kernels take
 #define DY_MAXW_SMEM 64     // widest slice the shared-memory factor kernel takes
+#define DY_MAXNB 4          // largest Lanczos block size
+#define DY_BLOCK_H 1024     // block Lanczos: k_max * nb bound (CGS2 coefficients kept in shared memory)
 #define DY_FACTOR_CTAS 304  // persistent grid of the wide-slice factor kernel (2 per SM on 152 SMs)
 
 // per-frequency state words
@@ -155,35 +157,42 @@ struct Geo {
   int real_axis;       // eta > 0 (an integer test on the device)
   int ring_S;          // copy-ring slots chosen by the autotuner (0: shared-memory heuristic)
   int ring_CR;         // rows per streamed chunk chosen by the autotuner (W > 64; 0: heuristic)
+  int nb;              // Lanczos block size (1: the scalar recurrence of Sec. 2.1)
 };
 
-// Device buffers of one plan; every per-frequency array is [K_cap][...].
+// Work slots: the X-matvec runs one cluster per (frequency f, block column c),
+// slot vs = f * nb + c; factors and per-frequency state are indexed by f.
+__host__ __device__ __forceinline__ int slot_freq(const Geo& g, int vs) { return g.nb > 1 ? vs / g.nb : vs; }
+
+// Device buffers of one plan; every per-frequency array is [K_cap][...],
+// every per-slot array [K_cap * nb][...].
 struct Bufs {
   const double* V;      // [N] trap/local potential, natural order
   const double* omega;  // [K] Matsubara frequencies
   const cxd* sigma;     // [K][N] self-energy, natural order
-  const double* q1;     // [N] real Lanczos start vector
+  const double* q1;     // [nb][N] real Lanczos start vector(s)
   const int* dd2nat;    // [Ndd] natural index of each DD slot, -1 on padding
   void* g;              // [K][p][Lx][W][W] slice factors g_s read by the sweeps (precision of the form)
   cxd* g64;             // [K][p][Lx][W][W] FP64 g_s kept for the mixed form's FP64 recursion
   cxd* diagB;           // [K][Ndd] diag(B^-1), zero on the interface
   cxd* offB;            // [K][p][Lx][W] diag of G_{s,s+1} (B_i^-1 between slices s, s+1), or null
   cxd* off2;            // [K][p][Lx][W] diag of G_{s,s+2} on the boundary rows (2D strips), or null
-  cxd* Q;               // [K][k_max+1][Ndd] Lanczos vectors
+  cxd* Q;               // [K][k_max+nb][Ndd] Lanczos vectors (column j*nb + c of block j)
   cxd* acc;             // [K][Ndd] running diag(Q T Q^T)
-  cxd* u;               // [K][Ndd] X q
-  cxd* v1;              // [K][Ndd] work vectors of the mixed form
+  cxd* u;               // [K*nb][Ndd] X q, per slot
+  cxd* v1;              // [K*nb][Ndd] work vectors of the mixed form, per slot
   cxd* v2;
   cxd* v3;
-  void* yscr;           // [K][p][Lx][W] forward-sweep intermediates (precision of the form)
-  cxd* bnd;             // [K][p][2][A] sweep values on the subdomain boundary rows
-  cxd* ifv;             // [K][6][(p-1)*A] interface Krylov vectors
+  void* yscr;           // [K*nb][p][Lx][W] forward-sweep intermediates (precision of the form)
+  cxd* bnd;             // [K*nb][p][2][A] sweep values on the subdomain boundary rows
+  cxd* ifv;             // [K*nb][IF_N][(p-1)*A] interface Krylov vectors
   cxd* pre;             // [K][p-1][3][A] tridiagonal preconditioner factors
-  cxd* lan;             // [K][k_max+1][2] (alpha_j, beta_j); beta_j couples q_{j-1}, q_j
+  cxd* lan;             // nb = 1: [K][k_max+1][2] (alpha_j, beta_j), beta_j couples q_{j-1}, q_j;
+                        // nb > 1: [K][k_max/nb+1][2][nb][nb] (A_j, B_j), B_j couples blocks j-1, j
   double* maxT;         // [K] running max |T| entry
   int* st;              // [K][ST_N]
   cxd* out;             // [K][N] diag(G), natural order
-  unsigned long long* sweeps;  // [K][p] subdomain sweeps performed (work accounting)
+  unsigned long long* sweeps;  // [K*nb][p] subdomain sweeps performed (work accounting)
   cxd* fwork;           // [DY_FACTOR_CTAS][2][W][W] wide-slice factor workspace (W > 64 only)
 };
 
@@ -237,8 +246,10 @@ template <typename R>
 cudaError_t launch_precond(const Geo& g, const Bufs& b, int K, cudaStream_t st);
 cudaError_t launch_init(const Geo& g, const Bufs& b, int K, cudaStream_t st);
 template <typename R>
-cudaError_t launch_xmatvec(const Geo& g, const Bufs& b, int K, int j, int mixed, cudaStream_t st);
+cudaError_t launch_xmatvec(const Geo& g, const Bufs& b, int K, int j, int mixed, int ncols, cudaStream_t st);
 cudaError_t launch_lanczos(const Geo& g, const Bufs& b, int K, int j, cudaStream_t st);
+cudaError_t launch_block_lanczos(const Geo& g, const Bufs& b, int K, int j, cudaStream_t st);
+cudaError_t launch_init_block(const Geo& g, const Bufs& b, int K, cudaStream_t st);
 cudaError_t launch_finalize(const Geo& g, const Bufs& b, int K, cudaStream_t st);
 template <typename R>
 cudaError_t launch_spmv(const Geo& g, const double* V, const double* omega, const cxd* sigma,
@@ -249,9 +260,9 @@ cudaError_t launch_bsolve(const Geo& g, const Bufs& b, int K, const cxd* q_dd, c
 // the X-matvec and subdomain-solve launchers exist for complex64 (k_xmatvec_c64.cu)
 // and complex128 (k_xmatvec_c128.cu)
 template <>
-cudaError_t launch_xmatvec<float>(const Geo& g, const Bufs& b, int K, int j, int mixed, cudaStream_t st);
+cudaError_t launch_xmatvec<float>(const Geo& g, const Bufs& b, int K, int j, int mixed, int ncols, cudaStream_t st);
 template <>
-cudaError_t launch_xmatvec<double>(const Geo& g, const Bufs& b, int K, int j, int mixed, cudaStream_t st);
+cudaError_t launch_xmatvec<double>(const Geo& g, const Bufs& b, int K, int j, int mixed, int ncols, cudaStream_t st);
 template <>
 cudaError_t launch_bsolve<float>(const Geo& g, const Bufs& b, int K, const cxd* q_dd, cxd* w_dd,
                                  cudaStream_t st);

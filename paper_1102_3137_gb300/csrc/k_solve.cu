@@ -18,13 +18,13 @@ __global__ void __launch_bounds__(DY_THREADS) k_lanczos(Geo g, Bufs b, int j) {
   int phase = 0;
   const size_t Ndd = g.Ndd;
   const int nsub = g.Lx * g.W, n = own_count(g, i);
-  cxd* Q = b.Q + (size_t)kf * (g.k_max + 1) * Ndd;
+  cxd* Q = b.Q + (size_t)kf * (g.k_max + g.nb) * Ndd;
   const cxd* qj = Q + (size_t)j * Ndd;
   const cxd* qm = (j > 0) ? Q + (size_t)(j - 1) * Ndd : nullptr;
   cxd* r = Q + (size_t)(j + 1) * Ndd;
   const cxd* u = b.u + (size_t)kf * Ndd;
   cxd* acc = b.acc + (size_t)kf * Ndd;
-  cxd* lan = b.lan + (size_t)kf * (g.k_max + 1) * 2;
+  cxd* lan = b.lan + (size_t)kf * (g.k_max + g.nb) * 2;
   const cxd beta_j = (j > 0) ? lan[2 * j + 1] : cxd{0, 0};
   // read before the first cluster barrier: CTA 0 updates it once all CTAs passed the last one
   const double maxT_prev = b.maxT[kf];
@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(DY_THREADS) k_init(Geo g, Bufs b) {
   const int i = blockIdx.x, kf = blockIdx.y;
   int phase = 0;
   const int nsub = g.Lx * g.W, n = own_count(g, i);
-  cxd* q = b.Q + (size_t)kf * (g.k_max + 1) * g.Ndd;
+  cxd* q = b.Q + (size_t)kf * (g.k_max + g.nb) * g.Ndd;
   cxd* acc = b.acc + (size_t)kf * g.Ndd;
   cxd v1[1] = {{0, 0}};
   for (int e = threadIdx.x; e < n; e += DY_THREADS) {
@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(DY_THREADS) k_init(Geo g, Bufs b) {
     int* st = b.st + (size_t)kf * ST_N;
     for (int k = 0; k < ST_N; ++k) st[k] = 0;
     if (g.p < 2) st[ST_DONE] = 1;        // one subdomain: X = 0, no Lanczos steps
-    cxd* lan = b.lan + (size_t)kf * (g.k_max + 1) * 2;
+    cxd* lan = b.lan + (size_t)kf * (g.k_max + g.nb) * 2;
     lan[0] = lan[1] = cxd{0, 0};
     b.maxT[kf] = 0.0;
   }

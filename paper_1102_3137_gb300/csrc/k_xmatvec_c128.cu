@@ -7,9 +7,9 @@ DY_SOLVE_VARIANT(double, 0)
 DY_SOLVE_VARIANT(double, 64)
 
 template <>
-cudaError_t launch_xmatvec<double>(const Geo& g, const Bufs& b, int K, int j, int mixed, cudaStream_t st) {
-  if (sweep_form<double>(g) == 0) return run_xmatvec<double, 0>(g, b, K, j, mixed, st);
-  return run_xmatvec<double, 64>(g, b, K, j, mixed, st);
+cudaError_t launch_xmatvec<double>(const Geo& g, const Bufs& b, int K, int j, int mixed, int ncols, cudaStream_t st) {
+  if (sweep_form<double>(g) == 0) return run_xmatvec<double, 0>(g, b, K, j, mixed, ncols, st);
+  return run_xmatvec<double, 64>(g, b, K, j, mixed, ncols, st);
 }
 
 template <>

@@ -7,12 +7,12 @@ DY_SOLVE_VARIANT(float, 0)
 DY_SOLVE_VARIANT(float, 16)
 
 template <>
-cudaError_t launch_xmatvec<float>(const Geo& g, const Bufs& b, int K, int j, int mixed, cudaStream_t st) {
+cudaError_t launch_xmatvec<float>(const Geo& g, const Bufs& b, int K, int j, int mixed, int ncols, cudaStream_t st) {
   switch (sweep_form<float>(g)) {
-    case 0: return run_xmatvec<float, 0>(g, b, K, j, mixed, st);
-    case 16: return run_xmatvec<float, 16>(g, b, K, j, mixed, st);
-    case 32: return run_xmatvec<float, 32>(g, b, K, j, mixed, st);
-    default: return run_xmatvec<float, 64>(g, b, K, j, mixed, st);
+    case 0: return run_xmatvec<float, 0>(g, b, K, j, mixed, ncols, st);
+    case 16: return run_xmatvec<float, 16>(g, b, K, j, mixed, ncols, st);
+    case 32: return run_xmatvec<float, 32>(g, b, K, j, mixed, ncols, st);
+    default: return run_xmatvec<float, 64>(g, b, K, j, mixed, ncols, st);
   }
 }
 

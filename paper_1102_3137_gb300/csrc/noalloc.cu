@@ -113,6 +113,7 @@ extern "C" int dyson_subdomain_diag_noalloc(const dyson_geometry* geom, int K, c
   if (!(geom->eta >= 0.0)) return dyson_internal_fail(DYSON_E_BAD_ARG, "noalloc: eta must be >= 0");
   g.eta = geom->eta;
   g.real_axis = geom->eta > 0.0 ? 1 : 0;
+  g.nb = 1;
   const size_t b_map = align256((size_t)ndd * sizeof(int));
   const size_t b_diag = align256((size_t)K * ndd * sizeof(cxd));
   const size_t b_g = align256((size_t)K * g.p * g.Lx * g.W * g.W * sizeof(cxd));

@@ -858,11 +858,11 @@ __device__ void sweep_chunked(const Geo& g, int i, const SweepArgs<R>& a, cx<R>*
 }
 
 template <typename R>
-__device__ __forceinline__ SweepArgs<R> sweep_base(const Geo& g, const Bufs& b, int kf, int i) {
+__device__ __forceinline__ SweepArgs<R> sweep_base(const Geo& g, const Bufs& b, int vs, int i) {
   SweepArgs<R> a;
   const size_t nsub = (size_t)g.Lx * g.W;
-  a.g = reinterpret_cast<const cx<R>*>(b.g) + ((size_t)kf * g.p + i) * nsub * g.W;
-  a.y = reinterpret_cast<cx<R>*>(b.yscr) + ((size_t)kf * g.p + i) * nsub;
+  a.g = reinterpret_cast<const cx<R>*>(b.g) + ((size_t)slot_freq(g, vs) * g.p + i) * nsub * g.W;
+  a.y = reinterpret_cast<cx<R>*>(b.yscr) + ((size_t)vs * g.p + i) * nsub;
   a.src = nullptr;
   a.lay_lo = a.lay_hi = nullptr;
   a.dst = nullptr;
@@ -872,18 +872,18 @@ __device__ __forceinline__ SweepArgs<R> sweep_base(const Geo& g, const Bufs& b, 
   return a;
 }
 
-__device__ __forceinline__ unsigned long long* sweep_cnt(const Geo& g, const Bufs& b, int kf, int i) {
-  return b.sweeps ? b.sweeps + (size_t)kf * g.p + i : nullptr;
+__device__ __forceinline__ unsigned long long* sweep_cnt(const Geo& g, const Bufs& b, int vs, int i) {
+  return b.sweeps ? b.sweeps + (size_t)vs * g.p + i : nullptr;
 }
 // boundary-row values and interface vectors are kept in the sweep precision R
 // (their buffers are sized for complex128, so either precision fits)
 template <typename R>
-__device__ __forceinline__ cx<R>* bnd_ptr(const Geo& g, const Bufs& b, int kf, int i, int hi) {
-  return reinterpret_cast<cx<R>*>(b.bnd) + (((size_t)kf * g.p + i) * 2 + hi) * g.A;
+__device__ __forceinline__ cx<R>* bnd_ptr(const Geo& g, const Bufs& b, int vs, int i, int hi) {
+  return reinterpret_cast<cx<R>*>(b.bnd) + (((size_t)vs * g.p + i) * 2 + hi) * g.A;
 }
 template <typename R>
-__device__ __forceinline__ cx<R>* ifv_ptr(const Geo& g, const Bufs& b, int kf, int slot) {
-  return reinterpret_cast<cx<R>*>(b.ifv) + ((size_t)kf * IF_N + slot) * nifc(g);
+__device__ __forceinline__ cx<R>* ifv_ptr(const Geo& g, const Bufs& b, int vs, int slot) {
+  return reinterpret_cast<cx<R>*>(b.ifv) + ((size_t)vs * IF_N + slot) * nifc(g);
 }
 
 // ---------------------------------------------------------------- interface pieces
@@ -942,12 +942,13 @@ __device__ __forceinline__ Aff2<R> aff_shfl_down(const Aff2<R>& f, int d) {
 // whole X-matvec kernel (capped at 128 per thread for two CTAs per SM) and
 // spill inside the sweeps.
 template <typename R>
-__device__ __noinline__ void precond_apply(const Geo& g, const Bufs& b, int kf, int i, const cx<R>* r,
+__device__ __noinline__ void precond_apply(const Geo& g, const Bufs& b, int vs, int i, const cx<R>* r,
                                            cx<R>* z) {
   using C = cx<R>;
   constexpr int E = 4, CH = 32 * E;
   const int Lx = g.Lx, A = g.A;
-  const C* __restrict__ pre = reinterpret_cast<const C*>(b.pre) + ((size_t)kf * nifc(g) + (size_t)i * A) * 3;
+  const C* __restrict__ pre =
+      reinterpret_cast<const C*>(b.pre) + ((size_t)slot_freq(g, vs) * nifc(g) + (size_t)i * A) * 3;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const C zero = {0, 0};
   for (int tr = wid; tr < g.T; tr += DY_WARPS) {
@@ -1096,21 +1097,21 @@ __device__ void cluster_sum_r(cg::cluster_group& cl, RedSmem& rs, int& phase, in
 // *conv is set to 0 if the cap was hit.
 template <typename R, int WF>
 __device__ int schur_cocg(cg::cluster_group& cl, RedSmem& rs, int& phase, const Geo& g,
-                          const Bufs& b, int kf, int i, double tol, cx<R>* sm, Pipe& pp,
+                          const Bufs& b, int vs, int i, double tol, cx<R>* sm, Pipe& pp,
                           int* conv) {
   using C = cx<R>;
   const int p = g.p, A = g.A;
   const bool has = i < p - 1;
-  C* X = ifv_ptr<R>(g, b, kf, IF_X);
-  C* Rv = ifv_ptr<R>(g, b, kf, IF_R);
-  C* Z = ifv_ptr<R>(g, b, kf, IF_Z);
-  C* P = ifv_ptr<R>(g, b, kf, IF_P);
-  C* SP = ifv_ptr<R>(g, b, kf, IF_SP);
-  const C* Bv = ifv_ptr<R>(g, b, kf, IF_B);
-  const C* dC = ifv_ptr<R>(g, b, kf, IF_D) + (size_t)i * A;
+  C* X = ifv_ptr<R>(g, b, vs, IF_X);
+  C* Rv = ifv_ptr<R>(g, b, vs, IF_R);
+  C* Z = ifv_ptr<R>(g, b, vs, IF_Z);
+  C* P = ifv_ptr<R>(g, b, vs, IF_P);
+  C* SP = ifv_ptr<R>(g, b, vs, IF_SP);
+  const C* Bv = ifv_ptr<R>(g, b, vs, IF_B);
+  const C* dC = ifv_ptr<R>(g, b, vs, IF_D) + (size_t)i * A;
   const size_t o = (size_t)i * A;
-  const C* bl_i = bnd_ptr<R>(g, b, kf, i, 1);
-  const C* bl_n = has ? bnd_ptr<R>(g, b, kf, i + 1, 0) : nullptr;
+  const C* bl_i = bnd_ptr<R>(g, b, vs, i, 1);
+  const C* bl_n = has ? bnd_ptr<R>(g, b, vs, i + 1, 0) : nullptr;
   const R tr = (R)g.t;
 
   if (has) {
@@ -1120,7 +1121,7 @@ __device__ int schur_cocg(cg::cluster_group& cl, RedSmem& rs, int& phase, const 
     }
   }
   __syncthreads();
-  if (has) precond_apply<R>(g, b, kf, i, Rv + o, Z + o);
+  if (has) precond_apply<R>(g, b, vs, i, Rv + o, Z + o);
   __syncthreads();
   C v2[2] = {{0, 0}, {0, 0}};
   if (has) {
@@ -1136,11 +1137,11 @@ __device__ int schur_cocg(cg::cluster_group& cl, RedSmem& rs, int& phase, const 
   const R bn = v2[1].x;
   *conv = 1;
   if (bn == (R)0) return 0;
-  SweepArgs<R> sa = sweep_base<R>(g, b, kf, i);
+  SweepArgs<R> sa = sweep_base<R>(g, b, vs, i);
   sa.lay_lo = (i > 0) ? P + (size_t)(i - 1) * A : nullptr;
   sa.lay_hi = has ? P + o : nullptr;
-  sa.bnd_lo = bnd_ptr<R>(g, b, kf, i, 0);
-  sa.bnd_hi = bnd_ptr<R>(g, b, kf, i, 1);
+  sa.bnd_lo = bnd_ptr<R>(g, b, vs, i, 0);
+  sa.bnd_hi = bnd_ptr<R>(g, b, vs, i, 1);
   const R tol2 = (R)(tol * tol);
   int it = 0;
   for (;;) {
@@ -1150,7 +1151,7 @@ __device__ int schur_cocg(cg::cluster_group& cl, RedSmem& rs, int& phase, const 
     }
     ++it;
     cl.sync();                                  // P of both neighbour layers is final
-    sweep<R, WF>(g, i, sa, sm, pp, sweep_cnt(g, b, kf, i));   // B^-1 E p on this subdomain
+    sweep<R, WF>(g, i, sa, sm, pp, sweep_cnt(g, b, vs, i));   // B^-1 E p on this subdomain
     cl.sync();                                  // boundary values of every subdomain written
     C v1[1] = {{0, 0}};
     if (has) {
@@ -1169,7 +1170,7 @@ __device__ int schur_cocg(cg::cluster_group& cl, RedSmem& rs, int& phase, const 
       }
     }
     __syncthreads();
-    if (has) precond_apply<R>(g, b, kf, i, Rv + o, Z + o);
+    if (has) precond_apply<R>(g, b, vs, i, Rv + o, Z + o);
     __syncthreads();
     v2[0] = v2[1] = C{0, 0};
     if (has) {
@@ -1193,27 +1194,29 @@ __device__ int schur_cocg(cg::cluster_group& cl, RedSmem& rs, int& phase, const 
 // Layer diagonal d_C = i w + mu - V - Sigma on this CTA's interface layer, in
 // precision R, computed once per launch for the interface products.
 template <typename R>
-__device__ void layer_diag(const Geo& g, const Bufs& b, int kf, int i) {
+__device__ void layer_diag(const Geo& g, const Bufs& b, int vs, int i) {
   if (i >= g.p - 1) return;
-  cx<R>* dC = ifv_ptr<R>(g, b, kf, IF_D) + (size_t)i * g.A;
+  cx<R>* dC = ifv_ptr<R>(g, b, vs, IF_D) + (size_t)i * g.A;
+  const int f = slot_freq(g, vs);
   for (int a = threadIdx.x; a < g.A; a += DY_THREADS)
-    dC[a] = cconv<R>(dyson_diag(g, b, kf, a + g.A * g.ylayer[i]));
+    dC[a] = cconv<R>(dyson_diag(g, b, f, a + g.A * g.ylayer[i]));
 }
 
 // res = rhs - H x (mode 0: full H; mode 1: B only, no interface coupling),
 // FP64, on this CTA's entries.  Returns partials (||res||^2, ||rhs||^2).
-__device__ void residual_H(const Geo& g, const Bufs& b, int kf, int i, const cxd* rhs,
+__device__ void residual_H(const Geo& g, const Bufs& b, int vs, int i, const cxd* rhs,
                            const cxd* x, cxd* res, int mode, double* rn, double* qn) {
   const int W = g.W, Lx = g.Lx, T = g.T, h = g.h[i], w = T * h, A = g.A;
   const size_t nsub = (size_t)Lx * W;
   const cxd* xs = x + i * nsub;
   const double t = g.t;
+  const int f = slot_freq(g, vs);
   double sr = 0, sq = 0;
   for (int e = threadIdx.x; e < (int)nsub; e += DY_THREADS) {
     const int s = e / W, j = e - s * W;
     if (j >= w) continue;
     const int tr = j % T, sl = j / T;
-    cxd d = dyson_diag(g, b, kf, sub_nat(g, i, s, j));
+    cxd d = dyson_diag(g, b, f, sub_nat(g, i, s, j));
     cxd nb = {0, 0};
     if (s > 0) nb = nb + xs[e - W];
     if (s < Lx - 1) nb = nb + xs[e + W];
@@ -1245,7 +1248,7 @@ __device__ void residual_H(const Geo& g, const Bufs& b, int kf, int i, const cxd
       if (xx < Lx - 1) nb = nb + xl[a + 1];
       if (tr > 0) nb = nb + xl[a - Lx];
       if (tr < T - 1) nb = nb + xl[a + Lx];
-      cxd hv = dyson_diag(g, b, kf, a + A * g.ylayer[i]) * xl[a] + t * nb;
+      cxd hv = dyson_diag(g, b, f, a + A * g.ylayer[i]) * xl[a] + t * nb;
       hv = hv + t * (xb[(size_t)xx * W + hi + tr] + xa[(size_t)xx * W + tr]);
       cxd q = rhs[o + a];
       cxd rr = q - hv;
@@ -1267,29 +1270,29 @@ __device__ void residual_H(const Geo& g, const Bufs& b, int kf, int i, const cxd
 // shrinking refinement residuals would leave float range otherwise).
 template <typename R, int WF>
 __device__ int solve_H(cg::cluster_group& cl, RedSmem& rs, int& phase, const Geo& g,
-                       const Bufs& b, int kf, int i, const cxd* rhs, cxd* xout, bool zero_B,
+                       const Bufs& b, int vs, int i, const cxd* rhs, cxd* xout, bool zero_B,
                        double sc, double tol, cx<R>* sm, Pipe& pp, int* conv) {
   const int A = g.A;
   const bool has = i < g.p - 1;
   const size_t nsub = (size_t)g.Lx * g.W;
-  cx<R>* Bv = ifv_ptr<R>(g, b, kf, IF_B);
+  cx<R>* Bv = ifv_ptr<R>(g, b, vs, IF_B);
   const cxd* rc = rhs + g.ifc_off + (size_t)i * A;
   const R tr = (R)g.t;
   const double isc = 1.0 / sc;
   if (!zero_B) {
-    SweepArgs<R> sa = sweep_base<R>(g, b, kf, i);
+    SweepArgs<R> sa = sweep_base<R>(g, b, vs, i);
     sa.src = rhs + i * nsub;
     sa.in_scale = isc;
     sa.dst = xout + i * nsub;
     sa.out_scale = sc;
     sa.dst_op = 0;
-    sa.bnd_lo = bnd_ptr<R>(g, b, kf, i, 0);
-    sa.bnd_hi = bnd_ptr<R>(g, b, kf, i, 1);
-    sweep<R, WF>(g, i, sa, sm, pp, sweep_cnt(g, b, kf, i));
+    sa.bnd_lo = bnd_ptr<R>(g, b, vs, i, 0);
+    sa.bnd_hi = bnd_ptr<R>(g, b, vs, i, 1);
+    sweep<R, WF>(g, i, sa, sm, pp, sweep_cnt(g, b, vs, i));
     cl.sync();
     if (has) {
-      const cx<R>* bl_i = bnd_ptr<R>(g, b, kf, i, 1);
-      const cx<R>* bl_n = bnd_ptr<R>(g, b, kf, i + 1, 0);
+      const cx<R>* bl_i = bnd_ptr<R>(g, b, vs, i, 1);
+      const cx<R>* bl_n = bnd_ptr<R>(g, b, vs, i + 1, 0);
       for (int a = threadIdx.x; a < A; a += DY_THREADS)
         Bv[(size_t)i * A + a] = cconv<R>(isc * rc[a]) - tr * (bl_i[a] + bl_n[a]);
     }
@@ -1297,16 +1300,16 @@ __device__ int solve_H(cg::cluster_group& cl, RedSmem& rs, int& phase, const Geo
     for (int a = threadIdx.x; a < A; a += DY_THREADS) Bv[(size_t)i * A + a] = cconv<R>(isc * rc[a]);
   }
   __syncthreads();
-  int it = schur_cocg<R, WF>(cl, rs, phase, g, b, kf, i, tol, sm, pp, conv);
+  int it = schur_cocg<R, WF>(cl, rs, phase, g, b, vs, i, tol, sm, pp, conv);
   cl.sync();
-  const cx<R>* X = ifv_ptr<R>(g, b, kf, IF_X);
-  SweepArgs<R> sb = sweep_base<R>(g, b, kf, i);
+  const cx<R>* X = ifv_ptr<R>(g, b, vs, IF_X);
+  SweepArgs<R> sb = sweep_base<R>(g, b, vs, i);
   sb.lay_lo = (i > 0) ? X + (size_t)(i - 1) * A : nullptr;
   sb.lay_hi = has ? X + (size_t)i * A : nullptr;
   sb.dst = xout + i * nsub;
   sb.out_scale = sc;
   sb.dst_op = zero_B ? 3 : 2;
-  sweep<R, WF>(g, i, sb, sm, pp, sweep_cnt(g, b, kf, i));
+  sweep<R, WF>(g, i, sb, sm, pp, sweep_cnt(g, b, vs, i));
   if (has) {
     cxd* xc = xout + g.ifc_off + (size_t)i * A;
     for (int a = threadIdx.x; a < A; a += DY_THREADS) xc[a] = sc * cconv<double>(X[(size_t)i * A + a]);
@@ -1426,15 +1429,18 @@ inline int ring_candidates(const Geo& g, int* S, int* CR, int max) {
 //              residuals of B, u against FP64 residuals of H, each until the
 //              relative residual is below refine_tol.
 template <typename R, int WF>
-__global__ void __launch_bounds__(DY_THREADS, 2) k_xmatvec(Geo g, Bufs b, int j, int mixed) {
+__global__ void __launch_bounds__(DY_THREADS, 2) k_xmatvec(Geo g, Bufs b, int j, int mixed, int ncols) {
   cg::cluster_group cl = cg::this_cluster();
   __shared__ RedSmem rs;
   __shared__ __align__(8) uint64_t bars[MAX_STAGES];
   __shared__ int err;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  const int i = blockIdx.x, kf = blockIdx.y, p = g.p, A = g.A;
-  int* st = b.st + (size_t)kf * ST_N;
-  if (st[ST_DONE]) return;                 // same value in every CTA of the cluster
+  // one cluster per (frequency, block column): slot vs = f * nb + c
+  const int i = blockIdx.x, vs = blockIdx.y, p = g.p, A = g.A;
+  const int f = slot_freq(g, vs), c = vs - f * g.nb;
+  if (c >= ncols) return;                  // same values in every CTA of the cluster
+  int* st = b.st + (size_t)f * ST_N;
+  if (st[ST_DONE]) return;
   Pipe pp;
   pp.bar = bars;
   const RingPlan rp = ring_plan<R>(g);
@@ -1447,69 +1453,69 @@ __global__ void __launch_bounds__(DY_THREADS, 2) k_xmatvec(Geo g, Bufs b, int j,
   pipe_init(pp);
   cx<R>* sm = reinterpret_cast<cx<R>*>(smem_raw + (size_t)rp.S * rp.CR * g.W * sizeof(cx<R>));
   pp.ybuf = rp.ybuf ? (void*)(sm + rp.zw) : nullptr;
-  layer_diag<R>(g, b, kf, i);
+  layer_diag<R>(g, b, vs, i);
   int phase = 0;
   const bool has = i < p - 1;
   const size_t Ndd = g.Ndd, nsub = (size_t)g.Lx * g.W;
-  const cxd* q = b.Q + ((size_t)kf * (g.k_max + 1) + j) * Ndd;
-  cxd* u = b.u + (size_t)kf * Ndd;
+  const cxd* q = b.Q + ((size_t)f * (g.k_max + g.nb) + (size_t)j * g.nb + c) * Ndd;
+  cxd* u = b.u + (size_t)vs * Ndd;
   int iters = 0, solves = 0, refines = 0, conv_all = 1, conv = 1;
 
   if (!mixed) {
     // w = B^-1 q_B, only its boundary rows are needed: E^T w
-    SweepArgs<R> sa = sweep_base<R>(g, b, kf, i);
+    SweepArgs<R> sa = sweep_base<R>(g, b, vs, i);
     sa.src = q + i * nsub;
-    sa.bnd_lo = bnd_ptr<R>(g, b, kf, i, 0);
-    sa.bnd_hi = bnd_ptr<R>(g, b, kf, i, 1);
-    sweep<R, WF>(g, i, sa, sm, pp, sweep_cnt(g, b, kf, i));
+    sa.bnd_lo = bnd_ptr<R>(g, b, vs, i, 0);
+    sa.bnd_hi = bnd_ptr<R>(g, b, vs, i, 1);
+    sweep<R, WF>(g, i, sa, sm, pp, sweep_cnt(g, b, vs, i));
     cl.sync();
-    cx<R>* Bv = ifv_ptr<R>(g, b, kf, IF_B);
+    cx<R>* Bv = ifv_ptr<R>(g, b, vs, IF_B);
     if (has) {
-      const cx<R>* bl_i = bnd_ptr<R>(g, b, kf, i, 1);
-      const cx<R>* bl_n = bnd_ptr<R>(g, b, kf, i + 1, 0);
+      const cx<R>* bl_i = bnd_ptr<R>(g, b, vs, i, 1);
+      const cx<R>* bl_n = bnd_ptr<R>(g, b, vs, i + 1, 0);
       const cxd* qc = q + g.ifc_off + (size_t)i * A;
       for (int a = threadIdx.x; a < A; a += DY_THREADS)
         Bv[(size_t)i * A + a] = (R)g.t * (bl_i[a] + bl_n[a]) - cconv<R>(qc[a]);
     }
     __syncthreads();
-    iters += schur_cocg<R, WF>(cl, rs, phase, g, b, kf, i, g.krylov_tol, sm, pp, &conv);
+    iters += schur_cocg<R, WF>(cl, rs, phase, g, b, vs, i, g.krylov_tol, sm, pp, &conv);
     conv_all &= conv;
     solves = 1;
     cl.sync();
-    const cx<R>* X = ifv_ptr<R>(g, b, kf, IF_X);
-    SweepArgs<R> sb = sweep_base<R>(g, b, kf, i);
+    const cx<R>* X = ifv_ptr<R>(g, b, vs, IF_X);
+    SweepArgs<R> sb = sweep_base<R>(g, b, vs, i);
     sb.lay_lo = (i > 0) ? X + (size_t)(i - 1) * A : nullptr;
     sb.lay_hi = has ? X + (size_t)i * A : nullptr;
     sb.dst = u + i * nsub;
     sb.dst_op = 0;
-    sweep<R, WF>(g, i, sb, sm, pp, sweep_cnt(g, b, kf, i));
+    sweep<R, WF>(g, i, sb, sm, pp, sweep_cnt(g, b, vs, i));
     if (has) {
       cxd* uc = u + g.ifc_off + (size_t)i * A;
       for (int a = threadIdx.x; a < A; a += DY_THREADS) uc[a] = -cconv<double>(X[(size_t)i * A + a]);
     }
   } else {
-    cxd* wv = b.v1 + (size_t)kf * Ndd;   // w_B, later the refinement corrections
-    cxd* rv = b.v2 + (size_t)kf * Ndd;   // FP64 residuals
-    cxd* hr = b.v3 + (size_t)kf * Ndd;   // right-hand side [0; q_C - E^T w_B]
+    cxd* wv = b.v1 + (size_t)vs * Ndd;   // w_B, later the refinement corrections
+    cxd* rv = b.v2 + (size_t)vs * Ndd;   // FP64 residuals
+    cxd* hr = b.v3 + (size_t)vs * Ndd;   // right-hand side [0; q_C - E^T w_B]
     // ---- w_B = B^-1 q_B, refined against FP64 residuals of B (subdomain-local)
     {
-      SweepArgs<R> sa = sweep_base<R>(g, b, kf, i);
+      SweepArgs<R> sa = sweep_base<R>(g, b, vs, i);
       sa.src = q + i * nsub;
       sa.dst = wv + i * nsub;
       sa.dst_op = 0;
-      sweep<R, WF>(g, i, sa, sm, pp, sweep_cnt(g, b, kf, i));
+      sweep<R, WF>(g, i, sa, sm, pp, sweep_cnt(g, b, vs, i));
       for (int r = 0; r < g.refine_max; ++r) {
         __syncthreads();
         double rn, qn;
-        residual_H(g, b, kf, i, q, wv, rv, 1, &rn, &qn);
+        residual_H(g, b, vs, i, q, wv, rv, 1, &rn, &qn);
         cxd v2[2] = {{rn, 0}, {qn, 0}};
         block_sum<2>(rs, v2);
         if (v2[0].x <= g.refine_tol * g.refine_tol * v2[1].x) break;
-        SweepArgs<R> sc = sweep_base<R>(g, b, kf, i);
+        SweepArgs<R> sc = sweep_base<R>(g, b, vs, i);
         sc.src = rv + i * nsub;
         sc.dst = wv + i * nsub;
         sc.dst_op = 1;
-        sweep<R, WF>(g, i, sc, sm, pp, sweep_cnt(g, b, kf, i));
+        sweep<R, WF>(g, i, sc, sm, pp, sweep_cnt(g, b, vs, i));
       }
     }
     cl.sync();                             // w_B of the neighbour subdomains is final
@@ -1539,7 +1545,7 @@ __global__ void __launch_bounds__(DY_THREADS, 2) k_xmatvec(Geo g, Bufs b, int j,
       hn = sqrt(v1[0].x);
     }
     if (hn > 0.0) {
-      iters += solve_H<R, WF>(cl, rs, phase, g, b, kf, i, hr, u, true, hn, g.krylov_tol, sm, pp, &conv);
+      iters += solve_H<R, WF>(cl, rs, phase, g, b, vs, i, hr, u, true, hn, g.krylov_tol, sm, pp, &conv);
       conv_all &= conv;
       ++solves;
     } else {
@@ -1549,12 +1555,12 @@ __global__ void __launch_bounds__(DY_THREADS, 2) k_xmatvec(Geo g, Bufs b, int j,
     for (int r = 0; r < g.refine_max && hn > 0.0; ++r) {
       cl.sync();
       double rn, qn;
-      residual_H(g, b, kf, i, hr, u, rv, 0, &rn, &qn);
+      residual_H(g, b, vs, i, hr, u, rv, 0, &rn, &qn);
       cxd v2[2] = {{rn, 0}, {qn, 0}};
       cluster_sum<2>(cl, rs, phase, p, v2);
       if (v2[0].x <= g.refine_tol * g.refine_tol * v2[1].x) break;
       ++refines;
-      iters += solve_H<R, WF>(cl, rs, phase, g, b, kf, i, rv, wv, false, sqrt(v2[0].x), g.krylov_tol, sm,
+      iters += solve_H<R, WF>(cl, rs, phase, g, b, vs, i, rv, wv, false, sqrt(v2[0].x), g.krylov_tol, sm,
                           pp, &conv);
       conv_all &= conv;
       ++solves;
@@ -1568,11 +1574,11 @@ __global__ void __launch_bounds__(DY_THREADS, 2) k_xmatvec(Geo g, Bufs b, int j,
   }
   __syncthreads();
   if (threadIdx.x == 0 && err) atomicOr(st + ST_STATUS, ST_WAIT_TIMEOUT);
-  if (i == 0 && threadIdx.x == 0) {
-    st[ST_ITERS] += iters;
-    st[ST_SOLVES] += solves;
-    st[ST_REFINE] += refines;
-    if (!conv_all) st[ST_STATUS] |= 4;
+  if (i == 0 && threadIdx.x == 0) {       // the nb clusters of a frequency share its counters
+    atomicAdd(st + ST_ITERS, iters);
+    atomicAdd(st + ST_SOLVES, solves);
+    atomicAdd(st + ST_REFINE, refines);
+    if (!conv_all) atomicOr(st + ST_STATUS, 4);
   }
   cl.sync();          // no CTA exits while a peer may still read its shared memory
 }
@@ -1583,7 +1589,7 @@ __global__ void __launch_bounds__(DY_THREADS, 2) k_bsolve(Geo g, Bufs b, const c
   __shared__ __align__(8) uint64_t bars[MAX_STAGES];
   __shared__ int err;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  const int i = blockIdx.x, kf = blockIdx.y;
+  const int i = blockIdx.x, kf = blockIdx.y, vs = kf * g.nb;   // scratch of the frequency's first slot
   const size_t nsub = (size_t)g.Lx * g.W;
   Pipe pp;
   pp.bar = bars;
@@ -1597,11 +1603,11 @@ __global__ void __launch_bounds__(DY_THREADS, 2) k_bsolve(Geo g, Bufs b, const c
   pipe_init(pp);
   cx<R>* sm = reinterpret_cast<cx<R>*>(smem_raw + (size_t)rp.S * rp.CR * g.W * sizeof(cx<R>));
   pp.ybuf = rp.ybuf ? (void*)(sm + rp.zw) : nullptr;
-  SweepArgs<R> sa = sweep_base<R>(g, b, kf, i);
+  SweepArgs<R> sa = sweep_base<R>(g, b, vs, i);
   sa.src = q + (size_t)kf * g.Ndd + i * nsub;
   sa.dst = w + (size_t)kf * g.Ndd + i * nsub;
   sa.dst_op = 0;
-  sweep<R, WF>(g, i, sa, sm, pp, sweep_cnt(g, b, kf, i));
+  sweep<R, WF>(g, i, sa, sm, pp, sweep_cnt(g, b, vs, i));
   if (i < g.p - 1)
     for (int a = threadIdx.x; a < g.A; a += DY_THREADS)
       w[(size_t)kf * g.Ndd + g.ifc_off + (size_t)i * g.A + a] = cxd{0, 0};
@@ -1652,16 +1658,16 @@ int sweep_form(const Geo& g) {
 // entry point; each is defined by DY_SOLVE_VARIANT in the translation unit
 // that compiles it, so the variants build in parallel.
 template <typename R, int WF>
-cudaError_t run_xmatvec(const Geo& g, const Bufs& b, int K, int j, int mixed, cudaStream_t st);
+cudaError_t run_xmatvec(const Geo& g, const Bufs& b, int K, int j, int mixed, int ncols, cudaStream_t st);
 template <typename R, int WF>
 cudaError_t run_bsolve(const Geo& g, const Bufs& b, int K, const cxd* q_dd, cxd* w_dd, cudaStream_t st);
 
 #define DY_SOLVE_VARIANT(R, WF)                                                                   \
   template <>                                                                                     \
-  cudaError_t run_xmatvec<R, WF>(const Geo& g, const Bufs& b, int K, int j, int mixed,            \
+  cudaError_t run_xmatvec<R, WF>(const Geo& g, const Bufs& b, int K, int j, int mixed, int ncols, \
                                  cudaStream_t st) {                                               \
-    return launch_cluster(k_xmatvec<R, WF>, dim3(g.p, K), g.p, sweep_smem<R>(g), st, g, b, j,    \
-                          mixed);                                                                 \
+    return launch_cluster(k_xmatvec<R, WF>, dim3(g.p, K * g.nb), g.p, sweep_smem<R>(g), st, g, b, \
+                          j, mixed, ncols);                                                       \
   }                                                                                               \
   template <>                                                                                     \
   cudaError_t run_bsolve<R, WF>(const Geo& g, const Bufs& b, int K, const cxd* q_dd, cxd* w_dd,   \

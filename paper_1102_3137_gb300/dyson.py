@@ -34,7 +34,7 @@ class dyson_geometry(C.Structure):
                 ("p", C.c_int), ("k_max", C.c_int), ("precision", C.c_int),
                 ("krylov_tol", C.c_double), ("krylov_maxit", C.c_int),
                 ("refine_tol", C.c_double), ("refine_max", C.c_int), ("max_freqs", C.c_int),
-                ("eta", C.c_double)]
+                ("eta", C.c_double), ("block_size", C.c_int)]
 
 
 class dyson_request(C.Structure):
@@ -80,6 +80,7 @@ def load(path: str = LIB_PATH):
         "dyson_plan_tuning": ([P, P, P, P, P, P], I),
         "dyson_solve": ([P, I, P, P, P, P, P, P, I, P], I),
         "dyson_solve_info": ([P, I, P, P, P, P], I),
+        "dyson_block_info": ([P, I, P, P], I),
         "dyson_apply_H": ([P, I, P, P, P, P, P, I, P], I),
         "dyson_apply_H_c64": ([P, I, P, P, P, P, P, I, P], I),
         "dyson_subdomain_diag": ([P, I, P, P, P, P, I, P], I),
@@ -164,7 +165,8 @@ def _stream(stream):
 
 
 def make_geometry(L, t=-1.0, mu=0.0, p=1, k_max=16, precision=DYSON_FP64, max_freqs=1,
-                  krylov_tol=0.0, krylov_maxit=0, refine_tol=0.0, refine_max=0, eta=0.0):
+                  krylov_tol=0.0, krylov_maxit=0, refine_tol=0.0, refine_max=0, eta=0.0,
+                  block_size=1):
     g = dyson_geometry()
     g.dim = len(L)
     for d in range(3):
@@ -173,6 +175,7 @@ def make_geometry(L, t=-1.0, mu=0.0, p=1, k_max=16, precision=DYSON_FP64, max_fr
     g.krylov_tol, g.krylov_maxit = float(krylov_tol), int(krylov_maxit)
     g.refine_tol, g.refine_max, g.max_freqs = float(refine_tol), int(refine_max), int(max_freqs)
     g.eta = float(eta)
+    g.block_size = int(block_size)
     return g
 
 
@@ -222,11 +225,13 @@ def dyson_plan_destroy(plan):
     _check(load().dyson_plan_destroy(plan))
 
 
-def dyson_solve(plan, K, omega, V, sigma, q1, diagG, status=None, stream=None):
+def dyson_solve(plan, K, omega, V, sigma, q1, diagG, status=None, stream=None, block_size=1):
+    """q1: [N] start vector, or [block_size][N] start block for a block plan."""
     N = V.shape[0] if hasattr(V, "shape") else len(V)
+    nb = max(1, int(block_size))
     mk = _kinds(omega, V, sigma, q1, diagG, status)
     _check(load().dyson_solve(plan, K, _ptr(omega, "f8", K), _ptr(V, "f8", N), _ptr(sigma, "c16", K * N),
-                              _ptr(q1, "f8", N), _ptr(diagG, "c16", K * N), _ptr(status, "i4", K),
+                              _ptr(q1, "f8", nb * N), _ptr(diagG, "c16", K * N), _ptr(status, "i4", K),
                               mk, _stream(stream)))
 
 
@@ -239,6 +244,14 @@ def dyson_solve_info(plan, K, k_max):
                                    refines.ctypes.data))
     return dict(alpha=ab[:, :, 0].copy(), beta=ab[:, :, 1].copy(), steps=steps, iters=iters,
                 refines=refines)
+
+
+def dyson_block_info(plan, K, k_max, nb):
+    """Block plans: (A[K][k_max/nb][nb][nb], B[K][k_max/nb][nb][nb], steps[K])."""
+    ab = np.zeros((K, k_max // nb, 2, nb, nb), dtype=np.complex128)
+    steps = np.zeros(K, dtype=np.int32)
+    _check(load().dyson_block_info(plan, K, ab.ctypes.data, steps.ctypes.data))
+    return ab[:, :, 0].copy(), ab[:, :, 1].copy(), steps
 
 
 def _row_call(fn, plan, K, omega, V, sigma, x, y, xdt="c16", stream=None):
@@ -329,7 +342,7 @@ def dyson_submit(server, geom, K, omega, V, sigma, q1, diagG, status=None):
     req.geom = geom
     req.K = int(K)
     req.omega, req.V = _ptr(omega, "f8", K), _ptr(V, "f8", N)
-    req.sigma, req.q1 = _ptr(sigma, "c16", K * N), _ptr(q1, "f8", N)
+    req.sigma, req.q1 = _ptr(sigma, "c16", K * N), _ptr(q1, "f8", max(1, geom.block_size) * N)
     req.diagG, req.status = _ptr(diagG, "c16", K * N), _ptr(status, "i4", K)
     t = C.c_uint64()
     _check(load().dyson_submit(server, C.byref(req), C.byref(t)))
@@ -361,6 +374,7 @@ class Plan:
     def __init__(self, L, t=-1.0, mu=0.0, p=1, k_max=16, precision=DYSON_FP64, max_freqs=1, **kw):
         self.geom = make_geometry(L, t, mu, p, k_max, precision, max_freqs, **kw)
         self.L, self.N, self.k_max = tuple(L), int(np.prod(L)), k_max
+        self.nb = max(1, self.geom.block_size)
         self.handle = dyson_plan_create(self.geom)
 
     def close(self):
@@ -378,8 +392,11 @@ class Plan:
         K = len(omega)
         if diagG is None:
             diagG = np.zeros((K, self.N), dtype=np.complex128)
-        dyson_solve(self.handle, K, omega, V, sigma, q1, diagG, status, stream)
+        dyson_solve(self.handle, K, omega, V, sigma, q1, diagG, status, stream, self.nb)
         return diagG
 
     def info(self, K):
+        if self.nb > 1:
+            A, B, steps = dyson_block_info(self.handle, K, self.k_max, self.nb)
+            return dict(A=A, B=B, steps=steps)
         return dyson_solve_info(self.handle, K, self.k_max)

@@ -113,3 +113,13 @@ def homogeneous_inputs(L: tuple, omega: np.ndarray, sigma0: complex, q_seed: int
     sigma = np.full((len(omega), N), sigma0, dtype=np.complex128)
     q1 = np.random.default_rng(q_seed).uniform(-1.0, 1.0, N)
     return np.asarray(omega, dtype=np.float64), V, sigma, q1
+
+
+def start_block(q1: np.ndarray, nb: int, seed: int = 97) -> np.ndarray:
+    """A real start block [nb][N] for block Lanczos: row 0 is q1, rows 1..nb-1
+    are uniform(-1, 1) draws from generators seeded (seed, row)."""
+    N = q1.shape[0]
+    rows = [np.asarray(q1, dtype=np.float64)]
+    for c in range(1, nb):
+        rows.append(np.random.default_rng((seed, c)).uniform(-1.0, 1.0, N))
+    return np.ascontiguousarray(np.stack(rows))

@@ -101,6 +101,19 @@ def test_real_axis_eta_validated(lib):
     assert D.dyson_plan_footprint(g) > 0
 
 
+def test_block_size_validated(lib):
+    for bad in (dict(block_size=2, k_max=9), dict(block_size=5, k_max=10), dict(block_size=-1, k_max=8),
+                dict(block_size=2, k_max=8, max_freqs=40000)):
+        g = D.make_geometry((16, 16), p=2, **{"max_freqs": 1, **bad})
+        with pytest.raises(D.DysonError) as e:
+            D.dyson_plan_footprint(g)
+        assert e.value.code == -1
+    g1 = D.make_geometry((16, 16), p=2, k_max=8, max_freqs=4)
+    g2 = D.make_geometry((16, 16), p=2, k_max=8, max_freqs=4, block_size=2)
+    # a block plan keeps nb work slots per frequency and k_max + nb basis columns
+    assert D.dyson_plan_footprint(g2) > D.dyson_plan_footprint(g1)
+
+
 def test_footprint(lib):
     g = D.make_geometry((128, 128), p=4, k_max=32, max_freqs=64)
     b = D.dyson_plan_footprint(g)
