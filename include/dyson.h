@@ -72,6 +72,11 @@ extern "C" {
                           Lanczos, re-orthogonalisation, the tridiagonal T_k and the
                           iterative-refinement residuals in FP64 */
 
+/* interface preconditioner of the H solves (dyson_geometry.precond) */
+#define DYSON_PRECOND_AUTO 0    /* exact layer blocks where they apply, else banded */
+#define DYSON_PRECOND_BANDED 1  /* banded approximation of each layer block of S */
+#define DYSON_PRECOND_LAYER 2   /* exact layer blocks S_ll (2D strips, Lx <= 160, slice width <= 32) */
+
 #define DYSON_MEM_HOST 0
 #define DYSON_MEM_DEVICE 1
 
@@ -89,7 +94,9 @@ typedef struct {
   double krylov_tol;  /* relative residual of each interface solve; 0 = default
                          (1e-13 FP64, 1e-5 mixed inner solves) */
   int krylov_maxit;   /* iteration cap of each interface solve; 0 = default (1000) */
-  double refine_tol;  /* mixed form: relative FP64 residual after refinement; 0 = 1e-13 */
+  double refine_tol;  /* mixed form: relative FP64 residual after refinement; 0 = 1e-15
+                         (refinement also stops once a pass no longer shrinks the residual
+                         4-fold: the FP64 rounding floor) */
   int refine_max;     /* mixed form: most refinement passes per solve; 0 = default (6) */
   int max_freqs;      /* most frequencies one dyson_solve call may carry (>= 1) */
   double eta;         /* frequency axis.  0: Matsubara, H_ii = i w_k + mu - V_i - Sigma_i
@@ -104,6 +111,13 @@ typedef struct {
                          multiplicity up to nb, which the scalar method cannot.  k_max counts
                          columns (k_max / nb block steps) and must be a multiple of nb with
                          k_max * nb <= 1024; max_freqs * nb <= 65535. */
+  int precond;        /* DYSON_PRECOND_*: preconditioner of the interface system S y = r (Eq. 4;
+                         the paper leaves the solver open).  LAYER inverts the exact diagonal
+                         blocks S_ll = C_ll - t^2 (surface Green's functions of the two strips
+                         along line l), computed in complex64 once per solve; only the coupling
+                         between different lines is left out, so COCG needs one or two
+                         iterations.  BANDED keeps the entries of S_ll within two sites.
+                         LAYER where it does not apply: DYSON_E_UNSUPPORTED. */
 } dyson_geometry;
 
 /* Library version string. */

@@ -74,6 +74,16 @@ int build_part(const dyson_geometry* in, Part* out, bool gpu) {
   g.Ndd = (int)ndd;
   g.ifc_off = g.p * g.Lx * g.W;
   g.penta = (g.T == 1 && g.W <= DY_MAXW_SMEM) ? 1 : 0;
+  if (in->precond < DYSON_PRECOND_AUTO || in->precond > DYSON_PRECOND_LAYER)
+    return fail(DYSON_E_BAD_ARG, "precond must be DYSON_PRECOND_AUTO, _BANDED or _LAYER");
+  {
+    const bool fits = g.T == 1 && g.p > 1 && g.W <= DY_LPRE_MAXW && g.Lx <= DY_LPRE_MAXLX;
+    if (in->precond == DYSON_PRECOND_LAYER && !fits)
+      return fail(DYSON_E_UNSUPPORTED, "exact layer preconditioner: 2D strips with p > 1, Lx <= " +
+                                           std::to_string(DY_LPRE_MAXLX) + " and slice width <= " +
+                                           std::to_string(DY_LPRE_MAXW) + " only");
+    g.lpre = (fits && in->precond != DYSON_PRECOND_BANDED) ? 1 : 0;
+  }
   g.k_max = in->k_max;
   if (g.k_max < 1 || g.k_max > 256) return fail(DYSON_E_BAD_ARG, "k_max must be in 1..256");
   g.nb = in->block_size > 1 ? in->block_size : 1;
@@ -97,7 +107,7 @@ int build_part(const dyson_geometry* in, Part* out, bool gpu) {
   g.real_axis = in->eta > 0.0 ? 1 : 0;
   g.krylov_tol = in->krylov_tol > 0 ? in->krylov_tol : (mixed ? 1e-5 : 1e-13);
   g.krylov_maxit = in->krylov_maxit > 0 ? in->krylov_maxit : 1000;
-  g.refine_tol = in->refine_tol > 0 ? in->refine_tol : 1e-13;
+  g.refine_tol = in->refine_tol > 0 ? in->refine_tol : 1e-15;
   g.refine_max = in->refine_max > 0 ? in->refine_max : 6;
   if (in->max_freqs < 1 || (long long)in->max_freqs * g.nb > 65535)
     return fail(DYSON_E_BAD_ARG, "max_freqs (times block_size) must be in 1..65535");
@@ -120,7 +130,8 @@ int build_part(const dyson_geometry* in, Part* out, bool gpu) {
 
 enum {
   B_V, B_OMEGA, B_SIGMA, B_Q1, B_DD2NAT, B_G, B_G64, B_DIAGB, B_Q, B_ACC, B_U, B_V1, B_V2, B_V3,
-  B_YSCR, B_BND, B_IFV, B_PRE, B_LAN, B_MAXT, B_ST, B_OUT, B_STATUS, B_SWEEPS, B_FWORK, B_OFFB, B_OFF2, B_COUNT
+  B_YSCR, B_BND, B_IFV, B_PRE, B_LAN, B_MAXT, B_ST, B_OUT, B_STATUS, B_SWEEPS, B_FWORK, B_OFFB, B_OFF2,
+  B_LPT, B_LPM, B_COUNT
 };
 
 size_t layout(const Geo& g, int K, bool mixed, size_t off[B_COUNT]) {
@@ -155,6 +166,9 @@ size_t layout(const Geo& g, int K, bool mixed, size_t off[B_COUNT]) {
   sz[B_FWORK] = g.W > DY_MAXW_SMEM ? (size_t)DY_FACTOR_CTAS * 2 * g.W * g.W * sizeof(cxd) : 0;
   sz[B_OFFB] = Kz * g.p * nsub * sizeof(cxd);
   sz[B_OFF2] = g.penta ? Kz * g.p * nsub * sizeof(cxd) : 0;
+  const size_t Lx2 = (size_t)g.Lx * g.Lx;
+  sz[B_LPT] = g.lpre ? Kz * g.p * 2 * Lx2 * sizeof(cxf) : 0;
+  sz[B_LPM] = g.lpre ? Kz * (g.p - 1) * Lx2 * cs : 0;
   size_t o = 0;
   for (int k = 0; k < B_COUNT; ++k) {
     off[k] = o;
@@ -497,6 +511,8 @@ int dyson_plan_create(const dyson_geometry* geom, dyson_plan* out) {
   b.fwork = p->g.W > DY_MAXW_SMEM ? at<cxd>(p, B_FWORK) : nullptr;
   b.offB = at<cxd>(p, B_OFFB);
   b.off2 = p->g.penta ? at<cxd>(p, B_OFF2) : nullptr;
+  b.lpt = p->g.lpre ? at<cxf>(p, B_LPT) : nullptr;
+  b.lpm = p->g.lpre ? (void*)at<char>(p, B_LPM) : nullptr;
   p->status_d = at<int>(p, B_STATUS);
   p->profile = false;
   p->tuned = false;

@@ -25,6 +25,8 @@
 #define DY_MAXW 256         // widest slice the sweep kernels take
 #define DY_MAXW_SMEM 64     // widest slice the shared-memory factor kernel takes
 #define DY_MAXNB 4          // largest Lanczos block size
+#define DY_LPRE_MAXLX 160   // widest interface line the exact layer preconditioner takes
+#define DY_LPRE_MAXW 32     // widest slice it takes
 #define DY_BLOCK_H 1024     // block Lanczos: k_max * nb bound (CGS2 coefficients kept in shared memory)
 #define DY_FACTOR_CTAS 304  // persistent grid of the wide-slice factor kernel (2 per SM on 152 SMs)
 
@@ -158,6 +160,7 @@ struct Geo {
   int ring_S;          // copy-ring slots chosen by the autotuner (0: shared-memory heuristic)
   int ring_CR;         // rows per streamed chunk chosen by the autotuner (W > 64; 0: heuristic)
   int nb;              // Lanczos block size (1: the scalar recurrence of Sec. 2.1)
+  int lpre;            // interface preconditioner: 1 exact layer blocks of S (2D strips), 0 banded
 };
 
 // Work slots: the X-matvec runs one cluster per (frequency f, block column c),
@@ -194,6 +197,8 @@ struct Bufs {
   cxd* out;             // [K][N] diag(G), natural order
   unsigned long long* sweeps;  // [K*nb][p] subdomain sweeps performed (work accounting)
   cxd* fwork;           // [DY_FACTOR_CTAS][2][W][W] wide-slice factor workspace (W > 64 only)
+  cx<float>* lpt;       // [K][p][2][Lx][Lx] boundary-row surface Green's functions (lpre)
+  void* lpm;            // [K][p-1][Lx][Lx] inverse layer blocks of S, precision of the form (lpre)
 };
 
 // interface Krylov vector slots inside ifv
@@ -250,6 +255,11 @@ cudaError_t launch_xmatvec(const Geo& g, const Bufs& b, int K, int j, int mixed,
 cudaError_t launch_lanczos(const Geo& g, const Bufs& b, int K, int j, cudaStream_t st);
 cudaError_t launch_block_lanczos(const Geo& g, const Bufs& b, int K, int j, cudaStream_t st);
 cudaError_t launch_init_block(const Geo& g, const Bufs& b, int K, cudaStream_t st);
+cudaError_t launch_surface(const Geo& g, const Bufs& b, int K, cudaStream_t st);
+template <typename R>
+cudaError_t launch_layer_inv(const Geo& g, const Bufs& b, int K, cudaStream_t st);
+size_t dyson_internal_surface_smem(const Geo& g);
+size_t dyson_internal_layer_inv_smem(const Geo& g);
 cudaError_t launch_finalize(const Geo& g, const Bufs& b, int K, cudaStream_t st);
 template <typename R>
 cudaError_t launch_spmv(const Geo& g, const double* V, const double* omega, const cxd* sigma,

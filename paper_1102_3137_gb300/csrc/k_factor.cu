@@ -457,6 +457,12 @@ __global__ void __launch_bounds__(DY_THREADS) k_precond(Geo g, Bufs b) {
 
 template <typename R, typename S>
 cudaError_t launch_factor(const Geo& g, const Bufs& b, int K, cudaStream_t st) {
+  if (g.lpre) {
+    // the boundary-row Green's functions for the layer preconditioner park their
+    // slice factors in b.g, so they run before the factorization fills it
+    cudaError_t e = launch_surface(g, b, K, st);
+    if (e != cudaSuccess) return e;
+  }
   if (g.W > DY_MAXW_SMEM) {
     // wide slices: FP64 recursion in global memory (both forms recurse in FP64)
     if (sizeof(R) != sizeof(double) || g.W > DY_MAXW || !b.fwork) return cudaErrorInvalidValue;
@@ -477,6 +483,7 @@ template cudaError_t launch_factor<float, float>(const Geo&, const Bufs&, int, c
 template <typename R>
 cudaError_t launch_precond(const Geo& g, const Bufs& b, int K, cudaStream_t st) {
   if (g.p < 2) return cudaSuccess;
+  if (g.lpre) return launch_layer_inv<R>(g, b, K, st);
   k_precond<R><<<dim3(g.p - 1, K), DY_THREADS, 0, st>>>(g, b);
   return cudaGetLastError();
 }

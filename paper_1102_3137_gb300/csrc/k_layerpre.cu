@@ -1,0 +1,247 @@
+// Exact interface-layer preconditioner for 2D strips: M = blkdiag_l(S_ll),
+// the diagonal blocks of the Schur complement S = C - E^T B^-1 E (Eq. 4) on
+// each interface line, inverted once per solve.  The paper leaves the
+// interface solver open and credits ARMS-type approximate Schur complements;
+// here S_ll is formed without approximation,
+//
+//   S_ll = C_ll - t^2 (P_top(l) + P_bot(l+1)),
+//
+// P_top(i) / P_bot(i) the restriction of B_i^-1 to the top / bottom row of
+// strip i, its "surface" Green's function along the row.  Only the coupling
+// between different lines (through a whole strip) is left out, which is
+// small, so COCG on S needs one or two iterations.  S itself is never formed.
+//
+// The preconditioner may be inexact, so everything here runs in complex64:
+//   k_surface    per (strip, frequency): the left-connected slice recursion
+//                along x, g_s = (D_s - t^2 g_{s-1})^-1, then backward
+//                G_ss = g_s + t^2 g_s G_{s+1,s+1} g_s and, for every s' > s,
+//                G_{s,s'} = -t g_s G_{s+1,s'} applied to the boundary columns
+//                of G_{s',s'} (kept in shared memory); P[s][s'] is their
+//                boundary entry.
+//   k_layer_inv  per (interface line, frequency): S_ll and its inverse by the
+//                sweep operator, symmetrised so that COCG sees a complex
+//                symmetric M^-1.
+#include "solve_device.cuh"
+
+namespace {
+
+using cxf_ = cx<float>;
+
+// In-place inverse of an n x n complex64 matrix (row stride n) in shared
+// memory by the sweep operator on the full matrix (pivots on the diagonal;
+// Im of the Dyson diagonal keeps them away from zero).  Thread t owns column
+// t % n and every (256 / n)-th row from t / n.
+__device__ void sweep_invert_f(cxf_* A, int n, cxf_* prow, cxf_* fcol) {
+  const int nrp = DY_THREADS / n;
+  const int c = threadIdx.x % n, r0 = threadIdx.x / n;
+  const bool act = r0 < nrp;
+  for (int k = 0; k < n; ++k) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < n; e += DY_THREADS) {
+      const cxf_ piv = cinv(A[k * n + k]);
+      prow[e] = A[k * n + e];
+      fcol[e] = (e == k) ? cxf_{-piv.x, -piv.y} : A[e * n + k] * piv;
+    }
+    __syncthreads();
+    if (act) {
+      const cxf_ pc = prow[c];
+      for (int r = r0; r < n; r += nrp) {
+        cxf_& a = A[r * n + c];
+        if (c == k) a = fcol[r];                                    // a_rk / a_kk; -1 / a_kk at r = k
+        else if (r == k) a = pc * cxf_{-fcol[k].x, -fcol[k].y};     // a_kc / a_kk
+        else a = cfma(cxf_{-fcol[r].x, -fcol[r].y}, pc, a);         // a_rc - a_rk a_kc / a_kk
+      }
+    }
+  }
+  __syncthreads();
+  // the sweep ends at -A^-1
+  for (int e = threadIdx.x; e < n * n; e += DY_THREADS) A[e] = cxf_{-A[e].x, -A[e].y};
+  __syncthreads();
+}
+
+// C = alpha X Y + beta D for W x W shared matrices (D may alias nothing, may be null)
+__device__ void small_matmul(cxf_* C, const cxf_* X, const cxf_* Y, int W, float alpha, const cxf_* D) {
+  for (int e = threadIdx.x; e < W * W; e += DY_THREADS) {
+    const int r = e / W, c = e - r * W;
+    cxf_ acc = {0.f, 0.f};
+    for (int k = 0; k < W; ++k) acc = cfma(X[r * W + k], Y[k * W + c], acc);
+    acc = cxf_{alpha * acc.x, alpha * acc.y};
+    if (D) acc = acc + D[e];
+    C[e] = acc;
+  }
+}
+
+constexpr int SURF_MAXW = 32;
+constexpr int SURF_NG = DY_THREADS / 32;                             // column groups (one per warp)
+constexpr int SURF_NCOL = (DY_LPRE_MAXLX + SURF_NG - 1) / SURF_NG;   // columns per thread at most
+
+__host__ __device__ __forceinline__ int surf_ldv(int Lx) { return Lx | 1; }   // odd stride: no bank conflicts
+
+__global__ void __launch_bounds__(DY_THREADS, 2) k_surface(Geo g, Bufs b) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int i = blockIdx.x, f = blockIdx.y;
+  const int W = g.W, Lx = g.Lx, w = g.h[i], n = W * W, ldv = surf_ldv(Lx);
+  const bool need_top = i < g.p - 1, need_bot = i > 0;
+  cxf_* Gs = reinterpret_cast<cxf_*>(smem_raw);   // g_s
+  cxf_* Gd = Gs + n;                              // G_ss
+  cxf_* Tm = Gd + n;
+  cxf_* prow = Tm + n;
+  cxf_* fcol = prow + W;
+  cxf_* Vt = fcol + W;                            // [W][ldv] boundary columns of G_{s,s'}, top row
+  cxf_* Vb = Vt + (size_t)W * ldv;                // same for the bottom row
+  // the slice factors are parked in the plan's factor buffer, which the
+  // factorization that follows overwrites
+  cxf_* gsv = reinterpret_cast<cxf_*>(b.g) + ((size_t)f * g.p + i) * (size_t)Lx * n;
+  cxf_* Pt = b.lpt + (((size_t)f * g.p + i) * 2 + 0) * (size_t)Lx * Lx;
+  cxf_* Pb = b.lpt + (((size_t)f * g.p + i) * 2 + 1) * (size_t)Lx * Lx;
+  const float t = d2f_bits(g.t), t2 = t * t;
+  const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
+
+  // forward: g_s = (D_s - t^2 g_{s-1})^-1, padding rows/columns carry the identity
+  for (int s = 0; s < Lx; ++s) {
+    for (int e = threadIdx.x; e < n; e += DY_THREADS) {
+      const int r = e / W, c = e - r * W;
+      cxf_ v = {0.f, 0.f};
+      if (r < w && c < w) {
+        if (r == c) {
+          const cxd d = dyson_diag(g, b, f, sub_nat(g, i, s, r));
+          v = cxf_{d2f_bits(d.x), d2f_bits(d.y)};
+        } else if (r == c + 1 || c == r + 1) {
+          v = cxf_{t, 0.f};
+        }
+        if (s > 0) v = cfma(cxf_{-t2, 0.f}, Gs[e], v);
+      } else if (r == c) {
+        v = cxf_{1.f, 0.f};
+      }
+      Gs[e] = v;
+    }
+    sweep_invert_f(Gs, W, prow, fcol);
+    for (int e = threadIdx.x; e < n; e += DY_THREADS) {
+      const int r = e / W, c = e - r * W;
+      if (r >= w || c >= w) Gs[e] = cxf_{0.f, 0.f};
+      gsv[(size_t)s * n + e] = Gs[e];
+    }
+    __syncthreads();
+  }
+  // backward: G_ss, and for every s' > s the boundary columns of
+  // G_{s,s'} = -t g_s G_{s+1,s'}; lane = row, warp = column group
+  for (int s = Lx - 1; s >= 0; --s) {
+    for (int e = threadIdx.x; e < n; e += DY_THREADS) Gs[e] = gsv[(size_t)s * n + e];
+    __syncthreads();
+    if (s == Lx - 1) {
+      for (int e = threadIdx.x; e < n; e += DY_THREADS) Gd[e] = Gs[e];
+    } else {
+      small_matmul(Tm, Gs, Gd, W, 1.f, nullptr);          // g_s G_{s+1,s+1}
+      __syncthreads();
+      small_matmul(Gd, Tm, Gs, W, t2, Gs);                 // g_s + t^2 g_s G g_s
+      cxf_ gr[SURF_MAXW];                                  // row `lane` of g_s (symmetric)
+#pragma unroll
+      for (int k = 0; k < SURF_MAXW; ++k) gr[k] = (lane < W && k < W) ? Gs[k * W + lane] : cxf_{0.f, 0.f};
+      for (int side = 0; side < 2; ++side) {
+        if (side == 0 ? !need_top : !need_bot) continue;
+        cxf_* V = side == 0 ? Vt : Vb;
+        cxf_ out[SURF_NCOL];
+#pragma unroll
+        for (int j = 0; j < SURF_NCOL; ++j) {
+          const int c = s + 1 + grp + SURF_NG * j;
+          cxf_ acc = {0.f, 0.f};
+          if (c < Lx) {
+#pragma unroll
+            for (int k = 0; k < SURF_MAXW; ++k)
+              if (k < W) acc = cfma(gr[k], V[k * ldv + c], acc);
+          }
+          out[j] = cxf_{-t * acc.x, -t * acc.y};
+        }
+        __syncthreads();                                   // every column read before any is rewritten
+        cxf_* P = side == 0 ? Pt : Pb;
+        const int rb = side == 0 ? w - 1 : 0;
+#pragma unroll
+        for (int j = 0; j < SURF_NCOL; ++j) {
+          const int c = s + 1 + grp + SURF_NG * j;
+          if (c < Lx && lane < W) {
+            V[lane * ldv + c] = out[j];
+            if (lane == rb) {
+              P[(size_t)s * Lx + c] = out[j];
+              P[(size_t)c * Lx + s] = out[j];
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();
+    // start the chain of column s' = s: the boundary columns of G_ss
+    for (int r = threadIdx.x; r < W; r += DY_THREADS) {
+      Vt[r * ldv + s] = Gd[r * W + (w - 1)];
+      Vb[r * ldv + s] = Gd[r * W + 0];
+    }
+    if (threadIdx.x == 0) {
+      Pt[(size_t)s * Lx + s] = Gd[(w - 1) * W + (w - 1)];
+      Pb[(size_t)s * Lx + s] = Gd[0];
+    }
+    __syncthreads();
+  }
+}
+
+// S_ll = C_ll - t^2 (P_top(l) + P_bot(l+1)) and M_l^-1, symmetrised, in the form's precision.
+template <typename R>
+__global__ void __launch_bounds__(DY_THREADS) k_layer_inv(Geo g, Bufs b) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int l = blockIdx.x, f = blockIdx.y, Lx = g.Lx, n = Lx * Lx;
+  cxf_* S = reinterpret_cast<cxf_*>(smem_raw);
+  cxf_* prow = S + n;
+  cxf_* fcol = prow + Lx;
+  const cxf_* Pt = b.lpt + (((size_t)f * g.p + l) * 2 + 0) * (size_t)n;
+  const cxf_* Pb = b.lpt + (((size_t)f * g.p + l + 1) * 2 + 1) * (size_t)n;
+  const float t = d2f_bits(g.t), t2 = t * t;
+  for (int e = threadIdx.x; e < n; e += DY_THREADS) {
+    const int r = e / Lx, c = e - r * Lx;
+    cxf_ v = {0.f, 0.f};
+    if (r == c) {
+      const cxd d = dyson_diag(g, b, f, r + g.A * g.ylayer[l]);
+      v = cxf_{d2f_bits(d.x), d2f_bits(d.y)};
+    } else if (r == c + 1 || c == r + 1) {
+      v = cxf_{t, 0.f};
+    }
+    S[e] = cfma(cxf_{-t2, 0.f}, Pt[e] + Pb[e], v);
+  }
+  sweep_invert_f(S, Lx, prow, fcol);
+  cx<R>* M = reinterpret_cast<cx<R>*>(b.lpm) + ((size_t)f * (g.p - 1) + l) * (size_t)n;
+  for (int e = threadIdx.x; e < n; e += DY_THREADS) {
+    const int r = e / Lx, c = e - r * Lx;
+    const cxf_ a = S[e], at = S[c * Lx + r];
+    const cxf_ v = {0.5f * (a.x + at.x), 0.5f * (a.y + at.y)};
+    M[e] = cx<R>{(R)v.x, (R)v.y};
+  }
+}
+
+}  // namespace
+
+size_t dyson_internal_surface_smem(const Geo& g) {
+  return (3 * (size_t)g.W * g.W + 2 * (size_t)g.W + 2 * (size_t)g.W * surf_ldv(g.Lx)) * sizeof(cxf_);
+}
+
+size_t dyson_internal_layer_inv_smem(const Geo& g) {
+  return ((size_t)g.Lx * g.Lx + 2 * (size_t)g.Lx) * sizeof(cxf_);
+}
+
+cudaError_t launch_surface(const Geo& g, const Bufs& b, int K, cudaStream_t st) {
+  if (!g.lpre) return cudaSuccess;
+  if (g.W > SURF_MAXW || g.Lx > DY_LPRE_MAXLX) return cudaErrorInvalidValue;
+  const size_t smem = dyson_internal_surface_smem(g);
+  cudaError_t e = raise_smem_limit((const void*)k_surface, smem);
+  if (e != cudaSuccess) return e;
+  k_surface<<<dim3(g.p, K), DY_THREADS, smem, st>>>(g, b);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_layer_inv(const Geo& g, const Bufs& b, int K, cudaStream_t st) {
+  if (!g.lpre) return cudaSuccess;
+  const size_t smem = dyson_internal_layer_inv_smem(g);
+  cudaError_t e = raise_smem_limit((const void*)k_layer_inv<R>, smem);
+  if (e != cudaSuccess) return e;
+  k_layer_inv<R><<<dim3(g.p - 1, K), DY_THREADS, smem, st>>>(g, b);
+  return cudaGetLastError();
+}
+template cudaError_t launch_layer_inv<float>(const Geo&, const Bufs&, int, cudaStream_t);
+template cudaError_t launch_layer_inv<double>(const Geo&, const Bufs&, int, cudaStream_t);

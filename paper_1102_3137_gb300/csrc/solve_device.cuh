@@ -32,6 +32,9 @@ namespace {
 constexpr double TERM_TOL = 1e-12;    // |beta_{j+1}| <= TERM_TOL * max|T|: invariant subspace
 constexpr double BRK_TOL = 1e-14;     // |r^T r| <= BRK_TOL * ||r||^2: breakdown
 constexpr int KMAX_SMEM = 256;        // largest Lanczos rank cap
+// refinement stops early once a pass no longer shrinks the squared FP64
+// residual 16-fold (the residual has reached its rounding floor)
+constexpr double REFINE_STALL = 1.0 / 16.0;
 
 __device__ __forceinline__ size_t own_idx(const Geo& g, int i, int e, int nsub) {
   return e < nsub ? (size_t)i * nsub + e : (size_t)g.ifc_off + (size_t)i * g.A + (e - nsub);
@@ -1093,6 +1096,36 @@ __device__ void cluster_sum_r(cg::cluster_group& cl, RedSmem& rs, int& phase, in
 // COCG for S y = b on the interface (S = C - E^T B^-1 E never formed), all in
 // precision R: the FP64 form solves to krylov_tol in FP64; the mixed form's
 // inner solves (refined in FP64 one level up) run entirely in complex64.
+// z = M_l^-1 r on interface line i with the exact layer block of S (2D
+// strips): a dense symmetric product, thread a owning output a; the stored
+// inverse is symmetric, so column a is read contiguously across threads.
+// r must be complete (a barrier after its writers) before the call.
+template <typename R>
+__device__ __noinline__ void lpre_apply(const Geo& g, const Bufs& b, int vs, int i, const cx<R>* r,
+                                        cx<R>* z) {
+  using C = cx<R>;
+  const int Lx = g.Lx;
+  const C* rsh = r;                 // every thread reads all of r: served by L1
+  const C* M = reinterpret_cast<const C*>(b.lpm) + ((size_t)slot_freq(g, vs) * (g.p - 1) + i) * (size_t)Lx * Lx;
+  for (int a = threadIdx.x; a < Lx; a += DY_THREADS) {
+    C acc0 = {0, 0}, acc1 = {0, 0};
+    int c = 0;
+    for (; c + 1 < Lx; c += 2) {
+      acc0 = cfma(M[(size_t)c * Lx + a], rsh[c], acc0);
+      acc1 = cfma(M[(size_t)(c + 1) * Lx + a], rsh[c + 1], acc1);
+    }
+    if (c < Lx) acc0 = cfma(M[(size_t)c * Lx + a], rsh[c], acc0);
+    z[a] = acc0 + acc1;
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void interface_precond(const Geo& g, const Bufs& b, int vs, int i, const cx<R>* r,
+                                                  cx<R>* z) {
+  if (g.lpre) lpre_apply<R>(g, b, vs, i, r, z);
+  else precond_apply<R>(g, b, vs, i, r, z);
+}
+
 // Right-hand side in IF_B, solution in IF_X.  Returns the iteration count;
 // *conv is set to 0 if the cap was hit.
 template <typename R, int WF>
@@ -1121,7 +1154,7 @@ __device__ int schur_cocg(cg::cluster_group& cl, RedSmem& rs, int& phase, const 
     }
   }
   __syncthreads();
-  if (has) precond_apply<R>(g, b, vs, i, Rv + o, Z + o);
+  if (has) interface_precond<R>(g, b, vs, i, Rv + o, Z + o);
   __syncthreads();
   C v2[2] = {{0, 0}, {0, 0}};
   if (has) {
@@ -1170,7 +1203,7 @@ __device__ int schur_cocg(cg::cluster_group& cl, RedSmem& rs, int& phase, const 
       }
     }
     __syncthreads();
-    if (has) precond_apply<R>(g, b, vs, i, Rv + o, Z + o);
+    if (has) interface_precond<R>(g, b, vs, i, Rv + o, Z + o);
     __syncthreads();
     v2[0] = v2[1] = C{0, 0};
     if (has) {
@@ -1504,6 +1537,7 @@ __global__ void __launch_bounds__(DY_THREADS, 2) k_xmatvec(Geo g, Bufs b, int j,
       sa.dst = wv + i * nsub;
       sa.dst_op = 0;
       sweep<R, WF>(g, i, sa, sm, pp, sweep_cnt(g, b, vs, i));
+      double prev = INFINITY;
       for (int r = 0; r < g.refine_max; ++r) {
         __syncthreads();
         double rn, qn;
@@ -1511,6 +1545,8 @@ __global__ void __launch_bounds__(DY_THREADS, 2) k_xmatvec(Geo g, Bufs b, int j,
         cxd v2[2] = {{rn, 0}, {qn, 0}};
         block_sum<2>(rs, v2);
         if (v2[0].x <= g.refine_tol * g.refine_tol * v2[1].x) break;
+        if (v2[0].x > REFINE_STALL * prev) break;        // at the FP64 rounding floor
+        prev = v2[0].x;
         SweepArgs<R> sc = sweep_base<R>(g, b, vs, i);
         sc.src = rv + i * nsub;
         sc.dst = wv + i * nsub;
@@ -1552,6 +1588,7 @@ __global__ void __launch_bounds__(DY_THREADS, 2) k_xmatvec(Geo g, Bufs b, int j,
       const int n = own_count(g, i);
       for (int e = threadIdx.x; e < n; e += DY_THREADS) u[own_idx(g, i, e, (int)nsub)] = cxd{0, 0};
     }
+    double prev = INFINITY;
     for (int r = 0; r < g.refine_max && hn > 0.0; ++r) {
       cl.sync();
       double rn, qn;
@@ -1559,6 +1596,8 @@ __global__ void __launch_bounds__(DY_THREADS, 2) k_xmatvec(Geo g, Bufs b, int j,
       cxd v2[2] = {{rn, 0}, {qn, 0}};
       cluster_sum<2>(cl, rs, phase, p, v2);
       if (v2[0].x <= g.refine_tol * g.refine_tol * v2[1].x) break;
+      if (v2[0].x > REFINE_STALL * prev) break;          // at the FP64 rounding floor
+      prev = v2[0].x;
       ++refines;
       iters += solve_H<R, WF>(cl, rs, phase, g, b, vs, i, rv, wv, false, sqrt(v2[0].x), g.krylov_tol, sm,
                           pp, &conv);

@@ -114,6 +114,23 @@ def test_block_size_validated(lib):
     assert D.dyson_plan_footprint(g2) > D.dyson_plan_footprint(g1)
 
 
+def test_precond_choice_validated(lib):
+    g = D.make_geometry((128, 128), p=4, k_max=8, max_freqs=2, precond=D.DYSON_PRECOND_LAYER)
+    assert D.dyson_plan_footprint(g) > 0
+    g3 = D.make_geometry((8, 8, 9), p=2, k_max=8, max_freqs=2, precond=D.DYSON_PRECOND_LAYER)
+    with pytest.raises(D.DysonError) as e:
+        D.dyson_plan_footprint(g3)                  # 3D slabs: only the banded form
+    assert e.value.code == -4
+    g.precond = 7
+    with pytest.raises(D.DysonError) as e:
+        D.dyson_plan_footprint(g)
+    assert e.value.code == -1
+    # the layer blocks add the surface Green's functions and the inverse blocks
+    ga = D.make_geometry((128, 128), p=4, k_max=8, max_freqs=2, precond=D.DYSON_PRECOND_AUTO)
+    gb = D.make_geometry((128, 128), p=4, k_max=8, max_freqs=2, precond=D.DYSON_PRECOND_BANDED)
+    assert D.dyson_plan_footprint(ga) > D.dyson_plan_footprint(gb)
+
+
 def test_footprint(lib):
     g = D.make_geometry((128, 128), p=4, k_max=32, max_freqs=64)
     b = D.dyson_plan_footprint(g)

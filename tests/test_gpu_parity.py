@@ -221,7 +221,7 @@ def test_repeat_is_bitwise(L, p, k, precision):
 def test_iteration_cap_reports_status():
     w = wl((16, 16), 2, 4, K=2)
     omega, V, sigma, q1 = I.make_inputs(w)
-    pl = plan_for(w, krylov_maxit=1)
+    pl = plan_for(w, krylov_maxit=1, precond=D.DYSON_PRECOND_BANDED)
     st = np.zeros(2, np.int32)
     out = pl.solve(omega, V, sigma, q1, status=st)
     assert np.all(st & D.DYSON_ST_NO_CONVERGENCE)
