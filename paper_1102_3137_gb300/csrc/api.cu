@@ -9,6 +9,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "dyson.h"
@@ -109,6 +110,7 @@ int build_part(const dyson_geometry* in, Part* out, bool gpu) {
   g.krylov_maxit = in->krylov_maxit > 0 ? in->krylov_maxit : 1000;
   g.refine_tol = in->refine_tol > 0 ? in->refine_tol : 1e-15;
   g.refine_max = in->refine_max > 0 ? in->refine_max : 6;
+  if (in->freq_groups < 0) return fail(DYSON_E_BAD_ARG, "freq_groups must be >= 0 (0: default)");
   if (in->max_freqs < 1 || (long long)in->max_freqs * g.nb > 65535)
     return fail(DYSON_E_BAD_ARG, "max_freqs (times block_size) must be in 1..65535");
   out->dd2nat.assign(g.Ndd, -1);
@@ -131,7 +133,7 @@ int build_part(const dyson_geometry* in, Part* out, bool gpu) {
 enum {
   B_V, B_OMEGA, B_SIGMA, B_Q1, B_DD2NAT, B_G, B_G64, B_DIAGB, B_Q, B_ACC, B_U, B_V1, B_V2, B_V3,
   B_YSCR, B_BND, B_IFV, B_PRE, B_LAN, B_MAXT, B_ST, B_OUT, B_STATUS, B_SWEEPS, B_FWORK, B_OFFB, B_OFF2,
-  B_LPT, B_LPM, B_COUNT
+  B_LPT, B_LPM, B_LPG, B_COUNT
 };
 
 size_t layout(const Geo& g, int K, bool mixed, size_t off[B_COUNT]) {
@@ -169,6 +171,7 @@ size_t layout(const Geo& g, int K, bool mixed, size_t off[B_COUNT]) {
   const size_t Lx2 = (size_t)g.Lx * g.Lx;
   sz[B_LPT] = g.lpre ? Kz * g.p * 2 * Lx2 * sizeof(cxf) : 0;
   sz[B_LPM] = g.lpre ? Kz * (g.p - 1) * Lx2 * cs : 0;
+  sz[B_LPG] = g.lpre ? Kz * g.p * nsub * g.W * sizeof(cxf) : 0;
   size_t o = 0;
   for (int k = 0; k < B_COUNT; ++k) {
     off[k] = o;
@@ -215,6 +218,9 @@ struct dyson_plan_s {
   std::vector<cudaEvent_t> evs;    // 2 per profiled kernel
   std::vector<int> ev_kind;        // DYSON_KERNEL_* of each profiled kernel
   int n_prof;                      // profiled kernels in the last enqueued sequence
+  int ngroups;                     // frequency groups run as parallel graph branches
+  std::vector<cudaStream_t> gs;    // one stream per group (group 0 highest priority)
+  std::vector<cudaEvent_t> gev;    // fork + one join event per group
 };
 
 namespace {
@@ -278,7 +284,7 @@ int finish(int mem_kind, cudaStream_t s) {
   } while (0)
 
 int enqueue_factor(dyson_plan p, int K, cudaStream_t s) {
-  if (p->mixed) LK((launch_factor<double, float>(p->g, p->b, K, s)));
+  if (p->mixed) LK((launch_factor<dfl, float>(p->g, p->b, K, s)));
   else LK((launch_factor<double, double>(p->g, p->b, K, s)));
   return DYSON_OK;
 }
@@ -319,27 +325,103 @@ int run_kernel(dyson_plan p, int kind, cudaStream_t s, bool cap, const char* wha
     if (rc_) return rc_;     \
   } while (0)
 
-int enqueue_solve(dyson_plan p, int K, cudaStream_t s, bool cap) {
+// The plan's buffers seen from frequency k0 on: every per-frequency array
+// advanced by k0 frequencies, every per-slot array by k0 * nb slots (byte
+// strides of the form's precision where the kernels read the buffer in it).
+// Kernels index frequencies from blockIdx.y, so a launch over this view with K
+// frequencies works on frequencies k0 .. k0 + K - 1 of the plan.
+Bufs sub_bufs(const Geo& g, const Bufs& b, bool mixed, int k0) {
+  if (k0 == 0) return b;
+  Bufs s = b;
+  const size_t K0 = (size_t)k0, S0 = K0 * g.nb, Ndd = g.Ndd, nsub = (size_t)g.Lx * g.W;
+  const size_t cs = mixed ? sizeof(cxf) : sizeof(cxd), Lx2 = (size_t)g.Lx * g.Lx;
+  auto adv = [](auto* ptr, size_t bytes) {
+    using T = std::remove_pointer_t<decltype(ptr)>;
+    return ptr ? reinterpret_cast<T*>(reinterpret_cast<char*>(const_cast<std::remove_const_t<T>*>(ptr)) + bytes)
+               : ptr;
+  };
+  s.omega = b.omega + K0;
+  s.sigma = b.sigma + K0 * g.N;
+  s.g = adv(reinterpret_cast<char*>(b.g), K0 * g.p * nsub * g.W * cs);
+  s.g64 = b.g64 ? b.g64 + K0 * g.p * nsub * g.W : nullptr;
+  s.diagB = b.diagB + K0 * Ndd;
+  s.offB = b.offB ? b.offB + K0 * g.p * nsub : nullptr;
+  s.off2 = b.off2 ? b.off2 + K0 * g.p * nsub : nullptr;
+  s.Q = b.Q + K0 * (g.k_max + g.nb) * Ndd;
+  s.acc = b.acc + K0 * Ndd;
+  s.u = b.u + S0 * Ndd;
+  s.v1 = b.v1 ? b.v1 + S0 * Ndd : nullptr;
+  s.v2 = b.v2 ? b.v2 + S0 * Ndd : nullptr;
+  s.v3 = b.v3 ? b.v3 + S0 * Ndd : nullptr;
+  s.yscr = adv(reinterpret_cast<char*>(b.yscr), S0 * g.p * nsub * cs);
+  s.bnd = adv(b.bnd, S0 * g.p * 2 * g.A * cs);
+  s.ifv = adv(b.ifv, S0 * IF_N * nifc(g) * cs);
+  s.pre = adv(b.pre, K0 * nifc(g) * 3 * cs);
+  s.lan = b.lan + K0 * (g.k_max + g.nb) * 2 * g.nb;
+  s.maxT = b.maxT + K0;
+  s.st = b.st + K0 * ST_N;
+  s.out = b.out + K0 * g.N;
+  s.sweeps = b.sweeps ? b.sweeps + S0 * g.p : nullptr;
+  s.lpt = b.lpt ? b.lpt + K0 * g.p * 2 * Lx2 : nullptr;
+  s.lpm = adv(reinterpret_cast<char*>(b.lpm), K0 * (g.p > 1 ? g.p - 1 : 0) * Lx2 * cs);
+  s.lpg = b.lpg ? b.lpg + K0 * g.p * nsub * g.W : nullptr;
+  return s;
+}
+
+// One batch of K frequencies (from the view b) on stream s.  (Running the
+// layer preconditioner's build beside the factorization on a second branch
+// was measured slower: the two kernels compete for issue slots.)
+int enqueue_range(dyson_plan p, const Bufs& b, int K, int* status, cudaStream_t s, bool cap) {
   const Geo& g = p->g;
-  p->n_prof = 0;
-  if (g.nb > 1) RUN(DYSON_KERNEL_INIT, "init", launch_init_block(g, p->b, K, s));
-  else RUN(DYSON_KERNEL_INIT, "init", launch_init(g, p->b, K, s));
-  if (p->mixed) RUN(DYSON_KERNEL_FACTOR, "factor", (launch_factor<double, float>(g, p->b, K, s)));
-  else RUN(DYSON_KERNEL_FACTOR, "factor", (launch_factor<double, double>(g, p->b, K, s)));
+  if (g.nb > 1) RUN(DYSON_KERNEL_INIT, "init", launch_init_block(g, b, K, s));
+  else RUN(DYSON_KERNEL_INIT, "init", launch_init(g, b, K, s));
+  if (p->mixed) RUN(DYSON_KERNEL_FACTOR, "factor", (launch_factor<dfl, float>(g, b, K, s)));
+  else RUN(DYSON_KERNEL_FACTOR, "factor", (launch_factor<double, double>(g, b, K, s)));
   if (g.p > 1) {
-    if (p->mixed) RUN(DYSON_KERNEL_PRECOND, "precond", launch_precond<float>(g, p->b, K, s));
-    else RUN(DYSON_KERNEL_PRECOND, "precond", launch_precond<double>(g, p->b, K, s));
+    if (p->mixed) RUN(DYSON_KERNEL_PRECOND, "precond", launch_precond<float>(g, b, K, s));
+    else RUN(DYSON_KERNEL_PRECOND, "precond", launch_precond<double>(g, b, K, s));
   }
   if (g.p > 1) {
     for (int j = 0; j < g.k_max / g.nb; ++j) {      // (block) Lanczos steps
-      if (p->mixed) RUN(DYSON_KERNEL_XMATVEC, "xmatvec", launch_xmatvec<float>(g, p->b, K, j, 1, g.nb, s));
-      else RUN(DYSON_KERNEL_XMATVEC, "xmatvec", launch_xmatvec<double>(g, p->b, K, j, 0, g.nb, s));
-      if (g.nb > 1) RUN(DYSON_KERNEL_LANCZOS, "lanczos", launch_block_lanczos(g, p->b, K, j, s));
-      else RUN(DYSON_KERNEL_LANCZOS, "lanczos", launch_lanczos(g, p->b, K, j, s));
+      if (p->mixed) RUN(DYSON_KERNEL_XMATVEC, "xmatvec", launch_xmatvec<float>(g, b, K, j, 1, g.nb, s));
+      else RUN(DYSON_KERNEL_XMATVEC, "xmatvec", launch_xmatvec<double>(g, b, K, j, 0, g.nb, s));
+      if (g.nb > 1) RUN(DYSON_KERNEL_LANCZOS, "lanczos", launch_block_lanczos(g, b, K, j, s));
+      else RUN(DYSON_KERNEL_LANCZOS, "lanczos", launch_lanczos(g, b, K, j, s));
     }
   }
-  RUN(DYSON_KERNEL_FINALIZE, "finalize", launch_finalize(g, p->b, K, s));
-  RUN(DYSON_KERNEL_STATUS, "status", launch_status(g, p->b, K, p->status_d, s));
+  RUN(DYSON_KERNEL_FINALIZE, "finalize", launch_finalize(g, b, K, s));
+  RUN(DYSON_KERNEL_STATUS, "status", launch_status(g, b, K, status, s));
+  return DYSON_OK;
+}
+
+// Groups a batch of K frequencies is split into (at least two frequencies each).
+int groups_for(dyson_plan p, int K) {
+  int G = p->ngroups;
+  while (G > 1 && K < 2 * G) --G;
+  return G;
+}
+
+// The whole solve.  With frequency groups, contiguous index ranges run as
+// parallel branches (forked from and joined back into s): a launch of one
+// group waits only for that group's previous step, so the slowest frequency's
+// chain of X-matvecs is not held back by every frequency's Lanczos step and
+// factorization, and the faster groups fill the SMs it leaves idle.
+int enqueue_solve(dyson_plan p, int K, cudaStream_t s, bool cap) {
+  p->n_prof = 0;
+  const int G = groups_for(p, K);
+  if (G <= 1) return enqueue_range(p, p->b, K, p->status_d, s, cap);
+  CK(cudaEventRecord(p->gev[0], s));
+  int k0 = 0;
+  for (int gi = 0; gi < G; ++gi) {
+    const int Kg = K / G + (gi < K % G ? 1 : 0);
+    CK(cudaStreamWaitEvent(p->gs[gi], p->gev[0], 0));
+    const Bufs sb = sub_bufs(p->g, p->b, p->mixed, k0);
+    int rc = enqueue_range(p, sb, Kg, p->status_d + k0, p->gs[gi], cap);
+    if (rc) return rc;
+    CK(cudaEventRecord(p->gev[1 + gi], p->gs[gi]));
+    CK(cudaStreamWaitEvent(s, p->gev[1 + gi], 0));
+    k0 += Kg;
+  }
   return DYSON_OK;
 }
 
@@ -358,7 +440,7 @@ int autotune(dyson_plan p, int K, cudaStream_t s) {
   Geo& g = p->g;
   if (g.nb > 1) LK(launch_init_block(g, p->b, K, s));
   else LK(launch_init(g, p->b, K, s));
-  if (p->mixed) LK((launch_factor<double, float>(g, p->b, K, s)));
+  if (p->mixed) LK((launch_factor<dfl, float>(g, p->b, K, s)));
   else LK((launch_factor<double, double>(g, p->b, K, s)));
   if (p->mixed) LK(launch_precond<float>(g, p->b, K, s));
   else LK(launch_precond<double>(g, p->b, K, s));
@@ -415,7 +497,8 @@ int get_graph(dyson_plan p, int K, cudaGraphExec_t* out) {
   }
   if (e != cudaSuccess) return fail(DYSON_E_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
   cudaGraphExec_t exec;
-  e = cudaGraphInstantiate(&exec, graph, 0);
+  // kernel nodes keep the priority of the stream they were captured from
+  e = cudaGraphInstantiate(&exec, graph, cudaGraphInstantiateFlagUseNodePriority);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) return fail(DYSON_E_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
   p->graphs[K] = exec;
@@ -513,12 +596,38 @@ int dyson_plan_create(const dyson_geometry* geom, dyson_plan* out) {
   b.off2 = p->g.penta ? at<cxd>(p, B_OFF2) : nullptr;
   b.lpt = p->g.lpre ? at<cxf>(p, B_LPT) : nullptr;
   b.lpm = p->g.lpre ? (void*)at<char>(p, B_LPM) : nullptr;
+  b.lpg = p->g.lpre ? at<cxf>(p, B_LPG) : nullptr;
   p->status_d = at<int>(p, B_STATUS);
   p->profile = false;
   p->tuned = false;
   p->tune_candidates = 0;
   p->tune_ms_heuristic = p->tune_ms_best = 0.f;
   p->n_prof = 0;
+  // frequency groups: not with the shared wide-slice factor workspace
+  p->ngroups = 1;
+  if (p->g.p > 1 && !b.fwork) {
+    p->ngroups = geom->freq_groups > 0 ? geom->freq_groups : DY_FREQ_GROUPS;
+    if (p->ngroups > DY_MAX_GROUPS) p->ngroups = DY_MAX_GROUPS;
+  }
+  if (p->ngroups > 1) {
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);      // hi: the greatest priority (numerically lowest)
+    for (int gi = 0; gi < p->ngroups && e == cudaSuccess; ++gi) {
+      cudaStream_t st;
+      const int prio = gi == 0 ? hi : (gi == 1 && hi < lo ? hi + 1 : lo);
+      e = cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, prio);
+      if (e == cudaSuccess) p->gs.push_back(st);
+    }
+    for (int gi = 0; gi <= p->ngroups && e == cudaSuccess; ++gi) {
+      cudaEvent_t ev;
+      e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+      if (e == cudaSuccess) p->gev.push_back(ev);
+    }
+  }
+  if (e != cudaSuccess) {
+    dyson_plan_destroy(p);
+    return fail(DYSON_E_CUDA, std::string("plan streams: ") + cudaGetErrorString(e));
+  }
   *out = p;
   return DYSON_OK;
 }
@@ -529,6 +638,8 @@ int dyson_plan_destroy(dyson_plan p) {
   cudaDeviceSynchronize();
   for (auto& kv : p->graphs) cudaGraphExecDestroy(kv.second);
   for (auto e : p->evs) cudaEventDestroy(e);
+  for (auto e : p->gev) cudaEventDestroy(e);
+  for (auto st : p->gs) cudaStreamDestroy(st);
   cudaStreamDestroy(p->cap);
   cudaFree(p->arena);
   delete p;

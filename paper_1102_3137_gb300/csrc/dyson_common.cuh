@@ -18,6 +18,7 @@
 #include <string>
 
 #include <cuda_runtime.h>
+#include "dfl.cuh"
 
 #define DY_MAXP 16          // largest cluster (one CTA per subdomain)
 #define DY_THREADS 256      // threads per CTA of every solver kernel
@@ -27,6 +28,8 @@
 #define DY_MAXNB 4          // largest Lanczos block size
 #define DY_LPRE_MAXLX 160   // widest interface line the exact layer preconditioner takes
 #define DY_LPRE_MAXW 32     // widest slice it takes
+#define DY_FREQ_GROUPS 4    // default frequency groups of a solve (parallel graph branches)
+#define DY_MAX_GROUPS 8
 #define DY_BLOCK_H 1024     // block Lanczos: k_max * nb bound (CGS2 coefficients kept in shared memory)
 #define DY_FACTOR_CTAS 304  // persistent grid of the wide-slice factor kernel (2 per SM on 152 SMs)
 
@@ -198,6 +201,7 @@ struct Bufs {
   unsigned long long* sweeps;  // [K*nb][p] subdomain sweeps performed (work accounting)
   cxd* fwork;           // [DY_FACTOR_CTAS][2][W][W] wide-slice factor workspace (W > 64 only)
   cx<float>* lpt;       // [K][p][2][Lx][Lx] boundary-row surface Green's functions (lpre)
+  cx<float>* lpg;       // [K][p][Lx][W][W] complex64 slice factors of that recursion (lpre scratch)
   void* lpm;            // [K][p-1][Lx][Lx] inverse layer blocks of S, precision of the form (lpre)
 };
 

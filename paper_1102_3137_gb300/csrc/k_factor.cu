@@ -178,8 +178,8 @@ __global__ void __launch_bounds__(DY_THREADS) k_factor(Geo g, Bufs b) {
         C acc = {0, 0};
         for (int c = lane; c < W; c += 32) acc = cfma(Bm[j * W + c], prevc[wid * W + c], acc);
         for (int off = 16; off > 0; off >>= 1) {
-          acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
-          acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+          acc.x += shfl_xor_any(acc.x, off);
+          acc.y += shfl_xor_any(acc.y, off);
         }
         if (lane == 0) o2[(size_t)(s < s2 ? s : s2) * W + j] = cconv<double>((-t) * acc);
       }
@@ -457,12 +457,6 @@ __global__ void __launch_bounds__(DY_THREADS) k_precond(Geo g, Bufs b) {
 
 template <typename R, typename S>
 cudaError_t launch_factor(const Geo& g, const Bufs& b, int K, cudaStream_t st) {
-  if (g.lpre) {
-    // the boundary-row Green's functions for the layer preconditioner park their
-    // slice factors in b.g, so they run before the factorization fills it
-    cudaError_t e = launch_surface(g, b, K, st);
-    if (e != cudaSuccess) return e;
-  }
   if (g.W > DY_MAXW_SMEM) {
     // wide slices: FP64 recursion in global memory (both forms recurse in FP64)
     if (sizeof(R) != sizeof(double) || g.W > DY_MAXW || !b.fwork) return cudaErrorInvalidValue;
@@ -477,13 +471,17 @@ cudaError_t launch_factor(const Geo& g, const Bufs& b, int K, cudaStream_t st) {
   return cudaGetLastError();
 }
 template cudaError_t launch_factor<double, double>(const Geo&, const Bufs&, int, cudaStream_t);
-template cudaError_t launch_factor<double, float>(const Geo&, const Bufs&, int, cudaStream_t);
+template cudaError_t launch_factor<dfl, float>(const Geo&, const Bufs&, int, cudaStream_t);
 template cudaError_t launch_factor<float, float>(const Geo&, const Bufs&, int, cudaStream_t);
 
 template <typename R>
 cudaError_t launch_precond(const Geo& g, const Bufs& b, int K, cudaStream_t st) {
   if (g.p < 2) return cudaSuccess;
-  if (g.lpre) return launch_layer_inv<R>(g, b, K, st);
+  if (g.lpre) {
+    cudaError_t e = launch_surface(g, b, K, st);
+    if (e != cudaSuccess) return e;
+    return launch_layer_inv<R>(g, b, K, st);
+  }
   k_precond<R><<<dim3(g.p - 1, K), DY_THREADS, 0, st>>>(g, b);
   return cudaGetLastError();
 }

@@ -89,9 +89,7 @@ __global__ void __launch_bounds__(DY_THREADS, 2) k_surface(Geo g, Bufs b) {
   cxf_* fcol = prow + W;
   cxf_* Vt = fcol + W;                            // [W][ldv] boundary columns of G_{s,s'}, top row
   cxf_* Vb = Vt + (size_t)W * ldv;                // same for the bottom row
-  // the slice factors are parked in the plan's factor buffer, which the
-  // factorization that follows overwrites
-  cxf_* gsv = reinterpret_cast<cxf_*>(b.g) + ((size_t)f * g.p + i) * (size_t)Lx * n;
+  cxf_* gsv = b.lpg + ((size_t)f * g.p + i) * (size_t)Lx * n;   // own scratch: runs beside the factorization
   cxf_* Pt = b.lpt + (((size_t)f * g.p + i) * 2 + 0) * (size_t)Lx * Lx;
   cxf_* Pb = b.lpt + (((size_t)f * g.p + i) * 2 + 1) * (size_t)Lx * Lx;
   const float t = d2f_bits(g.t), t2 = t * t;

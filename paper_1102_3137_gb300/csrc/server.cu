@@ -40,10 +40,10 @@ double now_s() {
 
 std::string geom_key(const dyson_geometry& g) {
   char buf[256];
-  std::snprintf(buf, sizeof(buf), "%d|%d,%d,%d|%.17g|%.17g|%d|%d|%d|%.17g|%d|%.17g|%d|%d|%.17g|%d|%d", g.dim,
+  std::snprintf(buf, sizeof(buf), "%d|%d,%d,%d|%.17g|%.17g|%d|%d|%d|%.17g|%d|%.17g|%d|%d|%.17g|%d|%d|%d", g.dim,
                 g.L[0], g.L[1], g.dim == 3 ? g.L[2] : 1, g.t, g.mu, g.p, g.k_max, g.precision,
                 g.krylov_tol, g.krylov_maxit, g.refine_tol, g.refine_max, g.max_freqs, g.eta,
-                g.block_size > 1 ? g.block_size : 1, g.precond);
+                g.block_size > 1 ? g.block_size : 1, g.precond, g.freq_groups);
   return buf;
 }
 

@@ -37,7 +37,8 @@ class dyson_geometry(C.Structure):
                 ("p", C.c_int), ("k_max", C.c_int), ("precision", C.c_int),
                 ("krylov_tol", C.c_double), ("krylov_maxit", C.c_int),
                 ("refine_tol", C.c_double), ("refine_max", C.c_int), ("max_freqs", C.c_int),
-                ("eta", C.c_double), ("block_size", C.c_int), ("precond", C.c_int)]
+                ("eta", C.c_double), ("block_size", C.c_int), ("precond", C.c_int),
+                ("freq_groups", C.c_int)]
 
 
 class dyson_request(C.Structure):
@@ -169,7 +170,7 @@ def _stream(stream):
 
 def make_geometry(L, t=-1.0, mu=0.0, p=1, k_max=16, precision=DYSON_FP64, max_freqs=1,
                   krylov_tol=0.0, krylov_maxit=0, refine_tol=0.0, refine_max=0, eta=0.0,
-                  block_size=1, precond=0):
+                  block_size=1, precond=0, freq_groups=0):
     g = dyson_geometry()
     g.dim = len(L)
     for d in range(3):
@@ -180,6 +181,7 @@ def make_geometry(L, t=-1.0, mu=0.0, p=1, k_max=16, precision=DYSON_FP64, max_fr
     g.eta = float(eta)
     g.block_size = int(block_size)
     g.precond = int(precond)
+    g.freq_groups = int(freq_groups)
     return g
 
 
