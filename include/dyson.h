@@ -320,6 +320,14 @@ int dyson_plan_set_profiling(dyson_plan plan, int on);
 int dyson_profile_read(dyson_plan plan, int max_kernels, int* kinds, float* ms, int* n);
 
 /*
+ * The same kernels as start and end times in ms from the earliest kernel start
+ * of that solve (kernels of different frequency groups overlap in time), for
+ * the time the GPU spends in one kind of kernel: the union of its intervals.
+ * Either output may be NULL; at most max_kernels written; *n as above.
+ */
+int dyson_profile_spans(dyson_plan plan, int max_kernels, float* start_ms, float* end_ms, int* n);
+
+/*
  * Work accounting of the last dyson_solve: sweeps[K][p] receives the number
  * of block forward/back substitutions (each reads the subdomain's stored
  * g_s twice) that the CTA of subdomain i performed for frequency k (summed

@@ -773,6 +773,28 @@ int dyson_profile_read(dyson_plan p, int max_kernels, int* kinds, float* ms, int
   return DYSON_OK;
 }
 
+int dyson_profile_spans(dyson_plan p, int max_kernels, float* start_ms, float* end_ms, int* n) {
+  int rc;
+  if ((rc = check_plan(p))) return rc;
+  if (!n) return fail(DYSON_E_BAD_ARG, "n is NULL");
+  if (!p->profile) return fail(DYSON_E_BAD_ARG, "profiling is off for this plan");
+  CK(cudaDeviceSynchronize());
+  *n = p->n_prof;
+  // offsets from the earliest start event of the sequence (kernels of different
+  // frequency groups run concurrently, so launch order is not time order)
+  int first = 0;
+  for (int k = 1; k < p->n_prof; ++k) {
+    float d = 0.f;
+    CK(cudaEventElapsedTime(&d, p->evs[2 * first], p->evs[2 * k]));
+    if (d < 0.f) first = k;
+  }
+  for (int k = 0; k < p->n_prof && k < max_kernels; ++k) {
+    if (start_ms) CK(cudaEventElapsedTime(&start_ms[k], p->evs[2 * first], p->evs[2 * k]));
+    if (end_ms) CK(cudaEventElapsedTime(&end_ms[k], p->evs[2 * first], p->evs[2 * k + 1]));
+  }
+  return DYSON_OK;
+}
+
 int dyson_lanczos_basis(dyson_plan p, int k, int nvec, double* Q) {
   int rc;
   if ((rc = check_plan(p))) return rc;

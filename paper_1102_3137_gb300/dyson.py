@@ -92,6 +92,7 @@ def load(path: str = LIB_PATH):
         "dyson_xmatvec": ([P, I, P, P, P, P, P, I, P], I),
         "dyson_plan_set_profiling": ([P, I], I),
         "dyson_profile_read": ([P, I, P, P, P], I),
+        "dyson_profile_spans": ([P, I, P, P, P], I),
         "dyson_work_counters": ([P, I, P], I),
         "dyson_lanczos_basis": ([P, I, I, P], I),
         "dyson_subdomain_diag_noalloc": ([C.POINTER(dyson_geometry), I, P, P, P, P, P], I),
@@ -307,6 +308,16 @@ def dyson_profile_read(plan, max_kernels=4096):
                                      C.addressof(n)))
     k = min(n.value, max_kernels)
     return kinds[:k].copy(), ms[:k].astype(np.float64)
+
+
+def dyson_profile_spans(plan, max_kernels=4096):
+    """(start_ms, end_ms) of every profiled kernel of the last solve, from its earliest start."""
+    a = np.zeros(max_kernels, np.float32)
+    e = np.zeros(max_kernels, np.float32)
+    n = C.c_int()
+    _check(load().dyson_profile_spans(plan, max_kernels, a.ctypes.data, e.ctypes.data, C.addressof(n)))
+    k = min(n.value, max_kernels)
+    return a[:k].astype(np.float64), e[:k].astype(np.float64)
 
 
 def dyson_work_counters(plan, K, p):
