@@ -123,7 +123,7 @@ typedef struct {
                          of the solve's CUDA graph on its own stream, the lowest-index group
                          at the highest stream priority.  Frequencies stay independent, so
                          results do not depend on the grouping.  Plans whose slice width
-                         exceeds 64 always use one batch. */
+                         exceeds 64 always use one batch; the serving loop takes 0 as 1. */
 } dyson_geometry;
 
 /* Library version string. */

@@ -31,7 +31,7 @@ using cxf_ = cx<float>;
 // memory by the sweep operator on the full matrix (pivots on the diagonal;
 // Im of the Dyson diagonal keeps them away from zero).  Thread t owns column
 // t % n and every (256 / n)-th row from t / n.
-__device__ void sweep_invert_f(cxf_* A, int n, cxf_* prow, cxf_* fcol) {
+__device__ __forceinline__ void sweep_invert_f(cxf_* A, int n, cxf_* prow, cxf_* fcol) {
   const int nrp = DY_THREADS / n;
   const int c = threadIdx.x % n, r0 = threadIdx.x / n;
   const bool act = r0 < nrp;
@@ -60,7 +60,8 @@ __device__ void sweep_invert_f(cxf_* A, int n, cxf_* prow, cxf_* fcol) {
 }
 
 // C = alpha X Y + beta D for W x W shared matrices (D may alias nothing, may be null)
-__device__ void small_matmul(cxf_* C, const cxf_* X, const cxf_* Y, int W, float alpha, const cxf_* D) {
+__device__ __forceinline__ void small_matmul(cxf_* C, const cxf_* X, const cxf_* Y, int W, float alpha,
+                                             const cxf_* D) {
   for (int e = threadIdx.x; e < W * W; e += DY_THREADS) {
     const int r = e / W, c = e - r * W;
     cxf_ acc = {0.f, 0.f};
@@ -71,16 +72,41 @@ __device__ void small_matmul(cxf_* C, const cxf_* X, const cxf_* Y, int W, float
   }
 }
 
+// The same for W = 32 with four rows per thread sharing each load of Y:
+// lane = column, warp = first row, rows warp + 8 j.
+__device__ __forceinline__ void small_matmul32(cxf_* C, const cxf_* X, const cxf_* Y, float alpha,
+                                               const cxf_* D) {
+  constexpr int W = 32;
+  const int c = threadIdx.x & 31, r0 = threadIdx.x >> 5;
+  cxf_ acc[4] = {};
+#pragma unroll 8
+  for (int k = 0; k < W; ++k) {
+    const cxf_ y = Y[k * W + c];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[j] = cfma(X[(r0 + 8 * j) * W + k], y, acc[j]);
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int e = (r0 + 8 * j) * W + c;
+    cxf_ v = cxf_{alpha * acc[j].x, alpha * acc[j].y};
+    if (D) v = v + D[e];
+    C[e] = v;
+  }
+}
+
 constexpr int SURF_MAXW = 32;
 constexpr int SURF_NG = DY_THREADS / 32;                             // column groups (one per warp)
 constexpr int SURF_NCOL = (DY_LPRE_MAXLX + SURF_NG - 1) / SURF_NG;   // columns per thread at most
 
 __host__ __device__ __forceinline__ int surf_ldv(int Lx) { return Lx | 1; }   // odd stride: no bank conflicts
 
+// WT: the slice width at compile time (32, the common 2D strip), or 0 for any
+// width up to 32 read from the geometry
+template <int WT>
 __global__ void __launch_bounds__(DY_THREADS, 2) k_surface(Geo g, Bufs b) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int i = blockIdx.x, f = blockIdx.y;
-  const int W = g.W, Lx = g.Lx, w = g.h[i], n = W * W, ldv = surf_ldv(Lx);
+  const int W = WT ? WT : g.W, Lx = g.Lx, w = g.h[i], n = W * W, ldv = surf_ldv(Lx);
   const bool need_top = i < g.p - 1, need_bot = i > 0;
   cxf_* Gs = reinterpret_cast<cxf_*>(smem_raw);   // g_s
   cxf_* Gd = Gs + n;                              // G_ss
@@ -129,9 +155,15 @@ __global__ void __launch_bounds__(DY_THREADS, 2) k_surface(Geo g, Bufs b) {
     if (s == Lx - 1) {
       for (int e = threadIdx.x; e < n; e += DY_THREADS) Gd[e] = Gs[e];
     } else {
-      small_matmul(Tm, Gs, Gd, W, 1.f, nullptr);          // g_s G_{s+1,s+1}
-      __syncthreads();
-      small_matmul(Gd, Tm, Gs, W, t2, Gs);                 // g_s + t^2 g_s G g_s
+      if constexpr (WT == 32) {
+        small_matmul32(Tm, Gs, Gd, 1.f, nullptr);          // g_s G_{s+1,s+1}
+        __syncthreads();
+        small_matmul32(Gd, Tm, Gs, t2, Gs);                 // g_s + t^2 g_s G g_s
+      } else {
+        small_matmul(Tm, Gs, Gd, W, 1.f, nullptr);
+        __syncthreads();
+        small_matmul(Gd, Tm, Gs, W, t2, Gs);
+      }
       cxf_ gr[SURF_MAXW];                                  // row `lane` of g_s (symmetric)
 #pragma unroll
       for (int k = 0; k < SURF_MAXW; ++k) gr[k] = (lane < W && k < W) ? Gs[k * W + lane] : cxf_{0.f, 0.f};
@@ -226,9 +258,15 @@ cudaError_t launch_surface(const Geo& g, const Bufs& b, int K, cudaStream_t st) 
   if (!g.lpre) return cudaSuccess;
   if (g.W > SURF_MAXW || g.Lx > DY_LPRE_MAXLX) return cudaErrorInvalidValue;
   const size_t smem = dyson_internal_surface_smem(g);
-  cudaError_t e = raise_smem_limit((const void*)k_surface, smem);
-  if (e != cudaSuccess) return e;
-  k_surface<<<dim3(g.p, K), DY_THREADS, smem, st>>>(g, b);
+  if (g.W == 32) {
+    cudaError_t e = raise_smem_limit((const void*)k_surface<32>, smem);
+    if (e != cudaSuccess) return e;
+    k_surface<32><<<dim3(g.p, K), DY_THREADS, smem, st>>>(g, b);
+  } else {
+    cudaError_t e = raise_smem_limit((const void*)k_surface<0>, smem);
+    if (e != cudaSuccess) return e;
+    k_surface<0><<<dim3(g.p, K), DY_THREADS, smem, st>>>(g, b);
+  }
   return cudaGetLastError();
 }
 

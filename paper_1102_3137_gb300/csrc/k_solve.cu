@@ -8,11 +8,16 @@ namespace {
 // One step of complex-symmetric Lanczos on X with the bilinear form
 // (Sec. 2.1, Freund et al.), full CGS2 re-orthogonalisation in the same form,
 // and the three-vector update of diag(Q T Q^T) (Sec. 2.3 after Eq. 9).
+// One cluster per frequency; SPLIT CTAs share each subdomain's entries
+// (interleaved), so the FP64 work of a frequency spreads over SPLIT * p SMs.
+template <int SPLIT>
 __global__ void __launch_bounds__(DY_THREADS) k_lanczos(Geo g, Bufs b, int j) {
   cg::cluster_group cl = cg::this_cluster();
   __shared__ RedSmem rs;
   __shared__ cxd hs[KMAX_SMEM];
-  const int i = blockIdx.x, kf = blockIdx.y, p = g.p;
+  const int i = blockIdx.x / SPLIT, part = blockIdx.x - i * SPLIT, kf = blockIdx.y, p = g.p * SPLIT;
+  const int e0 = threadIdx.x + part * DY_THREADS;
+  constexpr int ES = SPLIT * DY_THREADS;
   int* st = b.st + (size_t)kf * ST_N;
   if (st[ST_DONE]) return;
   int phase = 0;
@@ -30,13 +35,13 @@ __global__ void __launch_bounds__(DY_THREADS) k_lanczos(Geo g, Bufs b, int j) {
   const double maxT_prev = b.maxT[kf];
 
   cxd v1[1] = {{0, 0}};
-  for (int e = threadIdx.x; e < n; e += DY_THREADS) {
+  for (int e = e0; e < n; e += ES) {
     size_t k = own_idx(g, i, e, nsub);
     v1[0] = cfma(qj[k], u[k], v1[0]);
   }
   cluster_sum<1>(cl, rs, phase, p, v1);
   const cxd alpha = v1[0];
-  for (int e = threadIdx.x; e < n; e += DY_THREADS) {
+  for (int e = e0; e < n; e += ES) {
     size_t k = own_idx(g, i, e, nsub);
     cxd rv = cfma(-alpha, qj[k], u[k]);
     if (qm) rv = cfma(-beta_j, qm[k], rv);
@@ -47,7 +52,7 @@ __global__ void __launch_bounds__(DY_THREADS) k_lanczos(Geo g, Bufs b, int j) {
       cxd h8[8];
 #pragma unroll
       for (int m = 0; m < 8; ++m) h8[m] = cxd{0, 0};
-      for (int e = threadIdx.x; e < n; e += DY_THREADS) {
+      for (int e = e0; e < n; e += ES) {
         size_t k = own_idx(g, i, e, nsub);
         cxd rv = r[k];
 #pragma unroll
@@ -58,7 +63,7 @@ __global__ void __launch_bounds__(DY_THREADS) k_lanczos(Geo g, Bufs b, int j) {
       if (threadIdx.x < 8 && c0 + threadIdx.x <= j) hs[c0 + threadIdx.x] = h8[threadIdx.x];
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < n; e += DY_THREADS) {
+    for (int e = e0; e < n; e += ES) {
       size_t k = own_idx(g, i, e, nsub);
       cxd rv = r[k];
       for (int m = 0; m <= j; ++m) rv = cfma(-hs[m], Q[(size_t)m * Ndd + k], rv);   // fused: 4 FP64 ops
@@ -67,7 +72,7 @@ __global__ void __launch_bounds__(DY_THREADS) k_lanczos(Geo g, Bufs b, int j) {
     __syncthreads();
   }
   cxd v2[2] = {{0, 0}, {0, 0}};
-  for (int e = threadIdx.x; e < n; e += DY_THREADS) {
+  for (int e = e0; e < n; e += ES) {
     size_t k = own_idx(g, i, e, nsub);
     cxd rv = r[k];
     v2[0] = cfma(rv, rv, v2[0]);
@@ -93,12 +98,12 @@ __global__ void __launch_bounds__(DY_THREADS) k_lanczos(Geo g, Bufs b, int j) {
   }
   if (!done) {
     const cxd ib = cinv(beta);
-    for (int e = threadIdx.x; e < n; e += DY_THREADS) {
+    for (int e = e0; e < n; e += ES) {
       size_t k = own_idx(g, i, e, nsub);
       r[k] = r[k] * ib;
     }
   }
-  if (i == 0 && threadIdx.x == 0) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
     lan[2 * j] = alpha;
     st[ST_STEPS] = j + 1;
     if (done) {
@@ -204,7 +209,8 @@ int dyson_internal_ring_candidates(const Geo& g, bool mixed, int* S, int* CR, in
 
 cudaError_t launch_lanczos(const Geo& g, const Bufs& b, int K, int j, cudaStream_t st) {
   if (g.k_max > KMAX_SMEM) return cudaErrorInvalidValue;
-  return launch_cluster(k_lanczos, dim3(g.p, K), g.p, 0, st, g, b, j);
+  if (2 * g.p <= 8) return launch_cluster(k_lanczos<2>, dim3(2 * g.p, K), 2 * g.p, 0, st, g, b, j);
+  return launch_cluster(k_lanczos<1>, dim3(g.p, K), g.p, 0, st, g, b, j);
 }
 
 cudaError_t launch_init(const Geo& g, const Bufs& b, int K, cudaStream_t st) {

@@ -320,7 +320,10 @@ int dyson_submit(dyson_server s, const dyson_request* r, uint64_t* ticket) {
     const uint64_t t = s->next_ticket++;
     Req& q = s->reqs[t];
     q.r = *r;
-    q.key = geom_key(r->geom);
+    // several requests already share the GPU: frequency groups inside one solve would
+    // only add graph branches, so the server runs each solve as one batch by default
+    if (q.r.geom.freq_groups == 0) q.r.geom.freq_groups = 1;
+    q.key = geom_key(q.r.geom);
     q.t_submit = now_s();
     s->queue.push_back(t);
     *ticket = t;

@@ -261,18 +261,24 @@ def test_square128_full_batch_sampled(precision, tol):
     info = pl.info(w.K)
     assert np.all((st & (D.DYSON_ST_NO_CONVERGENCE | D.DYSON_ST_BREAKDOWN)) == 0)
     assert np.all(info["steps"] == w.k)
-    q1n = (q1 / np.sqrt(q1 @ q1)).astype(complex)
     for k in (0, 31, 63):
         subs, X = oracle_parts(w, omega[k], V, sigma[k])
         stepwise_check(w, pl, k, subs, X, q1, out[k], info, tol)
-        # the GPU's X-matvec accuracy on this frequency
-        pm = D.Plan(w.L, w.t, w.mu, w.p, w.k, precision, max_freqs=1)
-        u = np.zeros((1, w.N), complex)
-        D.dyson_xmatvec(pm.handle, 1, omega[k:k + 1], V, np.ascontiguousarray(sigma[k:k + 1]),
-                        q1n[None].copy(), u)
+        # the GPU's X-matvec accuracy on this frequency, over the run's own Lanczos
+        # vectors (each interface solve stops at its tolerance, so the error differs
+        # from vector to vector)
+        sel = [0, 8, 16, 24, w.k - 1]
+        qs = np.ascontiguousarray(D.dyson_lanczos_basis(pl.handle, k, w.k, w.N)[sel])
+        ns = len(sel)
+        pm = D.Plan(w.L, w.t, w.mu, w.p, w.k, precision, max_freqs=ns)
+        u = np.zeros((ns, w.N), complex)
+        D.dyson_xmatvec(pm.handle, ns, np.full(ns, omega[k]), V,
+                        np.ascontiguousarray(np.repeat(sigma[k:k + 1], ns, axis=0)), qs, u)
         pm.close()
-        ux = X(q1n)
-        eps = max(float(np.linalg.norm(u[0] - ux) / np.linalg.norm(ux)), 1e-15)
+        eps = 1e-15
+        for c in range(ns):
+            ux = X(qs[c])
+            eps = max(eps, float(np.linalg.norm(u[c] - ux) / np.linalg.norm(ux)))
         base, sens = oracle_sensitivity(w, subs, X, q1, eps)
         assert relerr(out[k], base) <= max(tol, 10 * sens), (k, eps, sens)
 
@@ -294,3 +300,25 @@ def test_autotuner_times_candidates_and_keeps_results(precision):
         assert np.array_equal(pl.solve(omega, V, sigma, q1), ref)
     other = plan_for(w, precision)
     assert np.array_equal(other.solve(omega, V, sigma, q1), ref)
+
+
+def test_profiling_kinds_durations_and_spans():
+    """Per-kernel events inside the replayed graph: one INIT..STATUS sequence per
+    frequency group, durations equal to the spans, every span inside the solve,
+    and the X-matvec launches of different groups overlapping in time."""
+    w = wl((40, 37), 3, 6, K=8)
+    omega, V, sigma, q1 = I.make_inputs(w)
+    pl = plan_for(w, D.DYSON_MIXED, freq_groups=4)
+    D.dyson_plan_set_profiling(pl.handle, 1)
+    pl.solve(omega, V, sigma, q1)
+    pl.solve(omega, V, sigma, q1)
+    kinds, ms = D.dyson_profile_read(pl.handle)
+    t0, t1 = D.dyson_profile_spans(pl.handle)
+    assert len(kinds) == len(t0) == 4 * (5 + 2 * w.k)     # init, factor, precond, k x (xmatvec, lanczos), finalize, status
+    assert np.sum(kinds == 3) == 4 * w.k and np.sum(kinds == 4) == 4 * w.k
+    assert np.all(t0 >= 0.0) and np.all(t1 >= t0)
+    assert np.allclose(t1 - t0, ms, atol=2e-3)
+    xs, xe = t0[kinds == 3], t1[kinds == 3]
+    order = np.argsort(xs)
+    assert np.any(xs[order][1:] < xe[order][:-1])          # some launches overlap
+    pl.close()
