@@ -131,3 +131,21 @@ def test_cubic32_full_batch_sampled(precision, tol):
     for k in (0, w.K - 1):
         subs, X = oracle_parts(w, omega[k], V, sigma[k])
         stepwise_check(w, pl, k, subs, X, q1, out[k], info, tol)
+
+
+def test_square512_full_batch_sampled():
+    """512^2, K = 32 in one launch, p = 16 (clusters of 16 CTAs), k = 64: the largest
+    2D workload.  Both forms; the lowest frequency (the worst conditioned) checked step
+    by step against the oracle's X, which is factorised once for both."""
+    w = I.WORKLOADS["square512_K32_p16_k64"]
+    omega, V, sigma, q1 = I.make_inputs(w)
+    subs, X = oracle_parts(w, omega[0], V, sigma[0])
+    for precision, tol in ((D.DYSON_FP64, TOL_FP64), (D.DYSON_MIXED, TOL_MIXED)):
+        pl = plan_for(w, precision)
+        st = np.zeros(w.K, np.int32)
+        out = pl.solve(omega, V, sigma, q1, status=st)
+        info = pl.info(w.K)
+        assert np.all((st & (D.DYSON_ST_NO_CONVERGENCE | D.DYSON_ST_BREAKDOWN)) == 0)
+        assert np.all(np.isfinite(out))
+        assert stepwise_check(w, pl, 0, subs, X, q1, out[0], info, tol) == w.k
+        pl.close()
