@@ -29,6 +29,9 @@ Readings of the paper taken here (the paper is silent or garbled there):
     breakdown when |r^T r| <= 1e-14 ||r||_2^2                 (Sec. 2.1, 2.3)
   * the H solve of Eq. 6 is a direct block-LU solve of the full lattice
     (the paper does not say which solver it used).
+  * recursive decomposition (Sec. 2.3 end; 2D): a box is cut in two by one
+    interface line through its middle, the cut direction alternating level by
+    level; boxes of at most min_sites sites are inverted directly.
   * block Lanczos (not in the paper; for degenerate spectra of X): blocks are
     split by a column-by-column bilinear Gram-Schmidt QR (applied twice);
     a column whose pivot falls to 1e-12 max|T| is deflated to zero; the run
@@ -529,6 +532,70 @@ def lowrank_diag_block(L, periodic, t, mu, V, sigma_k, omega_k, Q1, p: int, k_ma
     if return_info:
         return res, dict(A=As, B=Bs, steps=len(As), status=status, diagB=subs.diagB, Q=Q)
     return res
+
+
+def recursive_diag(L, t, z, q1, k_max: int, min_sites: int = 64, first_cut: str = "x"):
+    """diag(H^-1) by the recursive decomposition of Sec. 2.3 (end): 2D only.
+
+    A box of the lattice (its principal submatrix of H, open at the box edges) is
+    cut into two halves by one interface line, alternating the cut direction
+    level by level, (d_x, d_y) = (2, 1), (1, 2), ... when first_cut = "x".  Its
+    diagonal is [diag of each half's inverse, by the same method one level down;
+    0 on the line] + diag(Q_k T_k Q_k^T) of X_box = H_box^-1 - blkdiag(H_1^-1,
+    H_2^-1, 0) (Eqs. 5-9 applied to the box), with the start vector q1
+    restricted to the box.  Boxes of at most min_sites sites are inverted
+    directly.  With k_max past every level's closure the result is exact.
+    Returns the diagonal in natural order.
+    """
+    Lx, Ly = L
+    z = np.asarray(z, dtype=np.complex128)
+    q1 = np.asarray(q1, dtype=np.float64)
+
+    def sites(x0, x1, y0, y1):
+        return np.array([x + Lx * y for y in range(y0, y1 + 1) for x in range(x0, x1 + 1)], dtype=np.int64)
+
+    def box_H(idx, nx, ny):
+        return dense_H((nx, ny), (False, False), t, z[idx])
+
+    def rec(x0, x1, y0, y1, cut):
+        nx, ny = x1 - x0 + 1, y1 - y0 + 1
+        idx = sites(x0, x1, y0, y1)
+        Hb = box_H(idx, nx, ny)
+        if idx.size <= min_sites or (cut == "x" and nx < 3) or (cut == "y" and ny < 3):
+            if idx.size <= min_sites or (nx < 3 and ny < 3):
+                return idx, np.diag(np.linalg.inv(Hb))
+            cut = "y" if cut == "x" else "x"
+        if cut == "x":
+            xm = (x0 + x1) // 2
+            halves = [(x0, xm - 1, y0, y1), (xm + 1, x1, y0, y1)]
+        else:
+            ym = (y0 + y1) // 2
+            halves = [(x0, x1, y0, ym - 1), (x0, x1, ym + 1, y1)]
+        nxt = "y" if cut == "x" else "x"
+        pos = {int(v): k for k, v in enumerate(idx)}
+        parts = []
+        for h in halves:
+            hidx, hdiag = rec(*h, nxt)
+            parts.append((np.array([pos[int(v)] for v in hidx]), hidx, hdiag))
+        d = np.zeros(idx.size, dtype=np.complex128)
+        Hh = [box_H(hidx, h[1] - h[0] + 1, h[3] - h[2] + 1) for (_, hidx, _), h in zip(parts, halves)]
+
+        def xmatvec(q):
+            v = np.linalg.solve(Hb, q)                                  # Eq. 6 on the box
+            w = np.zeros_like(v)
+            for (loc, _, _), Hhalf in zip(parts, Hh):
+                w[loc] = np.linalg.solve(Hhalf, q[loc])                 # Eq. 7: the halves
+            return v - w                                                # Eq. 8
+
+        acc = cs_lanczos(xmatvec, q1[idx].astype(np.complex128), k_max)[0]
+        for loc, _, hdiag in parts:
+            d[loc] = hdiag
+        return idx, d + acc
+
+    idx, d = rec(0, Lx - 1, 0, Ly - 1, first_cut)
+    out = np.zeros(Lx * Ly, dtype=np.complex128)
+    out[idx] = d
+    return out
 
 
 def xmatvec(L, periodic, t, mu, V, sigma_k, omega_k, p, q, eta: float = 0.0):

@@ -544,3 +544,42 @@ def test_block_of_one_is_the_scalar_recurrence():
     r1 = O.lowrank_diag(L, per, -1.0, 0.0, V, sigma, math.pi / 10, q1, p, 7)
     r2 = O.lowrank_diag_block(L, per, -1.0, 0.0, V, sigma, math.pi / 10, q1[:, None], p, 7)
     assert np.max(np.abs(r1 - r2)) / np.max(np.abs(r1)) < 1e-12
+
+
+# --------------------------------------------------------------------------- recursive decomposition
+
+
+def test_recursive_decomposition_exact_past_closure():
+    """Sec. 2.3 end: the method applied recursively, cuts alternating between the
+    axes, three levels deep on a 12 x 10 lattice; with the rank cap past every
+    level's closure it reproduces the dense inverse's diagonal (library inverse),
+    whichever axis is cut first."""
+    rng = np.random.default_rng(3)
+    L, N = (12, 10), 120
+    z = rng.uniform(-2, 2, N) + 1j * rng.uniform(0.2, 0.8, N)
+    q1 = rng.uniform(-1, 1, N)
+    exact = np.diag(np.linalg.inv(O.dense_H(L, (False, False), -1.0, z)))
+    for cut in ("x", "y"):
+        r = O.recursive_diag(L, -1.0, z, q1, 200, min_sites=20, first_cut=cut)
+        assert np.max(np.abs(r - exact)) / np.max(np.abs(exact)) < 1e-11
+    # truncated levels are an approximation, not the exact diagonal
+    r = O.recursive_diag(L, -1.0, z, q1, 6, min_sites=20)
+    assert np.max(np.abs(r - exact)) / np.max(np.abs(exact)) > 1e-3
+
+
+def test_recursive_one_level_is_the_two_strip_method():
+    """One level of the recursion (halves inverted directly) cut along y at the
+    middle line is the low-rank method with p = 2 strips, at any rank cap: the
+    same X and start vector, reached through dense solves instead of the slice
+    recursion and the full-lattice block LU."""
+    rng = np.random.default_rng(4)
+    L, N = (12, 11), 132
+    V = rng.uniform(0, 0.5, N)
+    sigma = rng.uniform(-1, 1, N) + 1j * rng.uniform(0.1, 0.6, N)
+    w = math.pi / 10
+    z = O.dyson_diagonal(w, 0.0, V, sigma)
+    q1 = rng.uniform(-1, 1, N)
+    for k in (4, 12, 20):
+        a = O.recursive_diag(L, -1.0, z, q1, k, min_sites=60, first_cut="y")
+        b = O.lowrank_diag(L, (False, False, False), -1.0, 0.0, V, sigma, w, q1, 2, k)
+        assert np.max(np.abs(a - b)) / np.max(np.abs(b)) < 1e-11
