@@ -417,7 +417,7 @@ def run_ours(a, rank, world, local_rank):
     line = dict(
         metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=a.steps, warmup=a.warmup,
         ms_per_step=ms_per_step, higher_is_better=True, scaling="weak", vs_baseline=None,
-        dtype="mixed c64/f64" if prec == D.DYSON_MIXED else "c128 (f64)",
+        dtype="mixed c64/f64 (c64 sweeps, 2xf32 slice recursion, f64 Lanczos and refinement)" if prec == D.DYSON_MIXED else "c128 (f64)",
         data="synthetic",
         config=dict(workload=a.workload, lattice="x".join(map(str, w.L)), K=w.K, p=w.p, k=w.k,
                     form=a.form, N=w.N, beta=w.beta,
