@@ -8,6 +8,19 @@ DYSON_MEM_DEVICE; one call may not mix the two.
 
 If libdyson.so is missing or cannot be loaded every call raises: there is no
 fallback implementation.
+
+Typical use (128 x 128 lattice, 4 strips, rank 32, 64 Matsubara frequencies):
+
+    from paper_1102_3137_gb300 import build, dyson as D
+    build.build()                                   # once: nvcc, sm_103a
+    plan = D.Plan((128, 128), t=-1.0, mu=0.0, p=4, k_max=32,
+                  precision=D.DYSON_MIXED, max_freqs=64)
+    diagG = plan.solve(omega, V, sigma, q1)         # complex128 [64][16384]
+
+Geometry options beyond the positional ones (keyword arguments of Plan and
+make_geometry): krylov_tol, krylov_maxit, refine_tol, refine_max, eta (> 0:
+real axis), block_size (2..4: block Lanczos, q1 then [block_size][N]),
+precond (DYSON_PRECOND_AUTO / _BANDED / _LAYER), freq_groups (0: default).
 """
 from __future__ import annotations
 
