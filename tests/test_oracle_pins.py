@@ -583,3 +583,29 @@ def test_recursive_one_level_is_the_two_strip_method():
         a = O.recursive_diag(L, -1.0, z, q1, k, min_sites=60, first_cut="y")
         b = O.lowrank_diag(L, (False, False, False), -1.0, 0.0, V, sigma, w, q1, 2, k)
         assert np.max(np.abs(a - b)) / np.max(np.abs(b)) < 1e-11
+
+
+def test_block_lanczos_partial_deflation_keeps_exactness():
+    """4 x 5 lattice, p = 2: X has rank m = 4.  With a block of 3 the third block
+    holds the one remaining direction of range(X): two of its columns deflate to
+    zero, the block keeps its width, and the diagonal is already exact (dense
+    library inverse); one more step finds the whole next block deflated
+    (terminated)."""
+    rng = np.random.default_rng(9)
+    L, N = (4, 5), 20
+    V = rng.uniform(0, 0.5, N)
+    sigma = rng.uniform(-1, 1, N) + 1j * rng.uniform(0.1, 0.6, N)
+    w = math.pi / 10
+    exact = np.diag(np.linalg.inv(O.dense_H(L, (False, False), -1.0, O.dyson_diagonal(w, 0.0, V, sigma))))
+    Q1 = rng.uniform(-1, 1, (N, 3))
+    r, info = O.lowrank_diag_block(L, (False, False, False), -1.0, 0.0, V, sigma, w, Q1, 2, 9,
+                                   return_info=True)
+    nrm = np.linalg.norm(info["Q"], axis=0)
+    assert info["steps"] == 3 and int((nrm == 0).sum()) == 2
+    kept = info["Q"][:, nrm > 0]
+    assert np.max(np.abs(kept.T @ kept - np.eye(kept.shape[1]))) < 1e-12
+    assert np.max(np.abs(r - exact)) / np.max(np.abs(exact)) < 1e-12
+    r2, info2 = O.lowrank_diag_block(L, (False, False, False), -1.0, 0.0, V, sigma, w, Q1, 2, 12,
+                                     return_info=True)
+    assert info2["status"] == O.STATUS_TERMINATED and info2["steps"] == 3
+    assert np.max(np.abs(r2 - exact)) / np.max(np.abs(exact)) < 1e-12
