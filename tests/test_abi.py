@@ -144,3 +144,21 @@ def test_null_plan_is_an_error(lib):
     z = np.zeros(4)
     with pytest.raises(D.DysonError):
         D.dyson_solve(None, 1, z[:1], z, np.zeros(4, complex), z, np.zeros(4, complex))
+
+
+def test_layer_preconditioner_limits(lib):
+    # 2D strips with Lx <= 160 and slice width <= 32 take the exact layer blocks
+    ok = D.make_geometry((160, 33), p=2, k_max=4, max_freqs=1, precond=D.DYSON_PRECOND_LAYER)
+    assert D.dyson_plan_footprint(ok) > 0
+    for L, p in (((161, 33), 2), ((64, 70), 2)):      # line too long; slice width 36 > 32
+        g = D.make_geometry(L, p=p, k_max=4, max_freqs=1, precond=D.DYSON_PRECOND_LAYER)
+        with pytest.raises(D.DysonError) as e:
+            D.dyson_plan_footprint(g)
+        assert e.value.code == -4
+        g.precond = D.DYSON_PRECOND_AUTO                 # falls back to the banded form
+        auto = D.dyson_plan_footprint(g)
+        g.precond = D.DYSON_PRECOND_BANDED
+        assert D.dyson_plan_footprint(g) == auto
+    g = D.make_geometry((160, 33), p=1, k_max=4, max_freqs=1, precond=D.DYSON_PRECOND_LAYER)
+    with pytest.raises(D.DysonError):                    # no interface: nothing to precondition
+        D.dyson_plan_footprint(g)
