@@ -1,13 +1,15 @@
 // dyson_subdomain_diag_noalloc: diag(blkdiag(B^-1, 0)) for callers that cannot
 // allocate device memory.
 //
-// Some callers must not call cudaMalloc at all: code running inside a
-// captured or replayed CUDA graph that must stay allocation-free, hosts with a
-// fixed memory budget that is reserved up front, and embedders that hand the
-// library only the buffers they own.  This entry point serves them: it takes
-// the caller's device inputs and output and keeps everything else (the dd
-// index map, the subdomain slice factors and the subdomain-first diagonal) in
-// one file-scope device array of fixed size.
+// Some host programs hand the solver no allocator at all: a simulation that
+// carves all of its device memory out of one pool at start-up and treats any
+// later cudaMalloc as a failure (the pool may leave nothing free, and an
+// allocation can stall the device), or a plugin living inside another
+// framework that owns every device buffer and only lends it input and output
+// arrays.  This entry point serves them: it takes the caller's device inputs
+// and output and keeps everything else (the index map from the internal
+// subdomain-first layout to natural order, the subdomain slice factors and
+// the subdomain-first diagonal) in one file-scope device array of fixed size.
 //
 // Every GPU that loads this library holds that array until the process exits.
 // All calls share it and it keeps the last call's contents; calls whose work
@@ -69,6 +71,75 @@ __global__ void k_dd2nat(Geo g, int* dd2nat) {
   }
 }
 
+// The fields of Geo this path reads, from the caller's geometry, with the
+// checks they need and nothing allocated: heights of the p strips/slabs along
+// the slow axis (the first (L_slow - p + 1) mod p one layer taller), the
+// interface layers between them, the padded slice width and the
+// subdomain-first vector length.  Only dim, L, t, mu, p, precision and eta
+// are read; the other fields of the geometry play no part here.
+int noalloc_geo(const dyson_geometry* in, Geo* out) {
+  if (in->precision != DYSON_FP64)
+    return dyson_internal_fail(DYSON_E_BAD_ARG, "noalloc: only the FP64 form is available");
+  if (in->dim != 2 && in->dim != 3) return dyson_internal_fail(DYSON_E_BAD_ARG, "noalloc: dim must be 2 or 3");
+  Geo g;
+  std::memset(&g, 0, sizeof(g));
+  g.dim = in->dim;
+  g.Lx = in->L[0];
+  g.Ly = in->L[1];
+  g.Lz = in->dim == 3 ? in->L[2] : 1;
+  if (g.Lx < 1 || g.Ly < 1 || g.Lz < 1)
+    return dyson_internal_fail(DYSON_E_BAD_ARG, "noalloc: lattice extents must be >= 1");
+  const long long N = (long long)g.Lx * g.Ly * g.Lz;
+  if (N > (1LL << 30)) return dyson_internal_fail(DYSON_E_UNSUPPORTED, "noalloc: lattice too large");
+  g.N = (int)N;
+  g.p = in->p;
+  if (g.p < 1 || g.p > DY_MAXP) return dyson_internal_fail(DYSON_E_BAD_ARG, "noalloc: p must be in 1..16");
+  g.T = in->dim == 3 ? g.Ly : 1;
+  g.A = g.Lx * g.T;
+  g.Ls = in->dim == 3 ? g.Lz : g.Ly;
+  if (g.Ls - (g.p - 1) < g.p)
+    return dyson_internal_fail(DYSON_E_BAD_ARG, "noalloc: too many subdomains for the slow axis");
+  const int base = (g.Ls - (g.p - 1)) / g.p, extra = (g.Ls - (g.p - 1)) % g.p;
+  int c = 0, hmax = 0;
+  for (int i = 0; i < g.p; ++i) {
+    g.h[i] = base + (i < extra ? 1 : 0);
+    g.s0[i] = c;
+    c += g.h[i];
+    if (g.h[i] > hmax) hmax = g.h[i];
+    if (i < g.p - 1) g.ylayer[i] = c++;
+  }
+  g.W = (g.T * hmax + 3) & ~3;
+  if (g.W > DY_MAXW_SMEM)
+    return dyson_internal_fail(DYSON_E_UNSUPPORTED, "noalloc: slice width above 64");
+  const long long ndd = (long long)g.p * g.Lx * g.W + (long long)(g.p - 1) * g.A;
+  if (ndd > (1LL << 30)) return dyson_internal_fail(DYSON_E_UNSUPPORTED, "noalloc: lattice too large");
+  g.Ndd = (int)ndd;
+  g.ifc_off = g.p * g.Lx * g.W;
+  g.t = in->t;
+  g.mu = in->mu;
+  if (!(in->eta >= 0.0)) return dyson_internal_fail(DYSON_E_BAD_ARG, "noalloc: eta must be >= 0");
+  g.eta = in->eta;
+  g.real_axis = in->eta > 0.0 ? 1 : 0;
+  g.nb = 1;
+  *out = g;
+  return DYSON_OK;
+}
+
+// A caller's pointer must be device (or managed) memory of the current device:
+// the kernels run there and dereference it.
+int check_device_ptr(const void* ptr, int dev, const char* what) {
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, ptr);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return dyson_internal_fail(DYSON_E_BAD_ARG, std::string("noalloc: cannot query ") + what);
+  }
+  if ((at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) || at.device != dev)
+    return dyson_internal_fail(DYSON_E_BAD_ARG, std::string("noalloc: ") + what +
+                                                    " is not device memory of the current device");
+  return DYSON_OK;
+}
+
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 }  // namespace
@@ -78,42 +149,12 @@ extern "C" int dyson_subdomain_diag_noalloc(const dyson_geometry* geom, int K, c
                                             void* stream) {
   if (!geom || !omega || !V || !sigma || !diagB || K < 1)
     return dyson_internal_fail(DYSON_E_BAD_ARG, "noalloc: NULL pointer or K < 1");
-  if (geom->precision != DYSON_FP64)
-    return dyson_internal_fail(DYSON_E_BAD_ARG, "noalloc: only the FP64 form is available");
-  int heights[DY_MAXP] = {0};
-  int m = 0, ndd = 0;
-  int rc = dyson_partition(geom, heights, &m, &ndd, nullptr);
-  if (rc) return rc;
   Geo g;
-  std::memset(&g, 0, sizeof(g));
-  g.dim = geom->dim;
-  g.Lx = geom->L[0];
-  g.Ly = geom->L[1];
-  g.Lz = geom->dim == 3 ? geom->L[2] : 1;
-  g.N = g.Lx * g.Ly * g.Lz;
-  g.p = geom->p;
-  g.T = geom->dim == 3 ? g.Ly : 1;
-  g.A = g.Lx * g.T;
-  g.Ls = geom->dim == 3 ? g.Lz : g.Ly;
-  int c = 0, hmax = 0;
-  for (int i = 0; i < g.p; ++i) {
-    g.h[i] = heights[i];
-    g.s0[i] = c;
-    c += g.h[i];
-    if (g.h[i] > hmax) hmax = g.h[i];
-    if (i < g.p - 1) g.ylayer[i] = c++;
-  }
-  g.W = (g.T * hmax + 3) & ~3;
-  if (g.W > DY_MAXW_SMEM)
-    return dyson_internal_fail(DYSON_E_UNSUPPORTED, "noalloc: slice width above 64");
-  g.Ndd = ndd;
-  g.ifc_off = g.p * g.Lx * g.W;
-  g.t = geom->t;
-  g.mu = geom->mu;
-  if (!(geom->eta >= 0.0)) return dyson_internal_fail(DYSON_E_BAD_ARG, "noalloc: eta must be >= 0");
-  g.eta = geom->eta;
-  g.real_axis = geom->eta > 0.0 ? 1 : 0;
-  g.nb = 1;
+  int rc = noalloc_geo(geom, &g);
+  if (rc) return rc;
+  if (K > 65535)   // frequencies run on gridDim.y of the factor launch
+    return dyson_internal_fail(DYSON_E_BAD_ARG, "noalloc: K must be at most 65535");
+  const int ndd = g.Ndd;
   const size_t b_map = align256((size_t)ndd * sizeof(int));
   const size_t b_diag = align256((size_t)K * ndd * sizeof(cxd));
   const size_t b_g = align256((size_t)K * g.p * g.Lx * g.W * g.W * sizeof(cxd));
@@ -127,6 +168,14 @@ extern "C" int dyson_subdomain_diag_noalloc(const dyson_geometry* geom, int K, c
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices)
     return dyson_internal_fail(DYSON_E_CUDA, "noalloc: no usable current device");
+  {
+    const void* ptrs[4] = {omega, V, sigma, diagB};
+    const char* names[4] = {"omega", "V", "sigma", "diagB"};
+    for (int k = 0; k < 4; ++k) {
+      int rc2 = check_device_ptr(ptrs[k], dev, names[k]);
+      if (rc2) return rc2;
+    }
+  }
   void* base = nullptr;
   e = scratch_address(dev, &base);
   if (e != cudaSuccess)

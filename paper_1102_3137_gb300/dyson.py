@@ -43,6 +43,7 @@ DYSON_MEM_DEVICE = 1
 DYSON_ST_TERMINATED = 1
 DYSON_ST_BREAKDOWN = 2
 DYSON_ST_NO_CONVERGENCE = 4
+DYSON_ST_WAIT_TIMEOUT = 16
 
 
 class dyson_geometry(C.Structure):
@@ -109,6 +110,7 @@ def load(path: str = LIB_PATH):
         "dyson_work_counters": ([P, I, P], I),
         "dyson_lanczos_basis": ([P, I, I, P], I),
         "dyson_subdomain_diag_noalloc": ([C.POINTER(dyson_geometry), I, P, P, P, P, P], I),
+        "dyson_wait_selftest": ([C.c_double, P, P], I),
         "dyson_server_create": ([C.c_size_t, I, C.POINTER(P)], I),
         "dyson_server_destroy": ([P], I),
         "dyson_submit": ([P, C.POINTER(dyson_request), C.POINTER(C.c_uint64)], I),
@@ -340,13 +342,31 @@ def dyson_work_counters(plan, K, p):
 
 
 def dyson_subdomain_diag_noalloc(geom, K, omega, V, sigma, diagB, stream=None):
-    """Allocation-free diag(blkdiag(B^-1, 0)): device arrays only, no plan (see dyson.h)."""
-    N = V.shape[0] if hasattr(V, "shape") else len(V)
-    if _kinds(omega, V, sigma, diagB) != DYSON_MEM_DEVICE:
+    """Allocation-free diag(blkdiag(B^-1, 0)): CUDA tensors only, no plan (see dyson.h).
+
+    Every tensor must live on one CUDA device; the call runs with that device
+    current, and with no stream given, on that device's current torch stream.
+    N is the site count of the geometry: V needs N elements, sigma and diagB K*N.
+    """
+    import torch
+    ts = (omega, V, sigma, diagB)
+    if not all(isinstance(x, torch.Tensor) and x.is_cuda for x in ts):
         raise TypeError("dyson_subdomain_diag_noalloc takes CUDA tensors only")
-    _check(load().dyson_subdomain_diag_noalloc(C.byref(geom), K, _ptr(omega, "f8", K), _ptr(V, "f8", N),
-                                               _ptr(sigma, "c16", K * N), _ptr(diagB, "c16", K * N),
-                                               _stream(stream)))
+    dev = diagB.device
+    if any(x.device != dev for x in ts):
+        raise TypeError("dyson_subdomain_diag_noalloc: every tensor must be on one CUDA device")
+    N = int(np.prod([geom.L[d] for d in range(geom.dim)]))
+    with torch.cuda.device(dev):
+        s = int(stream) if stream is not None else torch.cuda.current_stream(dev).cuda_stream
+        _check(load().dyson_subdomain_diag_noalloc(C.byref(geom), K, _ptr(omega, "f8", K), _ptr(V, "f8", N),
+                                                   _ptr(sigma, "c16", K * N), _ptr(diagB, "c16", K * N), s))
+
+
+def dyson_wait_selftest(limit_s):
+    """Run the copy rings' bounded wait on an mbarrier nothing arrives on; (timed_out, waited_s)."""
+    to, ws = C.c_int(), C.c_double()
+    _check(load().dyson_wait_selftest(float(limit_s), C.byref(to), C.byref(ws)))
+    return bool(to.value), ws.value
 
 
 def dyson_lanczos_basis(plan, k, nvec, N):
