@@ -65,6 +65,9 @@ extern "C" {
 #define DYSON_ST_TERMINATED 1     /* Lanczos reached an invariant subspace before k_max: exact */
 #define DYSON_ST_BREAKDOWN 2      /* (r, r)_C vanished for r != 0 (Sec. 2.1); partial sum kept */
 #define DYSON_ST_NO_CONVERGENCE 4 /* an interface solve hit krylov_maxit */
+#define DYSON_ST_WAIT_TIMEOUT 16  /* a bounded device wait (copy ring) gave up after 2 s: the
+                                     kernel went on without hanging, the frequency's result is
+                                     not valid */
 
 /* precision forms */
 #define DYSON_FP64 0   /* every step in complex128 */
@@ -347,14 +350,32 @@ int dyson_work_counters(dyson_plan plan, int K, unsigned long long* sweeps);
 int dyson_lanczos_basis(dyson_plan plan, int k, int nvec, double* Q);
 
 /*
+ * Failure-detection self-test (the paper has no counterpart).  Every wait of
+ * the solver's kernels on a copy ring is bounded by the global timer: on
+ * time-out the kernel records DYSON_ST_WAIT_TIMEOUT and returns instead of
+ * hanging.  This call runs that same bounded wait, on the current device, on
+ * an mbarrier that nothing ever arrives on, with a limit of limit_s seconds
+ * (1e-6 .. 10): *timed_out = 1 when the wait gave up and the kernel returned;
+ * *waited_s (may be NULL) receives the time it waited.  The device stays
+ * usable afterwards.  Synchronous; allocates 8 bytes of device memory.
+ */
+int dyson_wait_selftest(double limit_s, int* timed_out, double* waited_s);
+
+/*
  * Allocation-free variant of dyson_subdomain_diag.  The paper has no
- * counterpart: this exists for callers that cannot call cudaMalloc at all
- * (work inside a captured or replayed CUDA graph that must not allocate,
- * processes whose device memory is reserved up front, embedders that pass only
- * their own buffers).  No plan is needed and nothing is allocated: omega [K],
- * V [N], sigma complex[K][N] and the output diagB complex[K][N] are the
- * caller's DEVICE pointers on the current device; the work is enqueued on
- * `stream` in the FP64 form and the call returns without waiting.
+ * counterpart.  It is meant for host programs that cannot let the solver
+ * allocate device memory: a simulation that reserves all of its device memory
+ * in one pool at start-up and treats any later cudaMalloc as an error (the pool
+ * may leave nothing free, and an allocation can stall the device while other
+ * work runs), or a plugin inside another framework that owns every device
+ * buffer and only lends it inputs and outputs.  No plan is needed and nothing
+ * is allocated: omega [K], V [N], sigma complex[K][N] and the output diagB
+ * complex[K][N] are the caller's DEVICE pointers on the current device (each is
+ * checked to be device memory of that device, else DYSON_E_BAD_ARG); the work
+ * is enqueued on `stream` in the FP64 form and the call returns without
+ * waiting.  Slice widths up to 64 only (DYSON_E_UNSUPPORTED above); K at most
+ * 65535.  Of the geometry only dim, L, t, mu, p, precision (must be
+ * DYSON_FP64) and eta are read.
  *
  * All other storage lives in one fixed device array of
  * DYSON_NOALLOC_SCRATCH_BYTES that the library reserves statically: every GPU
@@ -364,8 +385,8 @@ int dyson_lanczos_basis(dyson_plan plan, int k, int nvec, double* Q);
  * fewer frequencies per call.  All calls share the array and it keeps the last
  * call's contents; calls whose work overlaps on the GPU (other streams or
  * threads) race on it, so callers must serialise them.  The first call on a
- * device looks up the array's device address (once per device), so make that
- * first call before any stream capture that should contain later calls.
+ * device looks up the array's device address (once per device, with that
+ * device current); make that first call before any stream capture.
  */
 #define DYSON_NOALLOC_SCRATCH_BYTES (32u << 20)
 int dyson_subdomain_diag_noalloc(const dyson_geometry* geom, int K, const double* omega,

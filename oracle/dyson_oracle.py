@@ -25,8 +25,12 @@ Readings of the paper taken here (the paper is silent or garbled there):
     bilinear form                                             (Sec. 2.3)
   * diag(Q T Q^T) = sum_j alpha_j q_j*q_j + 2 sum_{j>=2} beta_j q_{j-1}*q_j
     with T = tridiag(beta_j, alpha_j, beta_{j+1})             (Eq. 9 text)
-  * stop when |beta_{j+1}| <= 1e-12 max|T| (invariant subspace reached);
-    breakdown when |r^T r| <= 1e-14 ||r||_2^2                 (Sec. 2.1, 2.3)
+  * stop when ||r||_2 <= 1e-12 max|T| (the new residual vanished: invariant
+    subspace reached; the paper names the 2-norm test as an alternative
+    stopping rule); breakdown when r does not vanish but its bilinear "norm"
+    does, |r^T r| <= 1e-14 ||r||_2^2 (Sec. 2.1, 2.3).  The 2-norm test comes
+    first, so an exactly vanishing (r, r)_C with r != 0 is a breakdown and not
+    a termination.
   * the H solve of Eq. 6 is a direct block-LU solve of the full lattice
     (the paper does not say which solver it used).
   * recursive decomposition (Sec. 2.3 end; 2D): a box is cut in two by one
@@ -34,7 +38,7 @@ Readings of the paper taken here (the paper is silent or garbled there):
     level; boxes of at most min_sites sites are inverted directly.
   * block Lanczos (not in the paper; for degenerate spectra of X): blocks are
     split by a column-by-column bilinear Gram-Schmidt QR (applied twice);
-    a column whose pivot falls to 1e-12 max|T| is deflated to zero; the run
+    a column whose 2-norm falls to 1e-12 max|T| is deflated to zero; the run
     terminates when a whole new block deflates; k_max counts columns.
 """
 from __future__ import annotations
@@ -362,14 +366,15 @@ def cs_lanczos(matvec, q1, k_max: int, term_tol: float = 1e-12, brk_tol: float =
             acc += 2.0 * beta_prev * Q[:, j - 1] * qj
         alphas.append(a)
         rr = r @ r
+        rn2 = np.vdot(r, r).real                 # ||r||_2^2 (conjugated)
         b = branch * np.sqrt(rr)
         maxT = max(max(abs(x) for x in alphas), max((abs(x) for x in betas), default=0.0))
         if j == k_max - 1:
             break
-        if abs(b) <= term_tol * maxT:
+        if np.sqrt(rn2) <= term_tol * maxT:      # r itself vanished: invariant subspace
             status = STATUS_TERMINATED
             break
-        if abs(rr) <= brk_tol * np.vdot(r, r).real:
+        if abs(rr) <= brk_tol * rn2:             # r != 0 but (r, r)_C ~ 0: breakdown
             status = STATUS_BREAKDOWN
             break
         betas.append(b)
@@ -382,7 +387,7 @@ def cs_lanczos(matvec, q1, k_max: int, term_tol: float = 1e-12, brk_tol: float =
 def _bilinear_qr(R, maxT: float, term_tol: float, brk_tol: float):
     """R = Q B in the bilinear form, column by column (Gram-Schmidt twice).
 
-    Q^T Q = I on the kept columns; a column whose pivot |B_cc| falls to
+    Q^T Q = I on the kept columns; a column whose 2-norm falls to
     term_tol * maxT is deflated (q_c = 0, B_cc = 0) and takes no further
     part.  Returns (Q, B, deflated[b], breakdown) where breakdown means
     (r, r)_C vanished for a column that is not small.
@@ -398,11 +403,12 @@ def _bilinear_qr(R, maxT: float, term_tol: float, brk_tol: float):
             r = r - Q[:, :c] @ h
             B[:c, c] += h
         rr = r @ r
+        rn2 = np.vdot(r, r).real
         b = np.sqrt(rr)
-        if abs(b) <= term_tol * maxT:
+        if np.sqrt(rn2) <= term_tol * maxT:      # the column vanished: deflate it
             defl[c] = True
             continue
-        if abs(rr) <= brk_tol * np.vdot(r, r).real:
+        if abs(rr) <= brk_tol * rn2:             # r != 0 but (r, r)_C ~ 0: breakdown
             return Q, B, defl, True
         B[c, c] = b
         Q[:, c] = r / b

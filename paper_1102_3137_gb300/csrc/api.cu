@@ -814,6 +814,21 @@ int dyson_lanczos_basis(dyson_plan p, int k, int nvec, double* Q) {
   return DYSON_OK;
 }
 
+int dyson_wait_selftest(double limit_s, int* timed_out, double* waited_s) {
+  if (!(limit_s >= 1e-6 && limit_s <= 10.0)) return fail(DYSON_E_BAD_ARG, "limit_s must be in [1e-6, 10]");
+  if (!timed_out) return fail(DYSON_E_BAD_ARG, "timed_out is NULL");
+  int* d = nullptr;
+  CK(cudaMalloc(&d, 2 * sizeof(int)));
+  int h[2] = {-1, 0};
+  cudaError_t e = launch_wait_selftest((unsigned long long)(limit_s * 1e9), d, 0);
+  if (e == cudaSuccess) e = cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return fail(DYSON_E_CUDA, std::string("wait self-test: ") + cudaGetErrorString(e));
+  *timed_out = h[0] == DYSON_ST_WAIT_TIMEOUT ? 1 : 0;
+  if (waited_s) *waited_s = h[1] * 1e-6;
+  return DYSON_OK;
+}
+
 int dyson_work_counters(dyson_plan p, int K, unsigned long long* sweeps) {
   int rc;
   if ((rc = check_plan(p)) || (rc = check_K(p, K))) return rc;

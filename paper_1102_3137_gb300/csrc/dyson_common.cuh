@@ -288,3 +288,4 @@ cudaError_t launch_gather(const Geo& g, const Bufs& b, int K, const cxd* nat, cx
 cudaError_t launch_scatter(const Geo& g, const Bufs& b, int K, const cxd* dd, cxd* nat,
                            size_t dd_stride, cudaStream_t st);
 cudaError_t launch_status(const Geo& g, const Bufs& b, int K, int* status, cudaStream_t st);
+cudaError_t launch_wait_selftest(unsigned long long limit_ns, int* out, cudaStream_t st);

@@ -7,7 +7,7 @@
 //   R_j = X Q_j - Q_j A_j - Q_{j-1} B_j^T  (then CGS2 against all blocks) = Q_{j+1} B_{j+1}
 //
 // with R_j split column by column by Gram-Schmidt (twice) in the bilinear
-// form; a column whose pivot falls to TERM_TOL max|T| is deflated to zero.
+// form; a column whose 2-norm falls to TERM_TOL max|T| is deflated to zero.
 // The diagonal of Q T Q^T gains diag(Q_j A_j Q_j^T) + 2 diag(Q_j B_j Q_{j-1}^T)
 // per block step (Eq. 9 per block).  One cluster per frequency, one CTA per
 // subdomain, fixed-order cluster reductions as in the scalar step.
@@ -56,7 +56,7 @@ __device__ int qr_column(cg::cluster_group& cl, RedSmem& rs, int& phase, const G
   const cxd beta = csqrt_principal(v2[0]);
   int res = 0;
   cxd scale = {0, 0};
-  if (sqrt(cabs2(beta)) <= tol) {
+  if (sqrt(v2[1].x) <= tol) {          // the column vanished (2-norm): deflate
     res = 1;
   } else if (sqrt(cabs2(v2[0])) <= BRK_TOL * v2[1].x) {
     return 2;

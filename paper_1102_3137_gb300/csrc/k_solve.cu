@@ -89,10 +89,10 @@ __global__ void __launch_bounds__(DY_THREADS) k_lanczos(Geo g, Bufs b, int j) {
   int done = 0, flag = 0;
   if (j == g.k_max - 1) {
     done = 1;
-  } else if (babs <= TERM_TOL * maxT) {
+  } else if (sqrt(v2[1].x) <= TERM_TOL * maxT) {      // r vanished: invariant subspace
     done = 1;
     flag = 1;
-  } else if (sqrt(cabs2(rr)) <= BRK_TOL * v2[1].x) {
+  } else if (sqrt(cabs2(rr)) <= BRK_TOL * v2[1].x) {   // r != 0, (r, r)_C ~ 0: breakdown
     done = 1;
     flag = 2;
   }
@@ -189,7 +189,30 @@ __global__ void k_status(const int* st, int K, int* status) {
     status[k] = st[(size_t)k * ST_N + ST_STATUS];
 }
 
+// Failure-detection self-test of the bounded wait every copy ring uses: one
+// thread waits on a fresh mbarrier that nothing arrives on (phase 0 never
+// completes), so the wait must give up after limit_ns; out[0] receives
+// ST_WAIT_TIMEOUT if it did (0 if the phase completed), out[1] the time waited
+// in microseconds.  No copy is in flight, so returning early is safe.
+__global__ void k_wait_selftest(unsigned long long limit_ns, int* out) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+    const unsigned long long t0 = global_ns();
+    const bool ok = mbar_wait_for(&bar, 0u, limit_ns);
+    const unsigned long long dt = global_ns() - t0;
+    out[0] = ok ? 0 : ST_WAIT_TIMEOUT;
+    out[1] = (int)(dt / 1000ull > 0x7fffffffull ? 0x7fffffffull : dt / 1000ull);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_wait_selftest(unsigned long long limit_ns, int* out, cudaStream_t st) {
+  k_wait_selftest<<<1, 32, 0, st>>>(limit_ns, out);
+  return cudaGetLastError();
+}
 
 size_t dyson_internal_sweep_smem(const Geo& g, bool mixed) {
   return mixed ? sweep_smem<float>(g) : sweep_smem<double>(g);

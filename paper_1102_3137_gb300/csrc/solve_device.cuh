@@ -23,13 +23,14 @@
 #pragma once
 #include <cooperative_groups.h>
 
+#include "dyson.h"
 #include "dyson_common.cuh"
 
 namespace cg = cooperative_groups;
 
 namespace {
 
-constexpr double TERM_TOL = 1e-12;    // |beta_{j+1}| <= TERM_TOL * max|T|: invariant subspace
+constexpr double TERM_TOL = 1e-12;    // ||r||_2 <= TERM_TOL * max|T|: invariant subspace
 constexpr double BRK_TOL = 1e-14;     // |r^T r| <= BRK_TOL * ||r||^2: breakdown
 constexpr int KMAX_SMEM = 256;        // largest Lanczos rank cap
 // refinement stops early once a pass no longer shrinks the squared FP64
@@ -119,7 +120,7 @@ __device__ void block_sum(RedSmem& rs, cxd (&v)[NV]) {
 // wait is bounded by the global timer: on time-out the kernel records
 // DYSON_ST_WAIT_TIMEOUT and goes on (no CTA may leave its cluster's barriers).
 constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;   // 2 s
-constexpr int ST_WAIT_TIMEOUT = 16;
+constexpr int ST_WAIT_TIMEOUT = DYSON_ST_WAIT_TIMEOUT;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -153,12 +154,15 @@ __device__ __forceinline__ unsigned long long global_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait_for(uint64_t* bar, uint32_t parity, unsigned long long limit_ns) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = global_ns();
   while (!mbar_try_wait(bar, parity))
-    if (global_ns() - t0 > WAIT_LIMIT_NS) return false;
+    if (global_ns() - t0 > limit_ns) return false;
   return true;
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  return mbar_wait_for(bar, parity, WAIT_LIMIT_NS);
 }
 
 // Per-CTA copy pipeline: S slots of one W x W block each, one mbarrier per slot.

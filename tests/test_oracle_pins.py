@@ -609,3 +609,90 @@ def test_block_lanczos_partial_deflation_keeps_exactness():
                                      return_info=True)
     assert info2["status"] == O.STATUS_TERMINATED and info2["steps"] == 3
     assert np.max(np.abs(r2 - exact)) / np.max(np.abs(exact)) < 1e-12
+
+
+# ------------------------------------------------- signs of Eq. 1, breakdown branch
+
+
+def _degree(L):
+    """Neighbours of each site of an open box, from its coordinates (natural order)."""
+    idx = np.indices(tuple(reversed(L))).reshape(len(L), -1)[::-1]    # idx[d] = coordinate d
+    return sum((idx[d] > 0).astype(int) + (idx[d] < L[d] - 1).astype(int) for d in range(len(L)))
+
+
+@pytest.mark.parametrize("axis", ["matsubara", "real"])
+def test_dyson_diagonal_signs_from_high_frequency_expansion(axis):
+    """Eq. 1 fixes H = w I + C + t A with w = i w_k (or w + i eta on the real axis)
+    and C_ii = mu - V_i - Sigma_i.  For |w| >> |C + t A| the inverse expands as
+    G = 1/w - (C + tA)/w^2 + (C + tA)^2/w^3 - ..., so
+        G_ii = 1/w - c_i/w^2 + (c_i^2 + t^2 Z_i)/w^3 + O(|w|^-4),   Z_i neighbours of i.
+    At |w| = 1e3 the second term is ~1e-3 of G_ii and the remainder ~1e-7, so the
+    signs of mu, V_i and Sigma_i (each O(1) and distinct here) and the t^2 Z_i term
+    are held to 1e-6; every single sign flip misses by more than 1e-4."""
+    L = (6, 5)
+    rng = np.random.default_rng(21)
+    N = 30
+    V = rng.uniform(0.5, 1.5, N)
+    sigma = rng.uniform(-1.0, 1.0, N) - 1j * rng.uniform(0.2, 0.7, N)
+    mu, t, wv, eta = 0.7, -1.0, 1e3, 0.05
+    if axis == "matsubara":
+        z = O.dyson_diagonal(wv, mu, V, sigma)
+        W = 1j * wv
+    else:
+        z = O.dyson_diagonal_real(wv, eta, mu, V, sigma)
+        W = wv + 1j * eta
+    G = O.exact_diag(L, (False,) * 3, t, z)
+    Z = _degree(L)
+
+    def series(m, v, s):
+        c = m - v - s
+        return 1 / W - c / W ** 2 + (c * c + t * t * Z) / W ** 3
+
+    rel = lambda ser: float(np.max(np.abs(G - ser) / np.abs(G)))
+    assert rel(series(mu, V, sigma)) < 1e-6
+    for wrong in (series(-mu, V, sigma), series(mu, -V, sigma), series(mu, V, -sigma)):
+        assert rel(wrong) > 1e-4
+
+
+def test_lanczos_breakdown_on_vanishing_bilinear_norm():
+    """Sec. 2.1: in the bilinear form the "norm" sqrt(r^T r) of a non-zero vector can
+    vanish.  Built by hand: q1 = e1 and X e1 = a e1 + b e2 give alpha_1 = a and
+    q2 = e2; X e2 = b e1 + a2 e2 + e3 + i e4 then leaves r = e3 + i e4, with
+    r^T r = 1 + i^2 = 0 while ||r||_2^2 = 2.  That is a breakdown (the partial sum
+    of the two steps kept, Eq. 9), not an invariant subspace."""
+    a, b, a2 = 0.3 + 0.2j, 0.8 - 0.1j, -0.5 + 0.4j
+    X = np.array([[a, b, 0, 0],
+                  [b, a2, 1, 1j],
+                  [0, 1, 0.2, 0.7],
+                  [0, 1j, 0.7, -0.3j]], dtype=complex)
+    assert np.array_equal(X, X.T)
+    q1 = np.array([1.0, 0.0, 0.0, 0.0])
+    acc, al, be, Q, st = O.cs_lanczos(lambda q: X @ q, q1, 4)
+    assert st == O.STATUS_BREAKDOWN and len(al) == 2
+    assert abs(al[0] - a) < 1e-15 and abs(al[1] - a2) < 1e-15
+    assert abs(be[0] - b) < 1e-15 or abs(be[0] + b) < 1e-15     # either square-root branch
+    beta = be[0]
+    want = np.zeros(4, complex)
+    want += a * Q[:, 0] ** 2 + a2 * Q[:, 1] ** 2 + 2 * beta * Q[:, 0] * Q[:, 1]
+    assert np.max(np.abs(acc - want)) < 1e-15
+    assert np.max(np.abs(acc - np.array([a, a2, 0, 0]))) < 1e-15
+    # a bilinear norm that does not vanish: the recurrence goes on
+    Y = X.copy()
+    Y[1, 3] = Y[3, 1] = 0.9j                 # r^T r = 1 - 0.81
+    _, al2, _, _, st2 = O.cs_lanczos(lambda q: Y @ q, q1, 4)
+    assert st2 != O.STATUS_BREAKDOWN and len(al2) > 2
+    # r = 0 after the first step: an invariant subspace, not a breakdown
+    Z = np.diag([a, a2, 0.2, 0.1]).astype(complex)
+    _, al3, _, _, st3 = O.cs_lanczos(lambda q: Z @ q, q1, 4)
+    assert st3 == O.STATUS_TERMINATED and len(al3) == 1
+
+
+def test_block_qr_breakdown_and_deflation():
+    """The block form's column split (R15): a column with r != 0 and r^T r = 0 is a
+    breakdown; a column that vanishes in the 2-norm is deflated."""
+    R = np.array([[1.0, 1.0], [0.0, 1.0], [0.0, 1j]], dtype=complex)   # column 1 less its e1 part: (0, 1, i)
+    _, _, defl, brk = O._bilinear_qr(R, 1.0, 1e-12, 1e-14)
+    assert brk and not defl.any()
+    R2 = np.array([[1.0, 2.0], [0.5, 1.0], [0.0, 0.0]], dtype=complex)  # column 1 = 2 x column 0
+    Q2, B2, defl2, brk2 = O._bilinear_qr(R2, 1.0, 1e-12, 1e-14)
+    assert not brk2 and list(defl2) == [False, True] and np.all(Q2[:, 1] == 0)
