@@ -168,15 +168,17 @@ int dyson_plan_destroy(dyson_plan plan);
 /*
  * Autotuner result (batched kernels' tile choice).  At a plan's first
  * dyson_solve with p > 1, before its graph is captured, the library times one
- * X-matvec launch for each copy-ring configuration the geometry admits (ring
- * slots; rows per streamed chunk when W > 64) on the caller's inputs and keeps
- * the fastest.  Reports the configuration in use (*ring_slots, *chunk_rows),
- * how many were timed (*candidates, 0 before the first solve) and the launch
- * times of the shared-memory heuristic's choice and of the kept one (ms).
- * Any output pointer may be NULL.  The paper has no counterpart.
+ * X-matvec launch for each configuration the geometry admits -- copy-ring
+ * slots, rows per streamed chunk when W > 64, and for the mixed form's
+ * complex64 two-chain sweeps (W <= 64) the CTA size, 256 threads at two CTAs
+ * per SM or 128 threads at four -- on the caller's inputs and keeps the
+ * fastest.  Reports the configuration in use (*ring_slots, *chunk_rows,
+ * *threads), how many were timed (*candidates, 0 before the first solve) and
+ * the launch times of the heuristic's choice and of the kept one (ms).  Any
+ * output pointer may be NULL.  The paper has no counterpart.
  */
 int dyson_plan_tuning(dyson_plan plan, int* ring_slots, int* chunk_rows, int* candidates,
-                      float* ms_heuristic, float* ms_best);
+                      float* ms_heuristic, float* ms_best, int* threads);
 
 /*
  * diag(G(i w_k)) for K frequencies (Eq. 1 solved by the method of Sec. 2.3):

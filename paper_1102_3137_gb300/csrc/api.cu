@@ -386,6 +386,7 @@ int enqueue_range(dyson_plan p, const Bufs& b, int K, int* status, cudaStream_t 
       if (p->mixed) RUN(DYSON_KERNEL_XMATVEC, "xmatvec", launch_xmatvec<float>(g, b, K, j, 1, g.nb, s));
       else RUN(DYSON_KERNEL_XMATVEC, "xmatvec", launch_xmatvec<double>(g, b, K, j, 0, g.nb, s));
       if (g.nb > 1) RUN(DYSON_KERNEL_LANCZOS, "lanczos", launch_block_lanczos(g, b, K, j, s));
+      else if (p->mixed && g.k_max <= 64) RUN(DYSON_KERNEL_LANCZOS, "lanczos", launch_lanczos_dd(g, b, K, j, s));
       else RUN(DYSON_KERNEL_LANCZOS, "lanczos", launch_lanczos(g, b, K, j, s));
     }
   }
@@ -433,8 +434,8 @@ int enqueue_solve(dyson_plan p, int K, cudaStream_t s, bool cap) {
 int autotune(dyson_plan p, int K, cudaStream_t s) {
   p->tuned = true;
   if (p->g.p < 2) return DYSON_OK;
-  int S[16], CR[16];
-  const int n = dyson_internal_ring_candidates(p->g, p->mixed, S, CR, 16);
+  int S[32], CR[32], NT[32];
+  const int n = dyson_internal_ring_candidates(p->g, p->mixed, S, CR, NT, 32);
   p->tune_candidates = n;
   if (n < 2) return DYSON_OK;
   Geo& g = p->g;
@@ -453,6 +454,7 @@ int autotune(dyson_plan p, int K, cudaStream_t s) {
   for (int c = 0; c < n && rc == DYSON_OK; ++c) {
     g.ring_S = S[c];
     g.ring_CR = CR[c];
+    g.xm_nt = NT[c];
     cudaError_t e = p->mixed ? launch_xmatvec<float>(g, p->b, K, 0, 1, g.nb, s)
                              : launch_xmatvec<double>(g, p->b, K, 0, 0, g.nb, s);
     if (e == cudaSuccess) e = cudaEventRecord(e0, s);
@@ -477,6 +479,7 @@ int autotune(dyson_plan p, int K, cudaStream_t s) {
   cudaEventDestroy(e1);
   g.ring_S = S[best];
   g.ring_CR = CR[best];
+  g.xm_nt = NT[best];
   p->tune_ms_best = best_ms;
   return rc;
 }
@@ -603,6 +606,15 @@ int dyson_plan_create(const dyson_geometry* geom, dyson_plan* out) {
   p->tune_candidates = 0;
   p->tune_ms_heuristic = p->tune_ms_best = 0.f;
   p->n_prof = 0;
+  // X-matvec CTA size (complex64 two-chain form): 128 threads, four CTAs per SM,
+  // when the solve's clusters would not all fit at two CTAs per SM; the
+  // autotuner may revise it at the first solve
+  if (p->mixed && p->g.W <= DY_MAXW_SMEM && p->g.p > 1) {
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
+    const long long ctas = (long long)p->g.p * p->Kcap * p->g.nb;
+    p->g.xm_nt = (sms > 0 && ctas > 2LL * sms) ? 128 : 256;
+  }
   // frequency groups: not with the shared wide-slice factor workspace
   p->ngroups = 1;
   if (p->g.p > 1 && !b.fwork) {
@@ -683,11 +695,12 @@ int dyson_solve(dyson_plan p, int K, const double* omega, const double* V, const
 }
 
 int dyson_plan_tuning(dyson_plan p, int* ring_slots, int* chunk_rows, int* candidates,
-                      float* ms_heuristic, float* ms_best) {
+                      float* ms_heuristic, float* ms_best, int* threads) {
   int rc;
   if ((rc = check_plan(p))) return rc;
-  int S = 0, CR = 0;
-  dyson_internal_ring_plan(p->g, p->mixed, &S, &CR);
+  int S = 0, CR = 0, NT = 0;
+  dyson_internal_ring_plan(p->g, p->mixed, &S, &CR, &NT);
+  if (threads) *threads = NT;
   if (ring_slots) *ring_slots = S;
   if (chunk_rows) *chunk_rows = CR;
   if (candidates) *candidates = p->tuned ? p->tune_candidates : 0;

@@ -133,6 +133,30 @@ __device__ __forceinline__ double f2d_bits(float f) {
   if (ef == 0xffu) hi = sign | 0x7ff00000u | (m >> 3), lo = m << 29;
   return __longlong_as_double((long long)(((unsigned long long)hi << 32) | lo));
 }
+// binary64 -> double-float by integer operations (no binary64 instruction):
+// hi takes the leading 24 significant bits (truncated: the exponent rebiased in
+// place, then sign, exponent and the top 23 mantissa bits funnel-shifted into
+// binary32 position), lo the remaining 29 bits rounded to 23 at the fixed
+// exponent of hi's last place (lo = F - B with F, B binary32 numbers of one
+// exponent, an exact subtraction); hi + lo holds 47 significant bits, relative
+// error at most 2^-47.  Magnitudes below 2^-103 keep only hi (absolute error
+// below 2^-126), below 2^-126 give a signed zero; infinities, NaN and
+// magnitudes of 2^128 and above are not handled (every input here is a finite
+// Lanczos or X-matvec vector entry).
+__device__ __forceinline__ dfl d2dfl_bits(double d) {
+  const unsigned hw = (unsigned)__double2hiint(d), lw = (unsigned)__double2loint(d);
+  const unsigned sign = hw & 0x80000000u;
+  const unsigned e11 = (hw >> 20) & 0x7ffu;                       // binary64 biased exponent
+  const unsigned hb = (__funnelshift_l(lw, hw - 0x38000000u, 3) & 0x7fffffffu) | sign;
+  const unsigned ebits = hb & 0x7f800000u;                        // exponent field of hi
+  const unsigned el = ebits - (23u << 23);                        // exponent of hi's last place
+  const unsigned m_lo = ((lw & 0x1fffffffu) + 32u) >> 6;          // may reach 2^23: carries into el
+  const float lo = __fsub_rn(__uint_as_float((el + m_lo) | sign), __uint_as_float(el | sign));
+  return dfl(e11 >= 897u ? __uint_as_float(hb) : 0.f, e11 >= 920u ? lo : 0.f);
+}
+// double-float -> binary64: both parts widened exactly, one binary64 add
+__device__ __forceinline__ double dfl2d_bits(dfl v) { return f2d_bits(v.hi) + f2d_bits(v.lo); }
+
 __device__ __forceinline__ cxf c2f_bits(cxd a) { return {d2f_bits(a.x), d2f_bits(a.y)}; }
 __device__ __forceinline__ cxd c2d_bits(cxf a) { return {f2d_bits(a.x), f2d_bits(a.y)}; }
 
@@ -164,6 +188,8 @@ struct Geo {
   int ring_CR;         // rows per streamed chunk chosen by the autotuner (W > 64; 0: heuristic)
   int nb;              // Lanczos block size (1: the scalar recurrence of Sec. 2.1)
   int lpre;            // interface preconditioner: 1 exact layer blocks of S (2D strips), 0 banded
+  int xm_nt;           // threads per X-matvec CTA in the complex64 two-chain form (128: four CTAs
+                       // per SM; 0 or 256: two), chosen by the heuristic or the autotuner
 };
 
 // Work slots: the X-matvec runs one cluster per (frequency f, block column c),
@@ -244,9 +270,9 @@ size_t dyson_internal_plan_bytes(dyson_plan_s* p);
 size_t dyson_internal_sweep_smem(const Geo& g, bool mixed);
 // Copy-ring configurations the autotuner times for this geometry and form:
 // up to max pairs (slots, chunk rows), the shared-memory heuristic's first.
-int dyson_internal_ring_candidates(const Geo& g, bool mixed, int* S, int* CR, int max);
+int dyson_internal_ring_candidates(const Geo& g, bool mixed, int* S, int* CR, int* NT, int max);
 // The copy-ring configuration the kernels use for this geometry (slots, chunk rows).
-void dyson_internal_ring_plan(const Geo& g, bool mixed, int* S, int* CR);
+void dyson_internal_ring_plan(const Geo& g, bool mixed, int* S, int* CR, int* NT);
 
 // ---------------------------------------------------------------- host launchers
 template <typename R, typename S>
@@ -289,3 +315,4 @@ cudaError_t launch_scatter(const Geo& g, const Bufs& b, int K, const cxd* dd, cx
                            size_t dd_stride, cudaStream_t st);
 cudaError_t launch_status(const Geo& g, const Bufs& b, int K, int* status, cudaStream_t st);
 cudaError_t launch_wait_selftest(unsigned long long limit_ns, int* out, cudaStream_t st);
+cudaError_t launch_lanczos_dd(const Geo& g, const Bufs& b, int K, int j, cudaStream_t st);

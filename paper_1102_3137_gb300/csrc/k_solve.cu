@@ -218,14 +218,15 @@ size_t dyson_internal_sweep_smem(const Geo& g, bool mixed) {
   return mixed ? sweep_smem<float>(g) : sweep_smem<double>(g);
 }
 
-void dyson_internal_ring_plan(const Geo& g, bool mixed, int* S, int* CR) {
+void dyson_internal_ring_plan(const Geo& g, bool mixed, int* S, int* CR, int* NT) {
   const RingPlan rp = mixed ? ring_plan<float>(g) : ring_plan<double>(g);
   *S = rp.S;
   *CR = rp.CR;
+  *NT = mixed ? xm_threads<float>(g) : xm_threads<double>(g);
 }
 
-int dyson_internal_ring_candidates(const Geo& g, bool mixed, int* S, int* CR, int max) {
-  return mixed ? ring_candidates<float>(g, S, CR, max) : ring_candidates<double>(g, S, CR, max);
+int dyson_internal_ring_candidates(const Geo& g, bool mixed, int* S, int* CR, int* NT, int max) {
+  return mixed ? ring_candidates<float>(g, S, CR, NT, max) : ring_candidates<double>(g, S, CR, NT, max);
 }
 
 

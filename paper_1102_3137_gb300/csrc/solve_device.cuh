@@ -73,7 +73,7 @@ __device__ void cluster_sum(cg::cluster_group& cl, RedSmem& rs, int& phase, int 
   __syncthreads();
   if (threadIdx.x < NV) {
     cxd s = {0, 0};
-    for (int w = 0; w < DY_WARPS; ++w) s = s + rs.wred[w * 8 + threadIdx.x];
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s = s + rs.wred[w * 8 + threadIdx.x];
     rs.slot[phase * 8 + threadIdx.x] = s;
   }
   cl.sync();
@@ -105,7 +105,7 @@ __device__ void block_sum(RedSmem& rs, cxd (&v)[NV]) {
   __syncthreads();
   if (threadIdx.x < NV) {
     cxd s = {0, 0};
-    for (int w = 0; w < DY_WARPS; ++w) s = s + rs.wred[w * 8 + threadIdx.x];
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s = s + rs.wred[w * 8 + threadIdx.x];
     rs.res[threadIdx.x] = s;
   }
   __syncthreads();
@@ -253,7 +253,7 @@ __device__ __forceinline__ void sweep_prepass(const Geo& g, int i, const SweepAr
   const double as = fabs(a.in_scale);
   const bool fast = sizeof(R) == 4 && as > 1e-30 && as < 1e30;
   const R scf = (R)a.in_scale;
-  for (int e = threadIdx.x; e < nrow; e += DY_THREADS) {
+  for (int e = threadIdx.x; e < nrow; e += (int)blockDim.x) {
     const int s = e / W, j = e - s * W;
     cxd v = {0, 0};
     if (j < w) {
@@ -286,7 +286,7 @@ __device__ __forceinline__ void sweep_postpass(const Geo& g, int i, const SweepA
   const double os = fabs(a.out_scale);
   const bool fast = sizeof(R) == 4 && os > 1e-30 && os < 1e30;
   const R scf = (R)a.out_scale;
-  for (int e = threadIdx.x; e < nrow; e += DY_THREADS) {
+  for (int e = threadIdx.x; e < nrow; e += (int)blockDim.x) {
     const int s = e / W, j = e - s * W;
     if (j >= w) continue;
     const cx<R> xr = yb[e];
@@ -782,7 +782,7 @@ __device__ void sweep_chunked(const Geo& g, int i, const SweepArgs<R>& a, cx<R>*
     fence_proxy_async();
     for (int q = 0; q < S && q < NQ; ++q) issue(q);
   }
-  for (int e = tid; e < nrow; e += DY_THREADS) {
+  for (int e = tid; e < nrow; e += (int)blockDim.x) {
     const int s = e / W, j = e - s * W;
     cxd v = {0, 0};
     if (j < w) {
@@ -799,7 +799,7 @@ __device__ void sweep_chunked(const Geo& g, int i, const SweepArgs<R>& a, cx<R>*
     yb[e] = cconv<R>(v);
   }
   __syncthreads();
-  for (int e = tid; e < W; e += DY_THREADS) zbuf[e] = yb[e];
+  for (int e = tid; e < W; e += (int)blockDim.x) zbuf[e] = yb[e];
   __syncthreads();
   for (int n = 0; n < NL; ++n) {
     const int s = slice_of(n);
@@ -845,7 +845,7 @@ __device__ void sweep_chunked(const Geo& g, int i, const SweepArgs<R>& a, cx<R>*
       }
     }
   }
-  for (int e = tid; e < nrow; e += DY_THREADS) {
+  for (int e = tid; e < nrow; e += (int)blockDim.x) {
     const int s = e / W, j = e - s * W;
     if (j >= w) continue;
     const cx<R> xr = yb[e];
@@ -958,7 +958,7 @@ __device__ __noinline__ void precond_apply(const Geo& g, const Bufs& b, int vs, 
       reinterpret_cast<const C*>(b.pre) + ((size_t)slot_freq(g, vs) * nifc(g) + (size_t)i * A) * 3;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const C zero = {0, 0};
-  for (int tr = wid; tr < g.T; tr += DY_WARPS) {
+  for (int tr = wid; tr < g.T; tr += (int)(blockDim.x >> 5)) {
     const int o = Lx * tr;
     const C* invd = pre + o;
     const C* l1 = pre + A + o;
@@ -1079,7 +1079,7 @@ __device__ void cluster_sum_r(cg::cluster_group& cl, RedSmem& rs, int& phase, in
   __syncthreads();
   if (threadIdx.x < NV) {
     cxd s = {0, 0};
-    for (int w = 0; w < DY_WARPS; ++w) s = s + rs.wred[w * 8 + threadIdx.x];
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s = s + rs.wred[w * 8 + threadIdx.x];
     rs.slot[phase * 8 + threadIdx.x] = s;
   }
   cl.sync();
@@ -1111,7 +1111,7 @@ __device__ __noinline__ void lpre_apply(const Geo& g, const Bufs& b, int vs, int
   const int Lx = g.Lx;
   const C* rsh = r;                 // every thread reads all of r: served by L1
   const C* M = reinterpret_cast<const C*>(b.lpm) + ((size_t)slot_freq(g, vs) * (g.p - 1) + i) * (size_t)Lx * Lx;
-  for (int a = threadIdx.x; a < Lx; a += DY_THREADS) {
+  for (int a = threadIdx.x; a < Lx; a += (int)blockDim.x) {
     C acc0 = {0, 0}, acc1 = {0, 0};
     int c = 0;
     for (; c + 1 < Lx; c += 2) {
@@ -1152,7 +1152,7 @@ __device__ int schur_cocg(cg::cluster_group& cl, RedSmem& rs, int& phase, const 
   const R tr = (R)g.t;
 
   if (has) {
-    for (int a = threadIdx.x; a < A; a += DY_THREADS) {
+    for (int a = threadIdx.x; a < A; a += (int)blockDim.x) {
       X[o + a] = C{0, 0};
       Rv[o + a] = Bv[o + a];
     }
@@ -1162,7 +1162,7 @@ __device__ int schur_cocg(cg::cluster_group& cl, RedSmem& rs, int& phase, const 
   __syncthreads();
   C v2[2] = {{0, 0}, {0, 0}};
   if (has) {
-    for (int a = threadIdx.x; a < A; a += DY_THREADS) {
+    for (int a = threadIdx.x; a < A; a += (int)blockDim.x) {
       C zz = Z[o + a], r = Rv[o + a];
       P[o + a] = zz;
       v2[0] = cfma(r, zz, v2[0]);
@@ -1192,7 +1192,7 @@ __device__ int schur_cocg(cg::cluster_group& cl, RedSmem& rs, int& phase, const 
     cl.sync();                                  // boundary values of every subdomain written
     C v1[1] = {{0, 0}};
     if (has) {
-      for (int a = threadIdx.x; a < A; a += DY_THREADS) {
+      for (int a = threadIdx.x; a < A; a += (int)blockDim.x) {
         C sp = layer_C_apply<R>(g, dC, P + o, a) - tr * (bl_i[a] + bl_n[a]);
         SP[o + a] = sp;
         v1[0] = cfma(P[o + a], sp, v1[0]);
@@ -1201,7 +1201,7 @@ __device__ int schur_cocg(cg::cluster_group& cl, RedSmem& rs, int& phase, const 
     cluster_sum_r<R, 1>(cl, rs, phase, p, v1);
     const C alpha = cdiv(rho, v1[0]);
     if (has) {
-      for (int a = threadIdx.x; a < A; a += DY_THREADS) {
+      for (int a = threadIdx.x; a < A; a += (int)blockDim.x) {
         X[o + a] = X[o + a] + alpha * P[o + a];
         Rv[o + a] = Rv[o + a] - alpha * SP[o + a];
       }
@@ -1211,7 +1211,7 @@ __device__ int schur_cocg(cg::cluster_group& cl, RedSmem& rs, int& phase, const 
     __syncthreads();
     v2[0] = v2[1] = C{0, 0};
     if (has) {
-      for (int a = threadIdx.x; a < A; a += DY_THREADS) {
+      for (int a = threadIdx.x; a < A; a += (int)blockDim.x) {
         C zz = Z[o + a], r = Rv[o + a];
         v2[0] = cfma(r, zz, v2[0]);
         v2[1].x += cabs2(r);
@@ -1222,7 +1222,7 @@ __device__ int schur_cocg(cg::cluster_group& cl, RedSmem& rs, int& phase, const 
     const C beta = cdiv(v2[0], rho);
     rho = v2[0];
     if (has) {
-      for (int a = threadIdx.x; a < A; a += DY_THREADS) P[o + a] = Z[o + a] + beta * P[o + a];
+      for (int a = threadIdx.x; a < A; a += (int)blockDim.x) P[o + a] = Z[o + a] + beta * P[o + a];
     }
   }
   return it;
@@ -1235,7 +1235,7 @@ __device__ void layer_diag(const Geo& g, const Bufs& b, int vs, int i) {
   if (i >= g.p - 1) return;
   cx<R>* dC = ifv_ptr<R>(g, b, vs, IF_D) + (size_t)i * g.A;
   const int f = slot_freq(g, vs);
-  for (int a = threadIdx.x; a < g.A; a += DY_THREADS)
+  for (int a = threadIdx.x; a < g.A; a += (int)blockDim.x)
     dC[a] = cconv<R>(dyson_diag(g, b, f, a + g.A * g.ylayer[i]));
 }
 
@@ -1249,7 +1249,7 @@ __device__ void residual_H(const Geo& g, const Bufs& b, int vs, int i, const cxd
   const double t = g.t;
   const int f = slot_freq(g, vs);
   double sr = 0, sq = 0;
-  for (int e = threadIdx.x; e < (int)nsub; e += DY_THREADS) {
+  for (int e = threadIdx.x; e < (int)nsub; e += (int)blockDim.x) {
     const int s = e / W, j = e - s * W;
     if (j >= w) continue;
     const int tr = j % T, sl = j / T;
@@ -1278,7 +1278,7 @@ __device__ void residual_H(const Geo& g, const Bufs& b, int vs, int i, const cxd
     const cxd* xb = x + i * nsub;           // subdomain i: its top row touches layer i
     const cxd* xa = x + (i + 1) * nsub;     // subdomain i+1: its bottom row touches layer i
     const int hi = T * (g.h[i] - 1);
-    for (int a = threadIdx.x; a < A; a += DY_THREADS) {
+    for (int a = threadIdx.x; a < A; a += (int)blockDim.x) {
       const int xx = a % Lx, tr = a / Lx;
       cxd nb = {0, 0};
       if (xx > 0) nb = nb + xl[a - 1];
@@ -1330,11 +1330,11 @@ __device__ int solve_H(cg::cluster_group& cl, RedSmem& rs, int& phase, const Geo
     if (has) {
       const cx<R>* bl_i = bnd_ptr<R>(g, b, vs, i, 1);
       const cx<R>* bl_n = bnd_ptr<R>(g, b, vs, i + 1, 0);
-      for (int a = threadIdx.x; a < A; a += DY_THREADS)
+      for (int a = threadIdx.x; a < A; a += (int)blockDim.x)
         Bv[(size_t)i * A + a] = cconv<R>(isc * rc[a]) - tr * (bl_i[a] + bl_n[a]);
     }
   } else if (has) {
-    for (int a = threadIdx.x; a < A; a += DY_THREADS) Bv[(size_t)i * A + a] = cconv<R>(isc * rc[a]);
+    for (int a = threadIdx.x; a < A; a += (int)blockDim.x) Bv[(size_t)i * A + a] = cconv<R>(isc * rc[a]);
   }
   __syncthreads();
   int it = schur_cocg<R, WF>(cl, rs, phase, g, b, vs, i, tol, sm, pp, conv);
@@ -1349,7 +1349,7 @@ __device__ int solve_H(cg::cluster_group& cl, RedSmem& rs, int& phase, const Geo
   sweep<R, WF>(g, i, sb, sm, pp, sweep_cnt(g, b, vs, i));
   if (has) {
     cxd* xc = xout + g.ifc_off + (size_t)i * A;
-    for (int a = threadIdx.x; a < A; a += DY_THREADS) xc[a] = sc * cconv<double>(X[(size_t)i * A + a]);
+    for (int a = threadIdx.x; a < A; a += (int)blockDim.x) xc[a] = sc * cconv<double>(X[(size_t)i * A + a]);
   }
   return it;
 }
@@ -1360,22 +1360,28 @@ constexpr size_t YBUF_MAX = 64 * 1024;   // forward intermediates kept on chip u
 // a whole slice block fits a slot, the W <= 64 strips; row chunks otherwise),
 // zw entries of z vectors (2 W; 6 W for the two-chain complex64 form, whose
 // ring is split evenly between its chains), and the on-chip row buffer when
-// it fits.
+// it fits.  per_sm is the number of CTAs per SM the budget is shared by: 2
+// (256 threads, ~100 KB each) or, for the complex64 two-chain form, 4 (128
+// threads, ~52 KB each, the row buffer on chip only up to 16 KB).
 struct RingPlan {
   int CR, S, zw;
   size_t ybuf, smem;
 };
+constexpr size_t CTA4_BUDGET = 52 * 1024;   // dynamic shared memory per CTA at four CTAs per SM
+constexpr size_t CTA4_YBUF_MAX = 16 * 1024;
 template <typename R>
-__host__ __device__ inline RingPlan ring_plan(int W, int Lx) {
+__host__ __device__ inline RingPlan ring_plan(int W, int Lx, int per_sm = 2) {
   RingPlan rp;
   const size_t cs = sizeof(cx<R>);
   const size_t yb = (size_t)Lx * W * cs;
   if (W <= DY_MAXW_SMEM) {
     const bool pair = sizeof(R) == 4;
+    const bool four = pair && per_sm == 4;
     rp.zw = pair ? 6 * W : 2 * W;
-    rp.ybuf = yb <= YBUF_MAX ? yb : 0;
+    rp.ybuf = yb <= (four ? CTA4_YBUF_MAX : YBUF_MAX) ? yb : 0;
     rp.CR = W;
-    long S = ((long)100 * 1024 - (long)rp.ybuf - (long)(rp.zw * cs)) / (long)(W * W * cs);   // two CTAs per SM
+    const long budget = four ? (long)CTA4_BUDGET : (long)100 * 1024;
+    long S = (budget - (long)rp.ybuf - (long)(rp.zw * cs)) / (long)(W * W * cs);
     if (S > MAX_STAGES) S = MAX_STAGES;
     if (S < 2) S = 2;
     if (pair) S &= ~1L;
@@ -1403,12 +1409,18 @@ __host__ __device__ inline RingPlan ring_plan(int W, int Lx) {
   rp.smem = rp.CR ? (size_t)rp.S * rp.CR * W * cs + (size_t)rp.zw * cs + rp.ybuf : 0;
   return rp;
 }
+// threads per CTA of the X-matvec of a geometry in precision R: 128 (four CTAs
+// per SM) for the complex64 two-chain form when the plan chose it, else 256
+template <typename R>
+__host__ __device__ inline int xm_threads(const Geo& g) {
+  return (sizeof(R) == 4 && g.W <= DY_MAXW_SMEM && g.xm_nt == 128) ? 128 : 256;
+}
 // The plan of a geometry: the heuristic above, or the autotuner's choice of
 // slots (and chunk rows for W > 64) with the same row buffer and z area.
 constexpr size_t SMEM_LIMIT = 225 * 1024;   // dynamic shared memory per CTA, below the 227 KB cap
 template <typename R>
 __host__ __device__ inline RingPlan ring_plan(const Geo& g) {
-  RingPlan rp = ring_plan<R>(g.W, g.Lx);
+  RingPlan rp = ring_plan<R>(g.W, g.Lx, xm_threads<R>(g) == 128 ? 4 : 2);
   if (g.ring_S > 0 && rp.CR > 0) {
     rp.S = g.ring_S;
     if (g.W > DY_MAXW_SMEM && g.ring_CR > 0) rp.CR = g.ring_CR;
@@ -1418,39 +1430,50 @@ __host__ __device__ inline RingPlan ring_plan(const Geo& g) {
 }
 // Configurations the autotuner times: the heuristic's first, then every slot
 // count 2..MAX_STAGES (even in the two-chain complex64 form) that fits, and
-// for W > 64 the chunk heights (divisors of W) with the most slots that fit.
+// for W > 64 the chunk heights (divisors of W) with the most slots that fit;
+// the complex64 two-chain form adds the same slot counts at 128 threads per
+// CTA (four CTAs per SM).  NT[] receives each configuration's threads per CTA.
 template <typename R>
-inline int ring_candidates(const Geo& g, int* S, int* CR, int max) {
-  const RingPlan h = ring_plan<R>(g.W, g.Lx);
+inline int ring_candidates(const Geo& g, int* S, int* CR, int* NT, int max) {
+  const int nt0 = xm_threads<R>(g);
+  const RingPlan h = ring_plan<R>(g.W, g.Lx, nt0 == 128 ? 4 : 2);
   if (h.CR == 0 || max < 1) return 0;
   int n = 0;
   S[n] = h.S;
   CR[n] = h.CR;
+  NT[n] = nt0;
   ++n;
-  const size_t cs = sizeof(cx<R>), fixed = (size_t)h.zw * cs + h.ybuf;
-  auto fits = [&](int s, int cr) { return (size_t)s * cr * g.W * cs + fixed <= SMEM_LIMIT; };
-  auto add = [&](int s, int cr) {
+  const size_t cs = sizeof(cx<R>);
+  auto fits = [&](int s, int cr, int nt) {
+    const RingPlan b = ring_plan<R>(g.W, g.Lx, nt == 128 ? 4 : 2);
+    const size_t fixed = (size_t)b.zw * cs + b.ybuf;
+    return (size_t)s * cr * g.W * cs + fixed <= (nt == 128 ? CTA4_BUDGET : SMEM_LIMIT);
+  };
+  auto add = [&](int s, int cr, int nt) {
     for (int k = 0; k < n; ++k)
-      if (S[k] == s && CR[k] == cr) return;
-    if (n < max && fits(s, cr)) {
+      if (S[k] == s && CR[k] == cr && NT[k] == nt) return;
+    if (n < max && fits(s, cr, nt)) {
       S[n] = s;
       CR[n] = cr;
+      NT[n] = nt;
       ++n;
     }
   };
   if (g.W <= DY_MAXW_SMEM) {
     const int step = sizeof(R) == 4 ? 2 : 1;        // two chains split the ring evenly
-    for (int s = 2; s <= MAX_STAGES; s += step) add(s, g.W);
+    for (int s = 2; s <= MAX_STAGES; s += step) add(s, g.W, 256);
+    if (sizeof(R) == 4)
+      for (int s = 2; s <= MAX_STAGES; s += step) add(s, g.W, 128);
   } else {
     for (int cr = g.W; cr >= 1; --cr) {
       if (g.W % cr) continue;
       int best = 0;
       for (int s = MAX_STAGES; s >= 2; --s)
-        if (fits(s, cr)) {
+        if (fits(s, cr, 256)) {
           best = s;
           break;
         }
-      if (best >= 3) add(best, cr);
+      if (best >= 3) add(best, cr, 256);
       if (n >= max) break;
     }
   }
@@ -1465,8 +1488,8 @@ inline int ring_candidates(const Geo& g, int* S, int* CR, int max) {
 //   mixed = 1: sweeps in complex64 (R = float).  w_B is refined against FP64
 //              residuals of B, u against FP64 residuals of H, each until the
 //              relative residual is below refine_tol.
-template <typename R, int WF>
-__global__ void __launch_bounds__(DY_THREADS, 2) k_xmatvec(Geo g, Bufs b, int j, int mixed, int ncols) {
+template <typename R, int WF, int NT>
+__global__ void __launch_bounds__(NT, NT == 128 ? 4 : 2) k_xmatvec(Geo g, Bufs b, int j, int mixed, int ncols) {
   cg::cluster_group cl = cg::this_cluster();
   __shared__ RedSmem rs;
   __shared__ __align__(8) uint64_t bars[MAX_STAGES];
@@ -1511,7 +1534,7 @@ __global__ void __launch_bounds__(DY_THREADS, 2) k_xmatvec(Geo g, Bufs b, int j,
       const cx<R>* bl_i = bnd_ptr<R>(g, b, vs, i, 1);
       const cx<R>* bl_n = bnd_ptr<R>(g, b, vs, i + 1, 0);
       const cxd* qc = q + g.ifc_off + (size_t)i * A;
-      for (int a = threadIdx.x; a < A; a += DY_THREADS)
+      for (int a = threadIdx.x; a < A; a += (int)blockDim.x)
         Bv[(size_t)i * A + a] = (R)g.t * (bl_i[a] + bl_n[a]) - cconv<R>(qc[a]);
     }
     __syncthreads();
@@ -1528,7 +1551,7 @@ __global__ void __launch_bounds__(DY_THREADS, 2) k_xmatvec(Geo g, Bufs b, int j,
     sweep<R, WF>(g, i, sb, sm, pp, sweep_cnt(g, b, vs, i));
     if (has) {
       cxd* uc = u + g.ifc_off + (size_t)i * A;
-      for (int a = threadIdx.x; a < A; a += DY_THREADS) uc[a] = -cconv<double>(X[(size_t)i * A + a]);
+      for (int a = threadIdx.x; a < A; a += (int)blockDim.x) uc[a] = -cconv<double>(X[(size_t)i * A + a]);
     }
   } else {
     cxd* wv = b.v1 + (size_t)vs * Ndd;   // w_B, later the refinement corrections
@@ -1562,7 +1585,7 @@ __global__ void __launch_bounds__(DY_THREADS, 2) k_xmatvec(Geo g, Bufs b, int j,
     {
       const int n = own_count(g, i);
       const int hi = g.T * (g.h[i] - 1);
-      for (int e = threadIdx.x; e < n; e += DY_THREADS) {
+      for (int e = threadIdx.x; e < n; e += (int)blockDim.x) {
         size_t k = own_idx(g, i, e, (int)nsub);
         cxd v = {0, 0};
         if (e >= (int)nsub) {
@@ -1579,7 +1602,7 @@ __global__ void __launch_bounds__(DY_THREADS, 2) k_xmatvec(Geo g, Bufs b, int j,
     {
       cxd v1[1] = {{0, 0}};
       if (has)
-        for (int a = threadIdx.x; a < A; a += DY_THREADS)
+        for (int a = threadIdx.x; a < A; a += (int)blockDim.x)
           v1[0].x += cabs2(hr[g.ifc_off + (size_t)i * A + a]);
       cluster_sum<1>(cl, rs, phase, p, v1);   // also: every CTA has read w_B before it is reused
       hn = sqrt(v1[0].x);
@@ -1590,7 +1613,7 @@ __global__ void __launch_bounds__(DY_THREADS, 2) k_xmatvec(Geo g, Bufs b, int j,
       ++solves;
     } else {
       const int n = own_count(g, i);
-      for (int e = threadIdx.x; e < n; e += DY_THREADS) u[own_idx(g, i, e, (int)nsub)] = cxd{0, 0};
+      for (int e = threadIdx.x; e < n; e += (int)blockDim.x) u[own_idx(g, i, e, (int)nsub)] = cxd{0, 0};
     }
     double prev = INFINITY;
     for (int r = 0; r < g.refine_max && hn > 0.0; ++r) {
@@ -1609,7 +1632,7 @@ __global__ void __launch_bounds__(DY_THREADS, 2) k_xmatvec(Geo g, Bufs b, int j,
       ++solves;
       __syncthreads();
       const int n = own_count(g, i);
-      for (int e = threadIdx.x; e < n; e += DY_THREADS) {
+      for (int e = threadIdx.x; e < n; e += (int)blockDim.x) {
         size_t k = own_idx(g, i, e, (int)nsub);
         u[k] = u[k] + wv[k];
       }
@@ -1652,15 +1675,15 @@ __global__ void __launch_bounds__(DY_THREADS, 2) k_bsolve(Geo g, Bufs b, const c
   sa.dst_op = 0;
   sweep<R, WF>(g, i, sa, sm, pp, sweep_cnt(g, b, vs, i));
   if (i < g.p - 1)
-    for (int a = threadIdx.x; a < g.A; a += DY_THREADS)
+    for (int a = threadIdx.x; a < g.A; a += (int)blockDim.x)
       w[(size_t)kf * g.Ndd + g.ifc_off + (size_t)i * g.A + a] = cxd{0, 0};
   __syncthreads();
   if (threadIdx.x == 0 && err) atomicOr(b.st + (size_t)kf * ST_N + ST_STATUS, ST_WAIT_TIMEOUT);
 }
 
 template <typename Kern, typename... Args>
-cudaError_t launch_cluster(Kern kern, dim3 grid, int cx_, size_t smem, cudaStream_t st,
-                           Args... args) {
+cudaError_t launch_cluster_nt(Kern kern, dim3 grid, int cx_, int threads, size_t smem, cudaStream_t st,
+                              Args... args) {
   cudaError_t e = raise_smem_limit((const void*)kern, smem);
   if (e != cudaSuccess) return e;
   if (cx_ > 8) {
@@ -1669,7 +1692,7 @@ cudaError_t launch_cluster(Kern kern, dim3 grid, int cx_, size_t smem, cudaStrea
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
-  cfg.blockDim = dim3(DY_THREADS);
+  cfg.blockDim = dim3(threads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
@@ -1680,6 +1703,11 @@ cudaError_t launch_cluster(Kern kern, dim3 grid, int cx_, size_t smem, cudaStrea
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+template <typename Kern, typename... Args>
+cudaError_t launch_cluster(Kern kern, dim3 grid, int cx_, size_t smem, cudaStream_t st, Args... args) {
+  return launch_cluster_nt(kern, grid, cx_, DY_THREADS, smem, st, args...);
 }
 
 template <typename R>
@@ -1709,8 +1737,11 @@ cudaError_t run_bsolve(const Geo& g, const Bufs& b, int K, const cxd* q_dd, cxd*
   template <>                                                                                     \
   cudaError_t run_xmatvec<R, WF>(const Geo& g, const Bufs& b, int K, int j, int mixed, int ncols, \
                                  cudaStream_t st) {                                               \
-    return launch_cluster(k_xmatvec<R, WF>, dim3(g.p, K * g.nb), g.p, sweep_smem<R>(g), st, g, b, \
-                          j, mixed, ncols);                                                       \
+    if (sizeof(R) == 4 && xm_threads<R>(g) == 128)                                                \
+      return launch_cluster_nt(k_xmatvec<R, WF, (sizeof(R) == 4 ? 128 : 256)>, dim3(g.p, K * g.nb), \
+                               g.p, 128, sweep_smem<R>(g), st, g, b, j, mixed, ncols);           \
+    return launch_cluster_nt(k_xmatvec<R, WF, 256>, dim3(g.p, K * g.nb), g.p, 256,                \
+                             sweep_smem<R>(g), st, g, b, j, mixed, ncols);                        \
   }                                                                                               \
   template <>                                                                                     \
   cudaError_t run_bsolve<R, WF>(const Geo& g, const Bufs& b, int K, const cxd* q_dd, cxd* w_dd,   \

@@ -95,7 +95,7 @@ def load(path: str = LIB_PATH):
         "dyson_plan_footprint": ([C.POINTER(dyson_geometry), C.POINTER(C.c_size_t)], I),
         "dyson_plan_create": ([C.POINTER(dyson_geometry), C.POINTER(P)], I),
         "dyson_plan_destroy": ([P], I),
-        "dyson_plan_tuning": ([P, P, P, P, P, P], I),
+        "dyson_plan_tuning": ([P, P, P, P, P, P, P], I),
         "dyson_solve": ([P, I, P, P, P, P, P, P, I, P], I),
         "dyson_solve_info": ([P, I, P, P, P, P], I),
         "dyson_block_info": ([P, I, P, P], I),
@@ -222,12 +222,13 @@ def dyson_partition(geom):
 
 
 def dyson_plan_tuning(plan):
-    """(ring slots, chunk rows, configurations timed, heuristic ms, kept ms) of a plan."""
-    s, cr, n = C.c_int(), C.c_int(), C.c_int()
+    """Ring slots, chunk rows, X-matvec threads per CTA, configurations timed, heuristic
+    and kept launch ms of a plan."""
+    s, cr, n, nt = C.c_int(), C.c_int(), C.c_int(), C.c_int()
     mh, mb = C.c_float(), C.c_float()
     _check(load().dyson_plan_tuning(plan, C.addressof(s), C.addressof(cr), C.addressof(n),
-                                    C.addressof(mh), C.addressof(mb)))
-    return dict(ring_slots=s.value, chunk_rows=cr.value, candidates=n.value,
+                                    C.addressof(mh), C.addressof(mb), C.addressof(nt)))
+    return dict(ring_slots=s.value, chunk_rows=cr.value, threads=nt.value, candidates=n.value,
                 ms_heuristic=mh.value, ms_best=mb.value)
 
 
