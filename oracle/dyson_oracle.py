@@ -612,6 +612,21 @@ def xmatvec(L, periodic, t, mu, V, sigma_k, omega_k, p, q, eta: float = 0.0):
     return full.solve(q) - subs.solve(q)
 
 
+def xmatvec_cancel_free(L, periodic, t, mu, V, sigma_k, omega_k, p, q, eta: float = 0.0):
+    """The same X q as xmatvec (Eqs. 6-8) through an equivalent form: with
+    w = blkdiag(B^-1, 0) q, H (v - w) = q - H w, so u = H^-1 (q - H w).  The
+    right-hand side vanishes on the subdomains up to rounding, so the
+    subtraction of two nearly equal vectors in Eq. 8 is avoided.  Both forms
+    give X q in exact arithmetic; their FP64 results differ at the rounding
+    level, which measures how much FP64 rounding of the X-matvec moves the
+    truncated Lanczos result."""
+    z = axis_diagonal(omega_k, mu, V, sigma_k, eta)
+    subs = Subdomains(L, periodic, t, z, p)
+    full = FullLattice(L, periodic, t, z)
+    w = subs.solve(q)
+    return full.solve(q - apply_H(L, periodic, t, mu, V, sigma_k, omega_k, w, eta))
+
+
 def apply_H(L, periodic, t, mu, V, sigma_k, omega_k, x, eta: float = 0.0):
     """y = H x by the stencil (Eq. 1), natural order, without forming H."""
     z = axis_diagonal(omega_k, mu, V, sigma_k, eta)

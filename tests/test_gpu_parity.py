@@ -14,8 +14,8 @@ from oracle import dyson_oracle as O
 from paper_1102_3137_gb300 import dyson as D
 from paper_1102_3137_gb300 import inputs as I
 
-from parity_util import (OPEN, TOL_FP64, TOL_MIXED, oracle_parts, oracle_sensitivity, plan_for,
-                         relerr, stepwise_check, wl)
+from parity_util import (OPEN, TOL_FP64, TOL_MIXED, oracle_parts, plan_for, relerr, rounding_bound,
+                         stepwise_check, wl)
 
 pytestmark = pytest.mark.gpu
 
@@ -250,10 +250,12 @@ def test_iteration_cap_reports_status():
 
 @pytest.mark.parametrize("precision,tol", [(D.DYSON_FP64, TOL_FP64), (D.DYSON_MIXED, TOL_MIXED)])
 def test_square128_full_batch_sampled(precision, tol):
-    """128x128, K = 64 in one launch (the benchmark's configuration), p = 4, k = 32:
-    sampled frequencies checked step by step, and directly against the oracle within
-    its own sensitivity at the GPU's X-matvec accuracy."""
-    w = I.WORKLOADS["square128_K64_p4_k32"]
+    """128x128, K = 64 in one launch, p = 4, k = 32: sampled frequencies checked step
+    by step at the form's tolerance, and directly against the oracle within the fixed
+    bound max(tol, amplification * 1e-13), the amplification of X-matvec rounding into
+    the truncated rank-32 diagonal measured on the oracle alone (tests/golden)."""
+    name = "square128_K64_p4_k32"
+    w = I.WORKLOADS[name]
     omega, V, sigma, q1 = I.make_inputs(w)
     pl = plan_for(w, precision)
     st = np.zeros(w.K, np.int32)
@@ -264,23 +266,8 @@ def test_square128_full_batch_sampled(precision, tol):
     for k in (0, 31, 63):
         subs, X = oracle_parts(w, omega[k], V, sigma[k])
         stepwise_check(w, pl, k, subs, X, q1, out[k], info, tol)
-        # the GPU's X-matvec accuracy on this frequency, over the run's own Lanczos
-        # vectors (each interface solve stops at its tolerance, so the error differs
-        # from vector to vector)
-        sel = [0, 8, 16, 24, w.k - 1]
-        qs = np.ascontiguousarray(D.dyson_lanczos_basis(pl.handle, k, w.k, w.N)[sel])
-        ns = len(sel)
-        pm = D.Plan(w.L, w.t, w.mu, w.p, w.k, precision, max_freqs=ns)
-        u = np.zeros((ns, w.N), complex)
-        D.dyson_xmatvec(pm.handle, ns, np.full(ns, omega[k]), V,
-                        np.ascontiguousarray(np.repeat(sigma[k:k + 1], ns, axis=0)), qs, u)
-        pm.close()
-        eps = 1e-15
-        for c in range(ns):
-            ux = X(qs[c])
-            eps = max(eps, float(np.linalg.norm(u[c] - ux) / np.linalg.norm(ux)))
-        base, sens = oracle_sensitivity(w, subs, X, q1, eps)
-        assert relerr(out[k], base) <= max(tol, 10 * sens), (k, eps, sens)
+        base = subs.diagB + O.cs_lanczos(X, q1, w.k)[0]
+        assert relerr(out[k], base) <= rounding_bound(name, k, tol), k
 
 
 @pytest.mark.parametrize("precision", [D.DYSON_FP64, D.DYSON_MIXED])

@@ -696,3 +696,35 @@ def test_block_qr_breakdown_and_deflation():
     R2 = np.array([[1.0, 2.0], [0.5, 1.0], [0.0, 0.0]], dtype=complex)  # column 1 = 2 x column 0
     Q2, B2, defl2, brk2 = O._bilinear_qr(R2, 1.0, 1e-12, 1e-14)
     assert not brk2 and list(defl2) == [False, True] and np.all(Q2[:, 1] == 0)
+
+
+def test_cancel_free_xmatvec_matches_dense_X():
+    """u = H^-1 (q - H w) is the X-matvec of Eqs. 6-8 (w = blkdiag(B^-1, 0) q)."""
+    rng = np.random.default_rng(12)
+    L, p = (9, 10), 3
+    omega, V, sigma, q1 = I.make_inputs(I.Workload("t", L, -1.0, 0.0, 0.01, 0.5, 10.0, 2, p, 4, 3))
+    z = O.dyson_diagonal(omega[0], 0.0, V, sigma[0])
+    H = O.dense_H(L, (False,) * 3, -1.0, z)
+    _, iface = O.dd_sites(L, p)
+    X, _ = _dense_X(H, np.concatenate(iface))
+    q = rng.normal(size=90) + 1j * rng.normal(size=90)
+    u = O.xmatvec_cancel_free(L, (False,) * 3, -1.0, 0.0, V, sigma[0], omega[0], p, q)
+    assert np.max(np.abs(u - X @ q)) < 1e-12 * np.max(np.abs(X @ q))
+
+
+def test_rounding_amplification_record_c2():
+    """The stored amplification of X-matvec rounding into the truncated rank-32 diagonal
+    (tests/golden/rounding_spread.json, written by make_rounding_spread.py from the
+    oracle alone) is what the oracle gives now, within a factor of 3 (it is a ratio of
+    rounding-level quantities, so its value moves with the BLAS's summation order)."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("mrs", os.path.join(GOLDEN, "make_rounding_spread.py"))
+    mrs = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mrs)
+    with open(os.path.join(GOLDEN, "rounding_spread.json")) as f:
+        rec = json.load(f)["square128_K64_p4_k32"]
+    for k in (0, 63):
+        now = mrs.spread("square128_K64_p4_k32", k)
+        ratio = now["amplification"] / rec[str(k)]["amplification"]
+        assert 1 / 3 < ratio < 3, (k, now, rec[str(k)])
+        assert now["delta"] < 1e-14                 # both forms of Eq. 8 agree to rounding
