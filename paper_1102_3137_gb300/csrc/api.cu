@@ -78,10 +78,13 @@ int build_part(const dyson_geometry* in, Part* out, bool gpu) {
   if (in->precond < DYSON_PRECOND_AUTO || in->precond > DYSON_PRECOND_LAYER)
     return fail(DYSON_E_BAD_ARG, "precond must be DYSON_PRECOND_AUTO, _BANDED or _LAYER");
   {
-    const bool fits = g.T == 1 && g.p > 1 && g.W <= DY_LPRE_MAXW && g.Lx <= DY_LPRE_MAXLX;
+    const bool fits = g.T == 1 && g.p > 1 && g.W <= DY_LPRE_MAXW &&
+                      (g.Lx <= DY_LPRE_MAXLX || (g.Lx <= DY_LPRE_MAXLX_G && g.W == DY_LPRE_MAXW));
     if (in->precond == DYSON_PRECOND_LAYER && !fits)
-      return fail(DYSON_E_UNSUPPORTED, "exact layer preconditioner: 2D strips with p > 1, Lx <= " +
+      return fail(DYSON_E_UNSUPPORTED, "exact layer preconditioner: 2D strips with p > 1 and either Lx <= " +
                                            std::to_string(DY_LPRE_MAXLX) + " and slice width <= " +
+                                           std::to_string(DY_LPRE_MAXW) + ", or Lx <= " +
+                                           std::to_string(DY_LPRE_MAXLX_G) + " and slice width " +
                                            std::to_string(DY_LPRE_MAXW) + " only");
     g.lpre = (fits && in->precond != DYSON_PRECOND_BANDED) ? 1 : 0;
   }
@@ -133,7 +136,7 @@ int build_part(const dyson_geometry* in, Part* out, bool gpu) {
 enum {
   B_V, B_OMEGA, B_SIGMA, B_Q1, B_DD2NAT, B_G, B_G64, B_DIAGB, B_Q, B_ACC, B_U, B_V1, B_V2, B_V3,
   B_YSCR, B_BND, B_IFV, B_PRE, B_LAN, B_MAXT, B_ST, B_OUT, B_STATUS, B_SWEEPS, B_FWORK, B_OFFB, B_OFF2,
-  B_LPT, B_LPM, B_LPG, B_COUNT
+  B_LPT, B_LPM, B_LPG, B_LPV, B_COUNT
 };
 
 size_t layout(const Geo& g, int K, bool mixed, size_t off[B_COUNT]) {
@@ -172,6 +175,7 @@ size_t layout(const Geo& g, int K, bool mixed, size_t off[B_COUNT]) {
   sz[B_LPT] = g.lpre ? Kz * g.p * 2 * Lx2 * sizeof(cxf) : 0;
   sz[B_LPM] = g.lpre ? Kz * (g.p - 1) * Lx2 * cs : 0;
   sz[B_LPG] = g.lpre ? Kz * g.p * nsub * g.W * sizeof(cxf) : 0;
+  sz[B_LPV] = (g.lpre && g.Lx > DY_LPRE_MAXLX) ? Kz * g.p * 2 * (size_t)g.Lx * g.W * sizeof(cxf) : 0;
   size_t o = 0;
   for (int k = 0; k < B_COUNT; ++k) {
     off[k] = o;
@@ -365,6 +369,7 @@ Bufs sub_bufs(const Geo& g, const Bufs& b, bool mixed, int k0) {
   s.lpt = b.lpt ? b.lpt + K0 * g.p * 2 * Lx2 : nullptr;
   s.lpm = adv(reinterpret_cast<char*>(b.lpm), K0 * (g.p > 1 ? g.p - 1 : 0) * Lx2 * cs);
   s.lpg = b.lpg ? b.lpg + K0 * g.p * nsub * g.W : nullptr;
+  s.lpv = b.lpv ? b.lpv + K0 * g.p * 2 * (size_t)g.Lx * g.W : nullptr;
   return s;
 }
 
@@ -600,6 +605,7 @@ int dyson_plan_create(const dyson_geometry* geom, dyson_plan* out) {
   b.lpt = p->g.lpre ? at<cxf>(p, B_LPT) : nullptr;
   b.lpm = p->g.lpre ? (void*)at<char>(p, B_LPM) : nullptr;
   b.lpg = p->g.lpre ? at<cxf>(p, B_LPG) : nullptr;
+  b.lpv = (p->g.lpre && p->g.Lx > DY_LPRE_MAXLX) ? at<cxf>(p, B_LPV) : nullptr;
   p->status_d = at<int>(p, B_STATUS);
   p->profile = false;
   p->tuned = false;

@@ -26,7 +26,8 @@
 #define DY_MAXW 256         // widest slice the sweep kernels take
 #define DY_MAXW_SMEM 64     // widest slice the shared-memory factor kernel takes
 #define DY_MAXNB 4          // largest Lanczos block size
-#define DY_LPRE_MAXLX 160   // widest interface line the exact layer preconditioner takes
+#define DY_LPRE_MAXLX 160   // widest interface line of the shared-memory layer preconditioner
+#define DY_LPRE_MAXLX_G 1024 // widest interface line of its global-memory form
 #define DY_LPRE_MAXW 32     // widest slice it takes
 #define DY_FREQ_GROUPS 4    // default frequency groups of a solve (parallel graph branches)
 #define DY_MAX_GROUPS 8
@@ -229,6 +230,7 @@ struct Bufs {
   cx<float>* lpt;       // [K][p][2][Lx][Lx] boundary-row surface Green's functions (lpre)
   cx<float>* lpg;       // [K][p][Lx][W][W] complex64 slice factors of that recursion (lpre scratch)
   void* lpm;            // [K][p-1][Lx][Lx] inverse layer blocks of S, precision of the form (lpre)
+  cx<float>* lpv;       // [K][p][2][Lx][W] boundary columns of the surface recursion (lpre, Lx > 160)
 };
 
 // interface Krylov vector slots inside ifv

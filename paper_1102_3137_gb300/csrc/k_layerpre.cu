@@ -21,7 +21,16 @@
 //   k_layer_inv  per (interface line, frequency): S_ll and its inverse by the
 //                sweep operator, symmetrised so that COCG sees a complex
 //                symmetric M^-1.
+// Lines longer than DY_LPRE_MAXLX (160) do not fit shared memory; there
+//   k_surface_g  keeps the boundary columns of G_{s,s'} in global memory
+//                (one warp per column, the column broadcast through shared
+//                memory), and
+//   k_layer_inv_g forms S_ll in place of P_top(l) and inverts it there by
+//                block Gauss-Jordan on 32 x 32 blocks (pivot block by the sweep
+//                operator in shared memory, row panel, rank-32 update of the
+//                rest, column panel), then writes the symmetrised inverse.
 #include "solve_device.cuh"
+#include "tc_tf32.cuh"
 
 namespace {
 
@@ -212,6 +221,220 @@ __global__ void __launch_bounds__(DY_THREADS, 2) k_surface(Geo g, Bufs b) {
   }
 }
 
+// The same surface Green's functions for lines longer than the shared-memory
+// form takes (Lx > DY_LPRE_MAXLX, slice width 32): the boundary columns
+// V[c][r] of G_{s,c}, c > s, live in global memory (b.lpv), column-major, and
+// the update V[:, c] <- -t g_s V[:, c] runs one warp per column: the warp
+// reads its column, broadcasts it through shared memory and lane r forms row
+// r of the product from its register copy of row r of g_s.  Only that warp
+// touches column c within a step, so the in-place update needs no barrier.
+__global__ void __launch_bounds__(DY_THREADS) k_surface_g(Geo g, Bufs b) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int W = 32, n = W * W;
+  const int i = blockIdx.x, f = blockIdx.y;
+  const int Lx = g.Lx, w = g.h[i];
+  const bool need_top = i < g.p - 1, need_bot = i > 0;
+  cxf_* Gs = reinterpret_cast<cxf_*>(smem_raw);   // g_s
+  cxf_* Gd = Gs + n;                              // G_ss
+  cxf_* Tm = Gd + n;
+  cxf_* prow = Tm + n;
+  cxf_* fcol = prow + W;
+  cxf_* colb = fcol + W;                          // [8 warps][W] column broadcast
+  cxf_* gsv = b.lpg + ((size_t)f * g.p + i) * (size_t)Lx * n;
+  cxf_* Pt = b.lpt + (((size_t)f * g.p + i) * 2 + 0) * (size_t)Lx * Lx;
+  cxf_* Pb = b.lpt + (((size_t)f * g.p + i) * 2 + 1) * (size_t)Lx * Lx;
+  cxf_* Vt = b.lpv + (((size_t)f * g.p + i) * 2 + 0) * (size_t)Lx * W;   // [Lx][W]
+  cxf_* Vb = b.lpv + (((size_t)f * g.p + i) * 2 + 1) * (size_t)Lx * W;
+  const float t = d2f_bits(g.t), t2 = t * t;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+
+  // forward: g_s = (D_s - t^2 g_{s-1})^-1, padding rows/columns carry the identity
+  for (int s = 0; s < Lx; ++s) {
+    for (int e = threadIdx.x; e < n; e += DY_THREADS) {
+      const int r = e / W, c = e - r * W;
+      cxf_ v = {0.f, 0.f};
+      if (r < w && c < w) {
+        if (r == c) {
+          const cxd d = dyson_diag(g, b, f, sub_nat(g, i, s, r));
+          v = cxf_{d2f_bits(d.x), d2f_bits(d.y)};
+        } else if (r == c + 1 || c == r + 1) {
+          v = cxf_{t, 0.f};
+        }
+        if (s > 0) v = cfma(cxf_{-t2, 0.f}, Gs[e], v);
+      } else if (r == c) {
+        v = cxf_{1.f, 0.f};
+      }
+      Gs[e] = v;
+    }
+    sweep_invert_f(Gs, W, prow, fcol);
+    for (int e = threadIdx.x; e < n; e += DY_THREADS) {
+      const int r = e / W, c = e - r * W;
+      if (r >= w || c >= w) Gs[e] = cxf_{0.f, 0.f};
+      gsv[(size_t)s * n + e] = Gs[e];
+    }
+    __syncthreads();
+  }
+  // backward: G_ss, and for every c > s the boundary columns of G_{s,c} = -t g_s G_{s+1,c}
+  cxf_* cb = colb + wid * W;
+  for (int s = Lx - 1; s >= 0; --s) {
+    for (int e = threadIdx.x; e < n; e += DY_THREADS) Gs[e] = gsv[(size_t)s * n + e];
+    __syncthreads();
+    if (s == Lx - 1) {
+      for (int e = threadIdx.x; e < n; e += DY_THREADS) Gd[e] = Gs[e];
+    } else {
+      small_matmul32(Tm, Gs, Gd, 1.f, nullptr);          // g_s G_{s+1,s+1}
+      __syncthreads();
+      small_matmul32(Gd, Tm, Gs, t2, Gs);                 // g_s + t^2 g_s G g_s
+      cxf_ gr[W];                                         // row `lane` of g_s (symmetric)
+#pragma unroll
+      for (int k = 0; k < W; ++k) gr[k] = Gs[k * W + lane];
+      for (int side = 0; side < 2; ++side) {
+        if (side == 0 ? !need_top : !need_bot) continue;
+        cxf_* V = side == 0 ? Vt : Vb;
+        cxf_* P = side == 0 ? Pt : Pb;
+        const int rb = side == 0 ? w - 1 : 0;
+        for (int c = s + 1 + wid; c < Lx; c += DY_WARPS) {
+          cb[lane] = V[(size_t)c * W + lane];
+          __syncwarp();
+          cxf_ acc0 = {0.f, 0.f}, acc1 = {0.f, 0.f};
+#pragma unroll
+          for (int k = 0; k < W; k += 2) {
+            acc0 = cfma(gr[k], cb[k], acc0);
+            acc1 = cfma(gr[k + 1], cb[k + 1], acc1);
+          }
+          const cxf_ acc = acc0 + acc1;
+          const cxf_ out = {-t * acc.x, -t * acc.y};
+          __syncwarp();                                   // the column is read before it is rewritten
+          V[(size_t)c * W + lane] = out;
+          if (lane == rb) {
+            P[(size_t)s * Lx + c] = out;
+            P[(size_t)c * Lx + s] = out;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    // start the chain of column c = s: the boundary columns of G_ss
+    for (int r = threadIdx.x; r < W; r += DY_THREADS) {
+      Vt[(size_t)s * W + r] = Gd[r * W + (w - 1)];
+      Vb[(size_t)s * W + r] = Gd[r * W + 0];
+    }
+    if (threadIdx.x == 0) {
+      Pt[(size_t)s * Lx + s] = Gd[(w - 1) * W + (w - 1)];
+      Pb[(size_t)s * Lx + s] = Gd[0];
+    }
+    __syncthreads();
+  }
+}
+
+// S_ll and its inverse for lines longer than the shared-memory form takes, in
+// place of P_top(l) (only line l reads it): A = S_ll, then block Gauss-Jordan
+// with NB x NB blocks,
+//   P = A_kk^-1;  A_kj <- P A_kj;  A_ij <- A_ij - A_ik A_kj;  A_ik <- -A_ik P;  A_kk <- P
+// (i, j != k), which leaves A^-1; pivots come from the sweep operator on the
+// diagonal block (Im S_ll > 0 keeps them away from zero).  The symmetrised
+// inverse is written in the form's precision.
+constexpr int LINV_NB = 32;
+template <typename R>
+__global__ void __launch_bounds__(DY_THREADS) k_layer_inv_g(Geo g, Bufs b) {
+  __shared__ __align__(16) cxf_ Pk[LINV_NB * LINV_NB];
+  __shared__ __align__(16) cxf_ X[LINV_NB * LINV_NB];
+  __shared__ __align__(16) cxf_ Y[LINV_NB * LINV_NB];
+  __shared__ cxf_ prow[LINV_NB], fcol[LINV_NB];
+  constexpr int NB = LINV_NB;
+  const int l = blockIdx.x, f = blockIdx.y, Lx = g.Lx;
+  const size_t n2 = (size_t)Lx * Lx;
+  cxf_* A = b.lpt + (((size_t)f * g.p + l) * 2 + 0) * n2;          // P_top(l), overwritten
+  const cxf_* Pb = b.lpt + (((size_t)f * g.p + l + 1) * 2 + 1) * n2;
+  const float t = d2f_bits(g.t), t2 = t * t;
+  for (size_t e = threadIdx.x; e < n2; e += DY_THREADS) {
+    const int r = (int)(e / Lx), c = (int)(e - (size_t)r * Lx);
+    cxf_ v = {0.f, 0.f};
+    if (r == c) {
+      const cxd d = dyson_diag(g, b, f, r + g.A * g.ylayer[l]);
+      v = cxf_{d2f_bits(d.x), d2f_bits(d.y)};
+    } else if (r == c + 1 || c == r + 1) {
+      v = cxf_{t, 0.f};
+    }
+    A[e] = cfma(cxf_{-t2, 0.f}, A[e] + Pb[e], v);
+  }
+  const int nbk = (Lx + NB - 1) / NB;
+  // load / store a block (rows r0.., cols c0..), zero-padded past Lx (identity on the diagonal pad)
+  auto ld = [&](cxf_* T, int r0, int c0, bool diag) {
+    for (int e = threadIdx.x; e < NB * NB; e += DY_THREADS) {
+      const int r = e / NB, c = e - r * NB;
+      cxf_ v = {0.f, 0.f};
+      if (r0 + r < Lx && c0 + c < Lx) v = A[(size_t)(r0 + r) * Lx + c0 + c];
+      else if (diag && r == c) v = cxf_{1.f, 0.f};
+      T[e] = v;
+    }
+  };
+  auto st = [&](const cxf_* T, int r0, int c0) {
+    for (int e = threadIdx.x; e < NB * NB; e += DY_THREADS) {
+      const int r = e / NB, c = e - r * NB;
+      if (r0 + r < Lx && c0 + c < Lx) A[(size_t)(r0 + r) * Lx + c0 + c] = T[e];
+    }
+  };
+  // C(r0, c0) <- C + alpha * (Xm Ym) or alpha * (Xm Ym) (overwrite), 32 x 32 x 32 on
+  // the tensor cores (3xTF32, binary32 accuracy): warp w computes the 16 x 8 tile
+  // at rows 16 (w / 4), columns 8 (w % 4)
+  auto mm = [&](const cxf_* Xm, const cxf_* Ym, int r0, int c0, float alpha, bool accumulate) {
+    const int wq = threadIdx.x >> 5, tm = 16 * (wq >> 2), tn = 8 * (wq & 3);
+    tc::CTile acc = {};
+    tc::cgemm_tile_3xtf32(acc, Xm, Ym, NB, tm, tn);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      int r, c;
+      tc::tile_pos(e, tm, tn, r, c);
+      if (r0 + r < Lx && c0 + c < Lx) {
+        cxf_& o = A[(size_t)(r0 + r) * Lx + c0 + c];
+        const cxf_ v = {alpha * acc.re[e], alpha * acc.im[e]};
+        o = accumulate ? o + v : v;
+      }
+    }
+  };
+  static_assert(LINV_NB == 32 && DY_THREADS == 256, "eight 16 x 8 tensor-core tiles per 32 x 32 block");
+  for (int kb = 0; kb < nbk; ++kb) {
+    const int k0 = kb * NB;
+    __syncthreads();
+    ld(Pk, k0, k0, true);
+    sweep_invert_f(Pk, NB, prow, fcol);                   // Pk = A_kk^-1
+    // row panel A_kj <- Pk A_kj
+    for (int jb = 0; jb < nbk; ++jb) {
+      if (jb == kb) continue;
+      __syncthreads();
+      ld(Y, k0, jb * NB, false);
+      __syncthreads();
+      mm(Pk, Y, k0, jb * NB, 1.f, false);
+    }
+    // rank-NB update of the rest with the old column panel
+    for (int ib = 0; ib < nbk; ++ib) {
+      if (ib == kb) continue;
+      __syncthreads();
+      ld(X, ib * NB, k0, false);
+      for (int jb = 0; jb < nbk; ++jb) {
+        if (jb == kb) continue;
+        __syncthreads();
+        ld(Y, k0, jb * NB, false);
+        __syncthreads();
+        mm(X, Y, ib * NB, jb * NB, -1.f, true);
+      }
+      // column panel of this block row: A_ik <- -A_ik Pk (X still holds the old A_ik)
+      __syncthreads();
+      mm(X, Pk, ib * NB, k0, -1.f, false);
+    }
+    __syncthreads();
+    st(Pk, k0, k0);
+  }
+  __syncthreads();
+  cx<R>* M = reinterpret_cast<cx<R>*>(b.lpm) + ((size_t)f * (g.p - 1) + l) * n2;
+  for (size_t e = threadIdx.x; e < n2; e += DY_THREADS) {
+    const int r = (int)(e / Lx), c = (int)(e - (size_t)r * Lx);
+    const cxf_ a = A[e], at = A[(size_t)c * Lx + r];
+    M[e] = cx<R>{(R)(0.5f * (a.x + at.x)), (R)(0.5f * (a.y + at.y))};
+  }
+}
+
 // S_ll = C_ll - t^2 (P_top(l) + P_bot(l+1)) and M_l^-1, symmetrised, in the form's precision.
 template <typename R>
 __global__ void __launch_bounds__(DY_THREADS) k_layer_inv(Geo g, Bufs b) {
@@ -251,12 +474,20 @@ size_t dyson_internal_surface_smem(const Geo& g) {
 }
 
 size_t dyson_internal_layer_inv_smem(const Geo& g) {
+  if (g.Lx > DY_LPRE_MAXLX) return 0;                      // global-memory form
   return ((size_t)g.Lx * g.Lx + 2 * (size_t)g.Lx) * sizeof(cxf_);
 }
 
+static size_t surface_g_smem() { return (3 * 32 * 32 + 2 * 32 + DY_WARPS * 32) * sizeof(cxf_); }
+
 cudaError_t launch_surface(const Geo& g, const Bufs& b, int K, cudaStream_t st) {
   if (!g.lpre) return cudaSuccess;
-  if (g.W > SURF_MAXW || g.Lx > DY_LPRE_MAXLX) return cudaErrorInvalidValue;
+  if (g.W > SURF_MAXW || g.Lx > DY_LPRE_MAXLX_G) return cudaErrorInvalidValue;
+  if (g.Lx > DY_LPRE_MAXLX) {
+    if (g.W != 32 || !b.lpv) return cudaErrorInvalidValue;
+    k_surface_g<<<dim3(g.p, K), DY_THREADS, surface_g_smem(), st>>>(g, b);
+    return cudaGetLastError();
+  }
   const size_t smem = dyson_internal_surface_smem(g);
   if (g.W == 32) {
     cudaError_t e = raise_smem_limit((const void*)k_surface<32>, smem);
@@ -273,6 +504,10 @@ cudaError_t launch_surface(const Geo& g, const Bufs& b, int K, cudaStream_t st) 
 template <typename R>
 cudaError_t launch_layer_inv(const Geo& g, const Bufs& b, int K, cudaStream_t st) {
   if (!g.lpre) return cudaSuccess;
+  if (g.Lx > DY_LPRE_MAXLX) {
+    k_layer_inv_g<R><<<dim3(g.p - 1, K), DY_THREADS, 0, st>>>(g, b);
+    return cudaGetLastError();
+  }
   const size_t smem = dyson_internal_layer_inv_smem(g);
   cudaError_t e = raise_smem_limit((const void*)k_layer_inv<R>, smem);
   if (e != cudaSuccess) return e;

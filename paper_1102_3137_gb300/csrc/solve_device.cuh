@@ -435,6 +435,7 @@ __device__ void sweep_pair(const Geo& g, int i, const SweepArgs<float>& a, cxf* 
   };
   auto rd = [&](int s, int r) { return yb[(size_t)s * W + r]; };
 
+
   __syncthreads();                       // previous users of ring, z buffers and yb are done
   if (tid == 0) {
     fence_proxy_async();
@@ -1111,15 +1112,23 @@ __device__ __noinline__ void lpre_apply(const Geo& g, const Bufs& b, int vs, int
   const int Lx = g.Lx;
   const C* rsh = r;                 // every thread reads all of r: served by L1
   const C* M = reinterpret_cast<const C*>(b.lpm) + ((size_t)slot_freq(g, vs) * (g.p - 1) + i) * (size_t)Lx * Lx;
+  // eight entries of the column in flight per thread before any is used: M is
+  // read from HBM on every application (long lines keep 2 MB per line), so the
+  // product is bound by how many loads each thread keeps outstanding
+  constexpr int U = 8;
   for (int a = threadIdx.x; a < Lx; a += (int)blockDim.x) {
-    C acc0 = {0, 0}, acc1 = {0, 0};
+    C acc[4] = {};
+    const C* col = M + a;
     int c = 0;
-    for (; c + 1 < Lx; c += 2) {
-      acc0 = cfma(M[(size_t)c * Lx + a], rsh[c], acc0);
-      acc1 = cfma(M[(size_t)(c + 1) * Lx + a], rsh[c + 1], acc1);
+    for (; c + U <= Lx; c += U) {
+      C mv[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) mv[u] = col[(size_t)(c + u) * Lx];
+#pragma unroll
+      for (int u = 0; u < U; ++u) acc[u & 3] = cfma(mv[u], rsh[c + u], acc[u & 3]);
     }
-    if (c < Lx) acc0 = cfma(M[(size_t)c * Lx + a], rsh[c], acc0);
-    z[a] = acc0 + acc1;
+    for (; c < Lx; ++c) acc[0] = cfma(col[(size_t)c * Lx], rsh[c], acc[0]);
+    z[a] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
   }
 }
 

@@ -147,10 +147,13 @@ def test_null_plan_is_an_error(lib):
 
 
 def test_layer_preconditioner_limits(lib):
-    # 2D strips with Lx <= 160 and slice width <= 32 take the exact layer blocks
-    ok = D.make_geometry((160, 33), p=2, k_max=4, max_freqs=1, precond=D.DYSON_PRECOND_LAYER)
-    assert D.dyson_plan_footprint(ok) > 0
-    for L, p in (((161, 33), 2), ((64, 70), 2)):      # line too long; slice width 36 > 32
+    # 2D strips with Lx <= 160 and slice width <= 32, or Lx <= 1024 and slice width 32,
+    # take the exact layer blocks
+    for L in ((160, 33), (200, 65), (1024, 65)):
+        ok = D.make_geometry(L, p=2, k_max=4, max_freqs=1, precond=D.DYSON_PRECOND_LAYER)
+        assert D.dyson_plan_footprint(ok) > 0
+    # line beyond 160 with slice width 16; slice width 36 > 32; line beyond 1024
+    for L, p in (((161, 33), 2), ((64, 70), 2), ((1025, 65), 2)):
         g = D.make_geometry(L, p=p, k_max=4, max_freqs=1, precond=D.DYSON_PRECOND_LAYER)
         with pytest.raises(D.DysonError) as e:
             D.dyson_plan_footprint(g)

@@ -17,7 +17,8 @@ PRE = [D.DYSON_PRECOND_LAYER, D.DYSON_PRECOND_BANDED]
 
 
 @pytest.mark.parametrize("pre", PRE)
-@pytest.mark.parametrize("L,p", [((40, 37), 3), ((17, 50), 4), ((100, 30), 2), ((160, 21), 3)])
+@pytest.mark.parametrize("L,p", [((40, 37), 3), ((17, 50), 4), ((100, 30), 2), ((160, 21), 3),
+                                 ((200, 65), 2), ((512, 97), 3)])     # the last two: lines beyond 160
 @pytest.mark.parametrize("precision,tol", [(D.DYSON_FP64, 1e-11), (D.DYSON_MIXED, 1e-9)])
 def test_xmatvec_both_preconditioners(L, p, pre, precision, tol):
     w = wl(L, p, 4, K=2)
@@ -65,4 +66,24 @@ def test_layer_blocks_cut_interface_iterations():
     # COCG to 1e-13 with M = blkdiag(S_ll) in exact arithmetic (oracle, this geometry):
     # 4 iterations at w_0, 3 at w_1; the lines couple through strips of height 24
     assert np.all(per[D.DYSON_PRECOND_LAYER] <= np.array([4.5, 3.5, 3.5, 3.5]))
+    assert np.all(per[D.DYSON_PRECOND_LAYER] < per[D.DYSON_PRECOND_BANDED])
+
+
+def test_long_line_layer_blocks_cut_interface_iterations():
+    """Lines longer than 160 sites take the global-memory form of the layer blocks
+    (surface Green's functions with the boundary columns in global memory, block
+    Gauss-Jordan inverse); it must still cut the interface iterations well below the
+    banded form's on the 512-site lines of the 512^2 benchmark's strips."""
+    w = wl((512, 65), 2, 4, K=3, beta=10.0)
+    omega, V, sigma, q1 = I.make_inputs(w)
+    per = {}
+    for pre in PRE:
+        pl = plan_for(w, D.DYSON_FP64, precond=pre)
+        pl.solve(omega, V, sigma, q1)
+        info = pl.info(w.K)
+        per[pre] = info["iters"] / info["steps"]
+        pl.close()
+    # one interface line: its exact block is S itself, so COCG needs the iterations the
+    # complex64 inverse leaves to reach 1e-13 (two or three)
+    assert np.all(per[D.DYSON_PRECOND_LAYER] <= 3.5)
     assert np.all(per[D.DYSON_PRECOND_LAYER] < per[D.DYSON_PRECOND_BANDED])
