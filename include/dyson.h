@@ -153,7 +153,7 @@ int dyson_plan_footprint(const dyson_geometry* geom, size_t* bytes);
  * domain-decomposition maps and allocates all device workspace for up to
  * geom->max_freqs frequencies.  *out is set on success.
  * Slice width W = (sites of one slice: h in 2D, Ly*h in 3D, h the tallest
- * subdomain) rounded up to a multiple of 4 must be <= 256, and, with p > 1,
+ * subdomain) rounded up to a multiple of 4 must be <= 320, and, with p > 1,
  * for W > 64 the sweep row buffer (Lx * W complex entries in the form's
  * precision) must leave room for the copy ring in shared memory; otherwise
  * DYSON_E_UNSUPPORTED.  With p = 1 the solve is the exact slice recursion
@@ -263,10 +263,13 @@ int dyson_xmatvec(dyson_plan plan, int K, const double* omega, const double* V,
  * self-consistency iteration needs all frequencies again with a new
  * self-energy, Sec. 3).  Requests are admitted in arrival order as soon as the
  * device-memory budget (bytes of resident plans) and a stream slot allow;
- * admitted requests run concurrently, each as one batched, graph-replayed
+ * while the oldest request waits for memory, later requests whose plan is
+ * resident and idle run in its place (at most 64 per waiting request).
+ * Admitted requests run concurrently, each as one batched, graph-replayed
  * solve on its own stream.  Plans (factors, Lanczos bases, workspace) stay
  * resident and are reused by later requests with the same geometry; idle
- * plans are evicted least recently used first when memory is needed.  A
+ * plans are evicted least recently used first when memory is needed and
+ * evicting them makes enough room.  A
  * request's result is the same alone and in any mix.  Thread-safe: any
  * thread may submit, poll and wait.
  */
@@ -274,7 +277,8 @@ typedef struct dyson_server_s* dyson_server;
 
 typedef struct {
   dyson_geometry geom;   /* geometry and sizes; geom.max_freqs is the plan's capacity */
-  int K;                 /* frequencies in this request, 1..geom.max_freqs */
+  int K;                 /* frequencies in this request (>= 1); more than geom.max_freqs run as
+                            consecutive chunks of max_freqs on the same plan and stream */
   const double* omega;   /* [K] host (pinned host memory lets the copies overlap) */
   const double* V;       /* [N] host */
   const double* sigma;   /* complex[K][N] host */

@@ -23,7 +23,7 @@
 #define DY_MAXP 16          // largest cluster (one CTA per subdomain)
 #define DY_THREADS 256      // threads per CTA of every solver kernel
 #define DY_WARPS (DY_THREADS / 32)
-#define DY_MAXW 256         // widest slice the sweep kernels take
+#define DY_MAXW 320         // widest slice the sweep kernels take (48^3 with p = 8: 288)
 #define DY_MAXW_SMEM 64     // widest slice the shared-memory factor kernel takes
 #define DY_MAXNB 4          // largest Lanczos block size
 #define DY_LPRE_MAXLX 160   // widest interface line of the shared-memory layer preconditioner

@@ -7,12 +7,17 @@
 //     queue as soon as device memory (a budget of plan bytes) and a stream
 //     slot allow, so requests that arrive while others run start right away
 //     and their work overlaps on the GPU;
+//   - while the head waits for memory, a later request whose plan is resident
+//     and idle (it needs no memory) is admitted in its place, a bounded number
+//     of times per head, so one large request does not hold up small ones;
 //   - plans (factors, Lanczos bases, workspace) stay resident on the device
 //     and are reused by later requests with the same geometry; idle plans are
-//     evicted, least recently used first, when a new geometry needs room;
-//   - each admitted request runs its whole batched solve (one captured graph)
-//     on its own stream; completion is detected with events, and the latency
-//     from submission to completion is recorded per request.
+//     evicted, least recently used first, when a new geometry needs room (and
+//     only when evicting them makes room);
+//   - each admitted request runs its whole batched solve (one captured graph
+//     per chunk of at most the plan's max_freqs frequencies) on its own
+//     stream; completion is detected with events, and the latency from
+//     submission to completion is recorded per request.
 // A request's result does not depend on what else runs: every frequency is
 // computed by its own thread-block cluster with fixed-order reductions.
 #include <algorithm>
@@ -66,7 +71,15 @@ struct Req {
   double t_submit = 0, t_start = 0, t_done = 0;
   PlanSlot* slot = nullptr;
   int stream = -1;
+  int bypassed = 0;                        // later requests admitted while this one waited
 };
+
+// Backfill: while the request at the head of the queue waits for memory, a later
+// request whose plan is resident and idle (it needs no memory) may run; at most
+// BACKFILL_PER_HEAD times per head request, so the head is not starved, and only
+// among the first BACKFILL_WINDOW queued requests.
+constexpr int BACKFILL_PER_HEAD = 64;
+constexpr size_t BACKFILL_WINDOW = 256;
 
 }  // namespace
 
@@ -117,7 +130,12 @@ PlanSlot* acquire_plan(dyson_server_s* s, Req& q, std::unique_lock<std::mutex>& 
     *err = dyson_last_error();
     return nullptr;
   }
-  // evict idle plans, least recently used first, until the new one fits
+  // evict idle plans, least recently used first, until the new one fits; when
+  // even evicting every idle plan would not make room, evict nothing and wait
+  size_t idle = 0;
+  for (PlanSlot* ps : s->plans)
+    if (!ps->busy) idle += ps->bytes;
+  if (s->used - idle + need > s->budget) return nullptr;
   while (s->used + need > s->budget) {
     PlanSlot* victim = nullptr;
     for (PlanSlot* ps : s->plans)
@@ -183,27 +201,44 @@ void worker_main(dyson_server_s* s) {
       s->cv_done.notify_all();
     }
     if (s->stop && s->queue.empty() && running_count(s) == 0) break;
-    // ---- admissions, in arrival order
+    // ---- admissions, in arrival order (with backfill, see BACKFILL_PER_HEAD)
     while (!s->queue.empty() && running_count(s) < s->max_inflight) {
-      const uint64_t t = s->queue.front();
-      Req& q = s->reqs[t];
+      uint64_t t = s->queue.front();
+      Req& head = s->reqs[t];
       int rc = DYSON_OK;
       std::string err;
-      PlanSlot* ps = acquire_plan(s, q, lk, &rc, &err);
-      if (!ps) {
-        if (rc) {                                 // cannot be served at all
-          q.state = Q_FAILED;
-          q.rc = rc;
-          q.err = err;
-          s->queue.pop_front();
-          s->cv_done.notify_all();
-          continue;
-        }
-        break;                                    // wait for memory
+      PlanSlot* ps = acquire_plan(s, head, lk, &rc, &err);
+      if (!ps && rc) {                            // cannot be served at all
+        head.state = Q_FAILED;
+        head.rc = rc;
+        head.err = err;
+        s->queue.pop_front();
+        s->cv_done.notify_all();
+        continue;
       }
+      if (ps) {
+        s->queue.pop_front();
+      } else {                                    // the head waits for memory
+        if (s->queue.front() != t || head.bypassed >= BACKFILL_PER_HEAD) break;
+        for (size_t j = 1; j < s->queue.size() && j <= BACKFILL_WINDOW && !ps; ++j) {
+          Req& c = s->reqs[s->queue[j]];
+          for (PlanSlot* cand : s->plans)
+            if (!cand->busy && cand->key == c.key) {
+              ps = cand;
+              break;
+            }
+          if (ps) {
+            ps->busy = true;
+            t = s->queue[j];
+            s->queue.erase(s->queue.begin() + (long)j);
+            head.bypassed++;
+          }
+        }
+        if (!ps) break;                           // nothing can run without memory: wait
+      }
+      Req& q = s->reqs[t];
       int k = 0;
       while (s->stream_owner[k]) ++k;
-      s->queue.pop_front();
       s->stream_owner[k] = t;
       q.slot = ps;
       q.stream = k;
@@ -217,8 +252,17 @@ void worker_main(dyson_server_s* s) {
       cudaStream_t st = s->streams[k];
       cudaEvent_t ev = s->events[k];
       lk.unlock();
-      int e = dyson_internal_solve_enqueue(ps->plan, r.K, r.omega, r.V, r.sigma, r.q1, r.diagG,
-                                           r.status, DYSON_MEM_HOST, st);
+      // a request with more frequencies than its plan holds runs as consecutive
+      // chunks of max_freqs on the same plan and stream (frequencies are independent)
+      int e = DYSON_OK;
+      const int cap = r.geom.max_freqs;
+      const size_t N = (size_t)r.geom.L[0] * r.geom.L[1] * (r.geom.dim == 3 ? r.geom.L[2] : 1);
+      for (int k0 = 0; k0 < r.K && !e; k0 += cap) {
+        const int kc = r.K - k0 < cap ? r.K - k0 : cap;
+        e = dyson_internal_solve_enqueue(ps->plan, kc, r.omega + k0, r.V, r.sigma + 2 * (size_t)k0 * N, r.q1,
+                                         r.diagG + 2 * (size_t)k0 * N, r.status ? r.status + k0 : nullptr,
+                                         DYSON_MEM_HOST, st);
+      }
       std::string msg = e ? dyson_last_error() : "";
       if (!e) {
         cudaError_t ce = cudaEventRecord(ev, st);
@@ -303,8 +347,8 @@ int dyson_server_destroy(dyson_server s) {
 
 int dyson_submit(dyson_server s, const dyson_request* r, uint64_t* ticket) {
   if (!s || !r || !ticket) return srv_fail(DYSON_E_BAD_ARG, "NULL server, request or ticket");
-  if (r->K < 1 || r->K > r->geom.max_freqs)
-    return srv_fail(DYSON_E_BAD_ARG, "request K must be in 1..geom.max_freqs");
+  if (r->K < 1 || r->geom.max_freqs < 1)
+    return srv_fail(DYSON_E_BAD_ARG, "request K and geom.max_freqs must be >= 1");
   if (!r->omega || !r->V || !r->sigma || !r->q1 || !r->diagG)
     return srv_fail(DYSON_E_BAD_ARG, "request buffers must not be NULL");
   size_t need = 0;

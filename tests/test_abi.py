@@ -90,6 +90,14 @@ def test_wide_slices_within_limits(lib):
     assert e.value.code == -4 and "row buffer" in str(e.value)
     g.precision = D.DYSON_MIXED
     assert D.dyson_plan_footprint(g) > 0
+    # 48^3 with p = 8: W = 48 * 6 = 288, within the 320 limit; its complex64 row
+    # buffer (110 KB) leaves room for the ring, the FP64 one (221 KB) does not
+    g = D.make_geometry((48, 48, 48), p=8, k_max=64, max_freqs=1, precision=D.DYSON_MIXED)
+    assert D.dyson_plan_footprint(g) > 0
+    g.precision = D.DYSON_FP64
+    with pytest.raises(D.DysonError) as e:
+        D.dyson_plan_footprint(g)
+    assert e.value.code == -4 and "row buffer" in str(e.value)
 
 
 def test_real_axis_eta_validated(lib):

@@ -93,3 +93,60 @@ def test_oversized_request_is_rejected():
         D.dyson_submit(srv, geom, 4, omega, V, sigma, q1, np.zeros((4, w.N), complex))
     assert e.value.code == -5
     D.dyson_server_destroy(srv)
+
+
+@pytest.mark.parametrize("prec,tol", [(D.DYSON_FP64, 1e-10), (D.DYSON_MIXED, 1e-6)])
+def test_request_larger_than_plan_runs_in_chunks_and_matches_oracle(prec, tol):
+    """K = 7 frequencies on a plan holding 3: three consecutive chunks on one stream.
+    16^2 with p = 2 has m = 16 interface sites; with the cap at 24 the Krylov space closes and
+    the served diagonal is the oracle's low-rank diagonal, itself the exact one."""
+    from oracle import dyson_oracle as O
+    K, cap = 7, 3
+    w, omega, V, sigma, q1 = request_inputs((16, 16), 2, 24, K, 31)
+    srv = D.dyson_server_create(4 << 30, max_inflight=2)
+    geom = D.make_geometry(w.L, w.t, w.mu, 2, 24, prec, max_freqs=cap)
+    out = np.zeros((K, w.N), complex)
+    st = np.zeros(K, np.int32)
+    D.dyson_wait(srv, D.dyson_submit(srv, geom, K, omega, V, sigma, q1, out, st))
+    D.dyson_server_destroy(srv)
+    assert np.all(st & D.DYSON_ST_TERMINATED)
+    ref = alone(w, omega, V, sigma, q1, prec)
+    assert np.max(np.abs(out - ref) / np.abs(ref)) <= (1e-12 if prec == D.DYSON_FP64 else 1e-7)
+    for k in range(K):
+        lr = O.lowrank_diag(w.L, (False,) * 3, w.t, w.mu, V, sigma[k], omega[k], q1, 2, 24)
+        ex = O.exact_diag(w.L, (False,) * 3, w.t, O.dyson_diagonal(omega[k], w.mu, V, sigma[k]))
+        assert np.max(np.abs(lr - ex) / np.abs(ex)) <= 1e-10
+        assert np.max(np.abs(out[k] - lr) / np.abs(lr)) <= tol
+
+
+def test_small_request_backfills_past_one_waiting_for_memory():
+    """A large request that must wait for memory (the budget holds one large plan)
+    does not hold up a later small request whose plan is resident and idle: the
+    small one runs at once, while the large one waits for the running one."""
+    small, big_a, big_b = ((16, 16), 2, 8, 2), ((128, 128), 4, 32, 16), ((128, 96), 4, 32, 16)
+    need = {g: D.dyson_plan_footprint(D.make_geometry(g[0], p=g[1], k_max=g[2], max_freqs=g[3]))
+            for g in (small, big_a, big_b)}
+    assert need[big_b] > 2 * need[small]
+    srv = D.dyson_server_create(need[big_a] + 2 * need[small], max_inflight=4)
+
+    def submit(g, seed):
+        w, omega, V, sigma, q1 = request_inputs(g[0], g[1], g[2], g[3], seed)
+        geom = D.make_geometry(w.L, w.t, w.mu, g[1], g[2], D.DYSON_FP64, max_freqs=g[3])
+        out = np.zeros((g[3], w.N), complex)
+        return D.dyson_submit(srv, geom, g[3], omega, V, sigma, q1, out), (w, omega, V, sigma, q1, out)
+
+    # the host buffers of a request must stay alive until its dyson_wait returns
+    t0, keep0 = submit(small, 41)
+    D.dyson_wait(srv, t0)                       # the small plan is now resident and idle
+    ta, keep_a = submit(big_a, 42)
+    tb, keep_b = submit(big_b, 43)              # waits: big_a runs, the budget holds one large plan
+    ts, (w, omega, V, sigma, q1, out) = submit(small, 44)
+    lat_s, _ = D.dyson_wait(srv, ts)
+    lat_b, _ = D.dyson_wait(srv, tb)
+    D.dyson_wait(srv, ta)
+    del keep0, keep_a, keep_b
+    assert lat_s < lat_b
+    assert np.array_equal(out, alone(w, omega, V, sigma, q1, D.DYSON_FP64))
+    stats = D.dyson_server_stats(srv)
+    assert stats["completed"] == 4 and stats["peak_bytes"] <= need[big_a] + 2 * need[small]
+    D.dyson_server_destroy(srv)

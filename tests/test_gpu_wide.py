@@ -1,11 +1,13 @@
-"""Wide slices (3D slabs, slice width W = Ly * h in (64, 256]): the global-memory
+"""Wide slices (3D slabs, slice width W = Ly * h in (64, 320]): the global-memory
 factor kernel and the row-chunked sweeps, against the oracle through the C ABI.
 
 Geometries and the paths they take (FP64 / mixed):
   (6, 9, 16)  p = 2: W = 72   row chunks (FP64) / one chunk per block (complex64)
   (4, 16, 17) p = 2: W = 128  chunked / chunked
   (5, 12, 26) p = 2: W = 156  chunked, W not a multiple of the 32-wide tiles
-  (3, 16, 33) p = 2: W = 256  the widest slice taken
+  (3, 16, 33) p = 2: W = 256
+  (8, 24, 25), (48, 24, 25) p = 2: W = 288, the slice of 48^3 slabs with p = 8
+  (the second with 48 slices, where only the complex64 row buffer stays on chip)
 """
 import numpy as np
 import pytest
@@ -162,3 +164,40 @@ def test_square512_full_batch_sampled():
     assert rounding_bound(name, 0, TOL_MIXED) == TOL_MIXED
     for pl, _, _, _ in runs:
         pl.close()
+
+
+@pytest.mark.parametrize("L,precision,tol", [((8, 24, 25), D.DYSON_FP64, TOL_FP64),
+                                             ((48, 24, 25), D.DYSON_MIXED, TOL_MIXED)])
+def test_slice_width_288(L, precision, tol):
+    """W = 24 * 12 = 288 > 256: diag(B^-1), the subdomain solve, the X-matvec and a
+    truncated solve (checked step by step) against the oracle."""
+    w = wl(L, 2, 8, K=2, seed=8)
+    heights, _, _ = D.dyson_partition(D.make_geometry(L, p=2))
+    assert L[1] * max(heights) == 288
+    omega, V, sigma, q1 = I.make_inputs(w)
+    pl = plan_for(w, precision)
+    dB = np.zeros((2, w.N), complex)
+    D.dyson_subdomain_diag(pl.handle, 2, omega, V, sigma, dB)
+    rng = np.random.default_rng(12)
+    q = rng.normal(size=(2, w.N)) + 1j * rng.normal(size=(2, w.N))
+    wv = np.zeros_like(q)
+    u = np.zeros_like(q)
+    D.dyson_subdomain_solve(pl.handle, 2, omega, V, sigma, q, wv)
+    D.dyson_xmatvec(pl.handle, 2, omega, V, sigma, q, u)
+    sweep_tol, xm_tol = (1e-12, 1e-11) if precision == D.DYSON_FP64 else (1e-5, 1e-9)
+    for k in range(2):
+        subs = O.Subdomains(w.L, OPEN, w.t, O.dyson_diagonal(omega[k], w.mu, V, sigma[k]), 2)
+        mask = subs.diagB != 0
+        assert relerr(dB[k][mask], subs.diagB[mask]) < 1e-12      # FP64 recursion in both forms
+        ref = subs.solve(q[k])
+        assert np.max(np.abs(wv[k] - ref)) <= sweep_tol * np.max(np.abs(ref))
+        ref = O.xmatvec(w.L, OPEN, w.t, w.mu, V, sigma[k], omega[k], 2, q[k])
+        assert np.max(np.abs(u[k] - ref)) <= xm_tol * np.max(np.abs(ref))
+    st = np.zeros(w.K, np.int32)
+    out = pl.solve(omega, V, sigma, q1, status=st)
+    assert np.all((st & (D.DYSON_ST_NO_CONVERGENCE | D.DYSON_ST_BREAKDOWN)) == 0)
+    info = pl.info(w.K)
+    for k in range(w.K):
+        subs, X = oracle_parts(w, omega[k], V, sigma[k])
+        assert stepwise_check(w, pl, k, subs, X, q1, out[k], info, tol) == w.k
+    pl.close()
