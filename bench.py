@@ -417,6 +417,22 @@ def run_ours(a, rank, world, local_rank):
                 basis="achieved = algorithmic bytes (flops) of all X-matvec launches of a step / "
                       "the union of their intervals; traffic = ncu DRAM bytes of those launches per step")
     roof["share_of_step"] = float(xm_union_ms / ms_per_step) if ms_per_step > 0 else None
+    # the Lanczos step (row a7/a8): CGS2 reads the basis three times per step (g = Q^T u;
+    # r1 = u - Q g with h = Q^T r1 in the same pass; r = r1 - Q h), plus ~6 vectors
+    # (u three times, q_{j+1} written, the running diagonal read and written); complex128
+    # entries of 16 B per site.  A frequency that ran n steps moves sum_{j=1..n} (3 j + 6) N 16 B.
+    lz = kms[kinds == 4]
+    steps_k = np.asarray(info["steps"], dtype=np.float64)
+    lz_bytes = float(sum((3.0 * n * (n + 1) / 2 + 6.0 * n) * w.N * 16.0 for n in steps_k))
+    lz_union = union_ms(t0[kinds == 4], t1[kinds == 4])
+    lz_ach = lz_bytes / (lz_union / 1e3) / 1e9 if lz_union > 0 else float("nan")
+    roof_lz = dict(bound="hbm", achieved=lz_ach, peak=hbm_peak, unit="GB/s", frac=lz_ach / hbm_peak,
+                   traffic=recorded_traffic("k_lanczos", a.workload),
+                   kernel="k_lanczos_dd" if prec == D.DYSON_MIXED else "k_lanczos", peak_source=peak_src,
+                   per_step_algorithmic_bytes=lz_bytes, launches_per_step=int(len(lz)),
+                   union_ms_per_step=lz_union, mean_launch_ms=float(lz.mean()) if len(lz) else None,
+                   basis="three reads of the basis per Lanczos step (CGS2) + 6 vectors, "
+                         "complex128, over the union of the step's Lanczos launch intervals")
     phases = {D.KERNEL_NAMES[int(k)]: round(float(kms[kinds == k].sum()), 3) for k in sorted(set(kinds))}
     tuning = D.dyson_plan_tuning(plan.handle)
 
@@ -485,7 +501,7 @@ def run_ours(a, rank, world, local_rank):
                     l2="per-step working set > L2: factors + Lanczos basis ~1 GB, no flush",
                     parallelism=f"replicas x{world}"),
         latency_ms=dict(p50=pct(0.50), p99=pct(0.99)),
-        roofline=roof, phases_ms_last_step=phases, autotuner=tuning,
+        roofline=roof, roofline_lanczos=roof_lz, phases_ms_last_step=phases, autotuner=tuning,
         interface_iterations_per_xmatvec=float(np.mean(info["iters"]) / max(1, w.k)),
         status_flags=sorted({int(x) for x in status}),
         cpu_baseline=({k: v for k, v in cpu.items() if k != "wall_s"} if cpu else None),
@@ -621,6 +637,39 @@ def run_serving(a):
     return out
 
 
+def run_profile_case(a):
+    """A small case of a workload for ncu: its first --freqs frequencies in --groups
+    frequency groups; one solve (autotuning, graph capture), then one more solve between
+    cudaProfilerStart and cudaProfilerStop (profile with --profile-from-start off)."""
+    import numpy as np
+    import torch
+    from paper_1102_3137_gb300 import build as B
+    from paper_1102_3137_gb300 import dyson as D
+    from paper_1102_3137_gb300 import inputs as I
+    B.build()
+    D.load()
+    dev = torch.device("cuda", 0)
+    w = I.WORKLOADS[a.workload]
+    K = a.freqs or w.K
+    omega, V, sigma, q1 = I.make_inputs(w)
+    t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+    om, Vd, sg, qd = t(omega[:K]), t(V), t(sigma[:K]), t(q1)
+    prec = D.DYSON_MIXED if a.form == "mixed" else D.DYSON_FP64
+    plan = D.Plan(w.L, w.t, w.mu, w.p, w.k, prec, max_freqs=K, freq_groups=a.groups)
+    out = torch.zeros((K, w.N), dtype=torch.complex128, device=dev)
+    st = torch.zeros(K, dtype=torch.int32, device=dev)
+    ss = torch.cuda.current_stream(dev).cuda_stream
+    D.dyson_solve(plan.handle, K, om, Vd, sg, qd, out, st, ss)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    D.dyson_solve(plan.handle, K, om, Vd, sg, qd, out, st, ss)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    flags = sorted({int(x) for x in st.cpu().numpy()})
+    plan.close()
+    return dict(profile_case=a.workload, form=a.form, K=K, groups=a.groups, status_flags=flags)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -637,7 +686,14 @@ def main():
     ap.add_argument("--requests", type=int, default=48)
     ap.add_argument("--inflight", type=int, default=8)
     ap.add_argument("--rate-fracs", type=float, nargs="+", default=[0.5, 0.8, 0.95, 2.0, 4.0])
+    ap.add_argument("--profile-case", action="store_true",
+                    help="run a small case for ncu (--freqs, --groups) and print no bench line")
+    ap.add_argument("--freqs", type=int, default=0, help="--profile-case: first K frequencies (0: all)")
+    ap.add_argument("--groups", type=int, default=1, help="--profile-case: frequency groups")
     a = ap.parse_args()
+    if a.profile_case:
+        print(json.dumps(run_profile_case(a)), flush=True)
+        return
     if a.serving:
         print(json.dumps(run_serving(a)), flush=True)
         return
