@@ -81,8 +81,8 @@ def recorded_traffic(kernel, workload):
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             d = json.load(f)
-        e = d.get(kernel, {})
-        if e.get("workload") == workload and e.get("source_hash") == kernel_source_hash():
+        e = d.get(kernel, {}).get(workload, {})
+        if e.get("source_hash") == kernel_source_hash():
             return float(e["dram_bytes_per_step"])
     except Exception:
         pass

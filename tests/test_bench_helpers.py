@@ -18,10 +18,11 @@ def test_recorded_traffic_needs_matching_source():
     path = os.path.join(bench.ROOT, "profiles", "traffic.json")
     with open(path) as f:
         rec = json.load(f)
-    for kernel, e in rec.items():
-        assert e["dram_bytes_per_step"] > 0 and e["workload"]
-        got = bench.recorded_traffic(kernel, e["workload"])
-        # a record applies only while the kernels are the ones it was taken from
-        assert got is None or got == e["dram_bytes_per_step"]
-        assert (got is not None) == (e["source_hash"] == bench.kernel_source_hash())
+    for kernel, per_workload in rec.items():
+        for workload, e in per_workload.items():
+            assert e["dram_bytes_per_step"] > 0
+            got = bench.recorded_traffic(kernel, workload)
+            # a record applies only while the kernels are the ones it was taken from
+            assert got is None or got == e["dram_bytes_per_step"]
+            assert (got is not None) == (e["source_hash"] == bench.kernel_source_hash())
     assert bench.recorded_traffic("k_xmatvec<float>", "no such workload") is None
