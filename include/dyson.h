@@ -97,9 +97,10 @@ typedef struct {
   double krylov_tol;  /* relative residual of each interface solve; 0 = default
                          (1e-13 FP64, 1e-5 mixed inner solves) */
   int krylov_maxit;   /* iteration cap of each interface solve; 0 = default (1000) */
-  double refine_tol;  /* mixed form: relative FP64 residual after refinement; 0 = 1e-15
-                         (refinement also stops once a pass no longer shrinks the residual
-                         4-fold: the FP64 rounding floor) */
+  double refine_tol;  /* mixed form: relative FP64 residual after refinement; 0 = 1e-13,
+                         the FP64 form's own interface tolerance (refinement also stops
+                         once a pass no longer shrinks the residual 4-fold: the FP64
+                         rounding floor) */
   int refine_max;     /* mixed form: most refinement passes per solve; 0 = default (6) */
   int max_freqs;      /* most frequencies one dyson_solve call may carry (>= 1) */
   double eta;         /* frequency axis.  0: Matsubara, H_ii = i w_k + mu - V_i - Sigma_i

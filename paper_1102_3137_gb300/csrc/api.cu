@@ -111,7 +111,7 @@ int build_part(const dyson_geometry* in, Part* out, bool gpu) {
   g.real_axis = in->eta > 0.0 ? 1 : 0;
   g.krylov_tol = in->krylov_tol > 0 ? in->krylov_tol : (mixed ? 1e-5 : 1e-13);
   g.krylov_maxit = in->krylov_maxit > 0 ? in->krylov_maxit : 1000;
-  g.refine_tol = in->refine_tol > 0 ? in->refine_tol : 1e-15;
+  g.refine_tol = in->refine_tol > 0 ? in->refine_tol : 1e-13;   // the FP64 form's krylov_tol
   g.refine_max = in->refine_max > 0 ? in->refine_max : 6;
   if (in->freq_groups < 0) return fail(DYSON_E_BAD_ARG, "freq_groups must be >= 0 (0: default)");
   if (in->max_freqs < 1 || (long long)in->max_freqs * g.nb > 65535)
@@ -136,7 +136,7 @@ int build_part(const dyson_geometry* in, Part* out, bool gpu) {
 enum {
   B_V, B_OMEGA, B_SIGMA, B_Q1, B_DD2NAT, B_G, B_G64, B_DIAGB, B_Q, B_ACC, B_U, B_V1, B_V2, B_V3,
   B_YSCR, B_BND, B_IFV, B_PRE, B_LAN, B_MAXT, B_ST, B_OUT, B_STATUS, B_SWEEPS, B_FWORK, B_OFFB, B_OFF2,
-  B_LPT, B_LPM, B_LPG, B_LPV, B_COUNT
+  B_LPT, B_LPM, B_LPG, B_LPV, B_HDIAG, B_COUNT
 };
 
 size_t layout(const Geo& g, int K, bool mixed, size_t off[B_COUNT]) {
@@ -176,6 +176,7 @@ size_t layout(const Geo& g, int K, bool mixed, size_t off[B_COUNT]) {
   sz[B_LPM] = g.lpre ? Kz * (g.p - 1) * Lx2 * cs : 0;
   sz[B_LPG] = g.lpre ? Kz * g.p * nsub * g.W * sizeof(cxf) : 0;
   sz[B_LPV] = (g.lpre && g.Lx > DY_LPRE_MAXLX) ? Kz * g.p * 2 * (size_t)g.Lx * g.W * sizeof(cxf) : 0;
+  sz[B_HDIAG] = mixed ? Kz * Ndd * sizeof(cxd) : 0;
   size_t o = 0;
   for (int k = 0; k < B_COUNT; ++k) {
     off[k] = o;
@@ -349,6 +350,7 @@ Bufs sub_bufs(const Geo& g, const Bufs& b, bool mixed, int k0) {
   s.g = adv(reinterpret_cast<char*>(b.g), K0 * g.p * nsub * g.W * cs);
   s.g64 = b.g64 ? b.g64 + K0 * g.p * nsub * g.W : nullptr;
   s.diagB = b.diagB + K0 * Ndd;
+  s.hdiag = b.hdiag ? b.hdiag + K0 * Ndd : nullptr;
   s.offB = b.offB ? b.offB + K0 * g.p * nsub : nullptr;
   s.off2 = b.off2 ? b.off2 + K0 * g.p * nsub : nullptr;
   s.Q = b.Q + K0 * (g.k_max + g.nb) * Ndd;
@@ -584,6 +586,7 @@ int dyson_plan_create(const dyson_geometry* geom, dyson_plan* out) {
   b.g = at<void>(p, B_G);
   b.g64 = p->mixed ? at<cxd>(p, B_G64) : nullptr;
   b.diagB = at<cxd>(p, B_DIAGB);
+  b.hdiag = p->mixed ? at<cxd>(p, B_HDIAG) : nullptr;
   b.Q = at<cxd>(p, B_Q);
   b.acc = at<cxd>(p, B_ACC);
   b.u = at<cxd>(p, B_U);

@@ -208,6 +208,7 @@ struct Bufs {
   void* g;              // [K][p][Lx][W][W] slice factors g_s read by the sweeps (precision of the form)
   cxd* g64;             // [K][p][Lx][W][W] FP64 g_s kept for the mixed form's FP64 recursion
   cxd* diagB;           // [K][Ndd] diag(B^-1), zero on the interface
+  cxd* hdiag;           // [K][Ndd] H_ii (Eq. 1) in DD layout, zero on padding (mixed form), or null
   cxd* offB;            // [K][p][Lx][W] diag of G_{s,s+1} (B_i^-1 between slices s, s+1), or null
   cxd* off2;            // [K][p][Lx][W] diag of G_{s,s+2} on the boundary rows (2D strips), or null
   cxd* Q;               // [K][k_max+nb][Ndd] Lanczos vectors (column j*nb + c of block j)

@@ -455,8 +455,25 @@ __global__ void __launch_bounds__(DY_THREADS) k_precond(Geo g, Bufs b) {
 
 }  // namespace
 
+// H_ii (Eq. 1) of every DD slot, zero on padding: the mixed form's FP64
+// residuals read it coalesced instead of gathering V and Sigma in natural order.
+__global__ void __launch_bounds__(DY_THREADS) k_hdiag(Geo g, Bufs b) {
+  const int kf = blockIdx.y;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < (size_t)g.Ndd;
+       k += (size_t)gridDim.x * blockDim.x) {
+    const int nat = b.dd2nat[k];
+    b.hdiag[(size_t)kf * g.Ndd + k] = nat >= 0 ? dyson_diag(g, b, kf, nat) : cxd{0, 0};
+  }
+}
+
 template <typename R, typename S>
 cudaError_t launch_factor(const Geo& g, const Bufs& b, int K, cudaStream_t st) {
+  if (b.hdiag) {
+    const size_t blocks = ((size_t)g.Ndd + DY_THREADS - 1) / DY_THREADS;
+    k_hdiag<<<dim3((unsigned)(blocks < 1024 ? blocks : 1024), K), DY_THREADS, 0, st>>>(g, b);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   if (g.W > DY_MAXW_SMEM) {
     // wide slices: FP64 recursion in global memory (both forms recurse in FP64)
     if (sizeof(R) != sizeof(double) || g.W > DY_MAXW || !b.fwork) return cudaErrorInvalidValue;

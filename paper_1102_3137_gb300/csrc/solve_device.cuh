@@ -253,6 +253,28 @@ __device__ __forceinline__ void sweep_prepass(const Geo& g, int i, const SweepAr
   const double as = fabs(a.in_scale);
   const bool fast = sizeof(R) == 4 && as > 1e-30 && as < 1e30;
   const R scf = (R)a.in_scale;
+  if constexpr (sizeof(R) == 4) {
+    if (a.src && fast) {                 // the common case: PU rows' loads in flight per thread
+      constexpr int PU = 4;
+      const int nt = (int)blockDim.x;
+      for (int e0 = threadIdx.x; e0 < nrow; e0 += PU * nt) {
+        cxd v[PU];
+        bool on[PU];
+#pragma unroll
+        for (int u = 0; u < PU; ++u) {
+          const int e = e0 + u * nt, j = e % W;
+          on[u] = e < nrow && j < w;
+          v[u] = on[u] ? a.src[e] : cxd{0, 0};
+        }
+#pragma unroll
+        for (int u = 0; u < PU; ++u) {
+          const int e = e0 + u * nt;
+          if (e < nrow) yb[e] = on[u] ? scf * c2f_bits(v[u]) : cx<R>{0, 0};
+        }
+      }
+      return;
+    }
+  }
   for (int e = threadIdx.x; e < nrow; e += (int)blockDim.x) {
     const int s = e / W, j = e - s * W;
     cxd v = {0, 0};
@@ -286,6 +308,39 @@ __device__ __forceinline__ void sweep_postpass(const Geo& g, int i, const SweepA
   const double os = fabs(a.out_scale);
   const bool fast = sizeof(R) == 4 && os > 1e-30 && os < 1e30;
   const R scf = (R)a.out_scale;
+  if constexpr (sizeof(R) == 4) {
+    if (a.dst && fast) {                 // the common case: PU rows' loads in flight per thread
+      constexpr int PU = 4;
+      const int nt = (int)blockDim.x;
+      const bool rd = a.dst_op == 1 || a.dst_op == 2;
+      for (int e0 = threadIdx.x; e0 < nrow; e0 += PU * nt) {
+        cx<R> xr[PU];
+        cxd dv[PU];
+        bool on[PU];
+#pragma unroll
+        for (int u = 0; u < PU; ++u) {
+          const int e = e0 + u * nt, j = e % W;
+          on[u] = e < nrow && j < w;
+          xr[u] = on[u] ? yb[e] : cx<R>{0, 0};
+          dv[u] = (on[u] && rd) ? a.dst[e] : cxd{0, 0};
+        }
+#pragma unroll
+        for (int u = 0; u < PU; ++u) {
+          if (!on[u]) continue;
+          const int e = e0 + u * nt, s = e / W, j = e - s * W;
+          const cxd xd = c2d_bits(scf * xr[u]);
+          cxd* d = a.dst + e;
+          if (a.dst_op == 0) *d = xd;
+          else if (a.dst_op == 1) *d = dv[u] + xd;
+          else if (a.dst_op == 2) *d = dv[u] - xd;
+          else *d = -xd;
+          if (a.bnd_lo && j < T) a.bnd_lo[s + Lx * j] = xr[u];
+          if (a.bnd_hi && j >= w - T) a.bnd_hi[s + Lx * (j - (w - T))] = xr[u];
+        }
+      }
+      return;
+    }
+  }
   for (int e = threadIdx.x; e < nrow; e += (int)blockDim.x) {
     const int s = e / W, j = e - s * W;
     if (j >= w) continue;
@@ -1244,57 +1299,80 @@ __device__ void layer_diag(const Geo& g, const Bufs& b, int vs, int i) {
   if (i >= g.p - 1) return;
   cx<R>* dC = ifv_ptr<R>(g, b, vs, IF_D) + (size_t)i * g.A;
   const int f = slot_freq(g, vs);
+  const cxd* hd = b.hdiag ? b.hdiag + (size_t)f * g.Ndd + g.ifc_off + (size_t)i * g.A : nullptr;
   for (int a = threadIdx.x; a < g.A; a += (int)blockDim.x)
-    dC[a] = cconv<R>(dyson_diag(g, b, f, a + g.A * g.ylayer[i]));
+    dC[a] = cconv<R>(hd ? hd[a] : dyson_diag(g, b, f, a + g.A * g.ylayer[i]));
 }
 
 // res = rhs - H x (mode 0: full H; mode 1: B only, no interface coupling),
 // FP64, on this CTA's entries.  Returns partials (||res||^2, ||rhs||^2).
-__device__ void residual_H(const Geo& g, const Bufs& b, int vs, int i, const cxd* rhs,
-                           const cxd* x, cxd* res, int mode, double* rn, double* qn) {
+// H_ii comes from the per-solve DD-layout copy (coalesced); each thread takes
+// RU sites per pass and issues all their loads before any arithmetic, so the
+// loads of a pass are in flight together.
+__device__ __noinline__ void residual_H(const Geo& g, const Bufs& b, int vs, int i, const cxd* rhs,
+                                        const cxd* x, cxd* res, int mode, double* rn, double* qn) {
+  constexpr int RU = 4;
   const int W = g.W, Lx = g.Lx, T = g.T, h = g.h[i], w = T * h, A = g.A;
-  const size_t nsub = (size_t)Lx * W;
-  const cxd* xs = x + i * nsub;
+  const int nsub = Lx * W, nt = (int)blockDim.x;
+  const cxd* xs = x + (size_t)i * nsub;
+  const cxd* rs_ = rhs + (size_t)i * nsub;
+  cxd* ro = res + (size_t)i * nsub;
   const double t = g.t;
   const int f = slot_freq(g, vs);
+  const cxd* hd = b.hdiag + (size_t)f * g.Ndd;
+  const cxd* hs = hd + (size_t)i * nsub;
+  const cxd* xlo = (mode == 0 && i > 0) ? x + g.ifc_off + (size_t)(i - 1) * A : nullptr;
+  const cxd* xhi = (mode == 0 && i < g.p - 1) ? x + g.ifc_off + (size_t)i * A : nullptr;
   double sr = 0, sq = 0;
-  for (int e = threadIdx.x; e < (int)nsub; e += (int)blockDim.x) {
-    const int s = e / W, j = e - s * W;
-    if (j >= w) continue;
-    const int tr = j % T, sl = j / T;
-    cxd d = dyson_diag(g, b, f, sub_nat(g, i, s, j));
-    cxd nb = {0, 0};
-    if (s > 0) nb = nb + xs[e - W];
-    if (s < Lx - 1) nb = nb + xs[e + W];
-    if (tr > 0) nb = nb + xs[e - 1];
-    if (tr < T - 1) nb = nb + xs[e + 1];
-    if (sl > 0) nb = nb + xs[e - T];
-    if (sl < h - 1) nb = nb + xs[e + T];
-    if (mode == 0) {
-      if (sl == 0 && i > 0) nb = nb + x[g.ifc_off + (size_t)(i - 1) * A + s + Lx * tr];
-      if (sl == h - 1 && i < g.p - 1) nb = nb + x[g.ifc_off + (size_t)i * A + s + Lx * tr];
+  for (int e0 = threadIdx.x; e0 < nsub; e0 += RU * nt) {
+    cxd d[RU], xv[RU], nb[RU], q[RU];
+    bool on[RU];
+#pragma unroll
+    for (int u = 0; u < RU; ++u) {
+      const int e = e0 + u * nt;
+      const int s = e / W, j = e - s * W;
+      on[u] = e < nsub && j < w;
+      d[u] = xv[u] = nb[u] = q[u] = cxd{0, 0};
+      if (on[u]) {
+        const int tr = j % T, sl = j / T;
+        d[u] = hs[e];
+        xv[u] = xs[e];
+        q[u] = rs_[e];
+        cxd n = {0, 0};
+        if (s > 0) n = n + xs[e - W];
+        if (s < Lx - 1) n = n + xs[e + W];
+        if (tr > 0) n = n + xs[e - 1];
+        if (tr < T - 1) n = n + xs[e + 1];
+        if (sl > 0) n = n + xs[e - T];
+        if (sl < h - 1) n = n + xs[e + T];
+        if (sl == 0 && xlo) n = n + xlo[s + Lx * tr];
+        if (sl == h - 1 && xhi) n = n + xhi[s + Lx * tr];
+        nb[u] = n;
+      }
     }
-    cxd hv = d * xs[e] + t * nb;
-    cxd q = rhs[i * nsub + e];
-    cxd rr = q - hv;
-    res[i * nsub + e] = rr;
-    sr += cabs2(rr);
-    sq += cabs2(q);
+#pragma unroll
+    for (int u = 0; u < RU; ++u) {
+      if (!on[u]) continue;
+      const cxd rr = q[u] - (d[u] * xv[u] + t * nb[u]);
+      ro[e0 + u * nt] = rr;
+      sr += cabs2(rr);
+      sq += cabs2(q[u]);
+    }
   }
   if (mode == 0 && i < g.p - 1) {
     const size_t o = g.ifc_off + (size_t)i * A;
     const cxd* xl = x + o;
-    const cxd* xb = x + i * nsub;           // subdomain i: its top row touches layer i
-    const cxd* xa = x + (i + 1) * nsub;     // subdomain i+1: its bottom row touches layer i
+    const cxd* xb = x + (size_t)i * nsub;         // subdomain i: its top row touches layer i
+    const cxd* xa = x + (size_t)(i + 1) * nsub;   // subdomain i+1: its bottom row touches layer i
     const int hi = T * (g.h[i] - 1);
-    for (int a = threadIdx.x; a < A; a += (int)blockDim.x) {
+    for (int a = threadIdx.x; a < A; a += nt) {
       const int xx = a % Lx, tr = a / Lx;
       cxd nb = {0, 0};
       if (xx > 0) nb = nb + xl[a - 1];
       if (xx < Lx - 1) nb = nb + xl[a + 1];
       if (tr > 0) nb = nb + xl[a - Lx];
       if (tr < T - 1) nb = nb + xl[a + Lx];
-      cxd hv = dyson_diag(g, b, f, a + A * g.ylayer[i]) * xl[a] + t * nb;
+      cxd hv = hd[o + a] * xl[a] + t * nb;
       hv = hv + t * (xb[(size_t)xx * W + hi + tr] + xa[(size_t)xx * W + tr]);
       cxd q = rhs[o + a];
       cxd rr = q - hv;

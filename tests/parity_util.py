@@ -10,7 +10,7 @@ TOL_FP64 = 1e-10
 TOL_MIXED = 1e-6
 OPEN = (False, False, False)
 # Relative accuracy of an X-matvec of either GPU form: the FP64 form's interface
-# solves stop at a relative residual of 1e-13; the mixed form refines in FP64 below it.
+# solves stop at a relative residual of 1e-13; the mixed form refines in FP64 to it.
 EPS_XMATVEC = 1e-13
 
 
