@@ -351,8 +351,10 @@ int dyson_work_counters(dyson_plan plan, int K, unsigned long long* sweeps);
  * checking the run step by step: Q complex[nvec][N] (host) receives q_1 ..
  * q_nvec in natural order (bilinear-normalised, Sec. 2.1), nvec <= k_max+nb
  * (block plans: column j*nb + c is column c of block j; deflated columns are 0);
- * vectors past the last step taken are left over from earlier work.  Waits for
- * the device; allocates a temporary device buffer.
+ * vectors past the last step taken are left over from earlier work.  The mixed
+ * form with nb = 1 and k_max <= 64 keeps its basis as double-floats (47
+ * significant bits per real part); those values are widened exactly here.
+ * Waits for the device; allocates a temporary device buffer.
  */
 int dyson_lanczos_basis(dyson_plan plan, int k, int nvec, double* Q);
 

@@ -91,6 +91,7 @@ int build_part(const dyson_geometry* in, Part* out, bool gpu) {
   g.k_max = in->k_max;
   if (g.k_max < 1 || g.k_max > 256) return fail(DYSON_E_BAD_ARG, "k_max must be in 1..256");
   g.nb = in->block_size > 1 ? in->block_size : 1;
+  g.qsplit = (in->precision == DYSON_MIXED && g.nb == 1 && g.k_max <= 64) ? 1 : 0;
   if (in->block_size < 0 || g.nb > DY_MAXNB)
     return fail(DYSON_E_BAD_ARG, "block_size must be in 0.." + std::to_string(DY_MAXNB));
   if (g.nb > 1 && (g.k_max % g.nb || g.k_max * g.nb > DY_BLOCK_H))
@@ -833,6 +834,15 @@ int dyson_lanczos_basis(dyson_plan p, int k, int nvec, double* Q) {
   if (e == cudaSuccess) e = cudaMemcpy(Q, tmp, bytes, cudaMemcpyDeviceToHost);
   cudaFree(tmp);
   if (e != cudaSuccess) return fail(DYSON_E_CUDA, std::string("basis copy: ") + cudaGetErrorString(e));
+  if (g.qsplit) {                          // double-float entries {re.hi, re.lo, im.hi, im.lo}: widen
+    const size_t n = (size_t)nvec * g.N;
+    for (size_t e2 = 0; e2 < n; ++e2) {
+      float f[4];
+      std::memcpy(f, Q + 2 * e2, sizeof(f));
+      Q[2 * e2] = (double)f[0] + (double)f[1];
+      Q[2 * e2 + 1] = (double)f[2] + (double)f[3];
+    }
+  }
   return DYSON_OK;
 }
 
@@ -988,6 +998,7 @@ int dyson_xmatvec(dyson_plan p, int K, const double* omega, const double* V, con
   else LK(launch_precond<double>(g, p->b, K, s));
   // one vector per frequency: column 0 of block 0, result in the frequency's first slot
   LK(launch_gather(g, p->b, K, qn, p->b.Q, (size_t)(g.k_max + g.nb) * g.Ndd, s));
+  LK(launch_qsplit(g, p->b, K, s));
   CK(cudaMemsetAsync(p->b.st, 0, (size_t)K * ST_N * sizeof(int), s));
   if (g.p > 1) {
     if (p->mixed) LK(launch_xmatvec<float>(g, p->b, K, 0, 1, 1, s));

@@ -158,6 +158,16 @@ __device__ __forceinline__ dfl d2dfl_bits(double d) {
 // double-float -> binary64: both parts widened exactly, one binary64 add
 __device__ __forceinline__ double dfl2d_bits(dfl v) { return f2d_bits(v.hi) + f2d_bits(v.lo); }
 
+// A complex number as two double-floats {re.hi, re.lo, im.hi, im.lo}: 16 bytes, the
+// size of the binary64 complex it stands for (47 significant bits per part).  The
+// mixed form keeps its Lanczos basis in this form, so the Lanczos step's dot
+// products and updates read it without splitting.
+struct cdfl {
+  dfl x, y;
+};
+__device__ __forceinline__ cdfl csplit(cxd a) { return {d2dfl_bits(a.x), d2dfl_bits(a.y)}; }
+__device__ __forceinline__ cxd cwiden(const cdfl& a) { return {dfl2d_bits(a.x), dfl2d_bits(a.y)}; }
+
 __device__ __forceinline__ cxf c2f_bits(cxd a) { return {d2f_bits(a.x), d2f_bits(a.y)}; }
 __device__ __forceinline__ cxd c2d_bits(cxf a) { return {f2d_bits(a.x), f2d_bits(a.y)}; }
 
@@ -191,6 +201,8 @@ struct Geo {
   int lpre;            // interface preconditioner: 1 exact layer blocks of S (2D strips), 0 banded
   int xm_nt;           // threads per X-matvec CTA in the complex64 two-chain form (128: four CTAs
                        // per SM; 0 or 256: two), chosen by the heuristic or the autotuner
+  int qsplit;          // the Lanczos basis is stored as double-floats (cdfl; mixed form, nb = 1,
+                       // k_max <= 64, where the double-float Lanczos step runs)
 };
 
 // Work slots: the X-matvec runs one cluster per (frequency f, block column c),
@@ -316,6 +328,7 @@ cudaError_t launch_gather(const Geo& g, const Bufs& b, int K, const cxd* nat, cx
                           size_t dd_stride, cudaStream_t st);
 cudaError_t launch_scatter(const Geo& g, const Bufs& b, int K, const cxd* dd, cxd* nat,
                            size_t dd_stride, cudaStream_t st);
+cudaError_t launch_qsplit(const Geo& g, const Bufs& b, int K, cudaStream_t st);
 cudaError_t launch_status(const Geo& g, const Bufs& b, int K, int* status, cudaStream_t st);
 cudaError_t launch_wait_selftest(unsigned long long limit_ns, int* out, cudaStream_t st);
 cudaError_t launch_lanczos_dd(const Geo& g, const Bufs& b, int K, int j, cudaStream_t st);

@@ -2,17 +2,19 @@
 // CGS2 re-orthogonalisation, Eq. 9 assembly) with its dot products and
 // basis updates in double-float arithmetic on the FP32 pipe.
 //
-// The basis Q, the X-matvec output u, the running diagonal and every scalar
-// of T stay in binary64 in memory.  What moves off the binary64 pipe (GB300
-// issues binary32 FMAs at ~64x its binary64 rate) is the arithmetic of the
-// three passes over Q: each binary64 entry is split into a double-float
-// (47 significant bits, by integer operations) and the products are
-// accumulated with TwoProduct/TwoSum (~2^-47 relative per operation).
+// The basis Q is stored as double-floats (cdfl: hi + lo binary32 per real
+// part, 47 significant bits, 16 bytes per complex entry like binary64), so the
+// passes over it read the split form directly; the X-matvec output u, the
+// running diagonal and every scalar of T stay in binary64.  What moves off the
+// binary64 pipe (GB300 issues binary32 FMAs at ~64x its binary64 rate) is the
+// arithmetic of the three passes over Q: products accumulated with
+// TwoProduct/TwoSum (~2^-47 relative per operation); u is split by integer
+// operations where it is read.
 //
 // Classical Gram-Schmidt twice, with the three-term part folded in:
 //   pass A:  g  = Q_j^T u                     (alpha_j = g_j)
 //   pass B:  r1 = u - Q_j g,   h = Q_j^T r1   (r1 kept per tile only)
-//   pass C:  r  = u - Q_j (g + h)             (written as binary64)
+//   pass C:  r  = u - Q_j (g + h)             (formed in binary64, stored split)
 // In exact arithmetic r1 = u - alpha_j q_j - beta_j q_{j-1} - Q_j h1 with
 // h1 = Q_j^T (u - alpha_j q_j - beta_j q_{j-1}) = g - alpha_j e_j - beta_j e_{j-1},
 // i.e. the first Gram-Schmidt pass of the recurrence's residual; pass C is
@@ -43,12 +45,6 @@ static_assert(DY_THREADS == 2 * TG, "two threads per site of a group");
 constexpr double TERM_TOL_DD = 64.0 * TERM_TOL;
 constexpr double BRK_TOL_DD = 64.0 * BRK_TOL;
 
-struct cdfl {
-  dfl x, y;
-};
-
-__device__ __forceinline__ cdfl csplit(cxd a) { return {d2dfl_bits(a.x), d2dfl_bits(a.y)}; }
-__device__ __forceinline__ cxd cwiden(const cdfl& a) { return {dfl2d_bits(a.x), dfl2d_bits(a.y)}; }
 __device__ __forceinline__ cdfl czero() { return {dfl(0.f, 0.f), dfl(0.f, 0.f)}; }
 
 // acc + a*b for double-floats: the product's hi part and its exact error
@@ -127,21 +123,21 @@ __device__ __forceinline__ void put_partials(LanDDSmem& sm, int vphase, int j, c
 // sum over l = l0, l0 + dl, ... <= j of Q_l[k] c_l (double-float): the entries of
 // eight vectors are loaded before any is used (eight loads in flight per
 // thread), then summed in two interleaved chains
-__device__ __forceinline__ cdfl basis_sum(const cxd* Q, size_t Ndd, size_t k, int j, int l0, int dl,
+__device__ __forceinline__ cdfl basis_sum(const cdfl* Q, size_t Ndd, size_t k, int j, int l0, int dl,
                                           const cdfl* coef) {
   cdfl s0 = czero(), s1 = czero();
   for (int lb = l0; lb <= j; lb += 8 * dl) {
-    cxd qv[8];
+    cdfl qv[8];
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
       const int l = lb + m * dl;
-      qv[m] = l <= j ? Q[(size_t)l * Ndd + k] : cxd{0, 0};
+      qv[m] = l <= j ? Q[(size_t)l * Ndd + k] : czero();
     }
 #pragma unroll
     for (int m = 0; m < 8; m += 2) {
       const int l = lb + m * dl;
-      if (l <= j) cmac(s0, csplit(qv[m]), coef[l]);
-      if (l + dl <= j) cmac(s1, csplit(qv[m + 1]), coef[l + dl]);
+      if (l <= j) cmac(s0, qv[m], coef[l]);
+      if (l + dl <= j) cmac(s1, qv[m + 1], coef[l + dl]);
     }
   }
   return cadd(cnorm(s0), cnorm(s1));
@@ -160,10 +156,11 @@ __global__ void __launch_bounds__(DY_THREADS, 2) k_lanczos_dd(Geo g, Bufs b, int
   const size_t Ndd = g.Ndd;
   const int nsub = g.Lx * g.W, n = own_count(g, i);
   const int ngrp = (n + TG - 1) / TG;
-  const cxd* Q = b.Q + (size_t)kf * (g.k_max + g.nb) * Ndd;
-  const cxd* qj = Q + (size_t)j * Ndd;
-  const cxd* qm = (j > 0) ? Q + (size_t)(j - 1) * Ndd : nullptr;
-  cxd* r = b.Q + (size_t)kf * (g.k_max + g.nb) * Ndd + (size_t)(j + 1) * Ndd;
+  // the basis is stored as double-floats (Geo::qsplit)
+  cdfl* Q = reinterpret_cast<cdfl*>(b.Q + (size_t)kf * (g.k_max + g.nb) * Ndd);
+  const cdfl* qj = Q + (size_t)j * Ndd;
+  const cdfl* qm = (j > 0) ? Q + (size_t)(j - 1) * Ndd : nullptr;
+  cdfl* r = Q + (size_t)(j + 1) * Ndd;
   const cxd* u = b.u + (size_t)kf * Ndd;
   cxd* acc = b.acc + (size_t)kf * Ndd;
   cxd* lan = b.lan + (size_t)kf * (g.k_max + g.nb) * 2;
@@ -188,15 +185,15 @@ __global__ void __launch_bounds__(DY_THREADS, 2) k_lanczos_dd(Geo g, Bufs b, int
         if (e >= n) break;
         const size_t k = own_idx(g, i, e, nsub);
         const cdfl ud = sm.st[0][c];
-        cxd qv[LPW];
+        cdfl qv[LPW];
 #pragma unroll
         for (int m = 0; m < LPW; ++m) {
           const int l = w + DY_WARPS * m;
-          qv[m] = l <= j ? Q[(size_t)l * Ndd + k] : cxd{0, 0};
+          qv[m] = l <= j ? Q[(size_t)l * Ndd + k] : czero();
         }
 #pragma unroll
         for (int m = 0; m < LPW; ++m)
-          if (w + DY_WARPS * m <= j) cmac(a[m], csplit(qv[m]), ud);
+          if (w + DY_WARPS * m <= j) cmac(a[m], qv[m], ud);
       }
       __syncthreads();
     }
@@ -229,16 +226,16 @@ __global__ void __launch_bounds__(DY_THREADS, 2) k_lanczos_dd(Geo g, Bufs b, int
         const int e = e0 + c;
         if (e >= n) break;
         const size_t k = own_idx(g, i, e, nsub);
-        cxd qv[LPW];
+        cdfl qv[LPW];
 #pragma unroll
         for (int m = 0; m < LPW; ++m) {
           const int l = w + DY_WARPS * m;
-          qv[m] = l <= j ? Q[(size_t)l * Ndd + k] : cxd{0, 0};
+          qv[m] = l <= j ? Q[(size_t)l * Ndd + k] : czero();
         }
         const cdfl r1 = csub(csub(csplit(u[k]), sm.st[0][c]), sm.st[1][c]);
 #pragma unroll
         for (int m = 0; m < LPW; ++m)
-          if (w + DY_WARPS * m <= j) cmac(a[m], csplit(qv[m]), r1);
+          if (w + DY_WARPS * m <= j) cmac(a[m], qv[m], r1);
       }
       __syncthreads();
     }
@@ -262,16 +259,16 @@ __global__ void __launch_bounds__(DY_THREADS, 2) k_lanczos_dd(Geo g, Bufs b, int
       const cxd uv = u[k];
       const cxd rv = {(uv.x - f2d_bits(tot.x.hi)) - f2d_bits(tot.x.lo),
                       (uv.y - f2d_bits(tot.y.hi)) - f2d_bits(tot.y.lo)};
-      r[k] = rv;
+      r[k] = csplit(rv);
       v2[0] = cfma(rv, rv, v2[0]);
       v2[1].x += cabs2(rv);
-      const cdfl qjd = csplit(qj[k]);
+      const cdfl qjd = qj[k];
       cdfl sq = czero(), d = czero();
       cmac(sq, qjd, qjd);
       cmac(d, ad, cnorm(sq));
       if (qm) {
         cdfl pr = czero();
-        cmac(pr, csplit(qm[k]), qjd);
+        cmac(pr, qm[k], qjd);
         cmac(d, bd, cnorm(pr));
       }
       d = cnorm(d);
@@ -295,15 +292,15 @@ __global__ void __launch_bounds__(DY_THREADS, 2) k_lanczos_dd(Geo g, Bufs b, int
     flag = 2;
   }
   if (!done) {
-    // q_{j+1} = r / beta in double-float, written back in binary64
+    // q_{j+1} = r / beta in double-float
     const cdfl ib = csplit(cinv(beta));
     for (int gr = part + half * SPLIT; gr < ngrp; gr += 2 * SPLIT) {
       const int e = gr * TG + c0;
       if (e < n) {
         const size_t k = own_idx(g, i, e, nsub);
         cdfl q = czero();
-        cmac(q, csplit(r[k]), ib);
-        r[k] = cwiden(cnorm(q));
+        cmac(q, r[k], ib);
+        r[k] = cnorm(q);
       }
     }
   }

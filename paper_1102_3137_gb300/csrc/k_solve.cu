@@ -140,7 +140,9 @@ __global__ void __launch_bounds__(DY_THREADS) k_init(Geo g, Bufs b) {
   const cxd inv = cinv(csqrt_principal(v1[0]));
   for (int e = threadIdx.x; e < n; e += DY_THREADS) {
     size_t k = own_idx(g, i, e, nsub);
-    q[k] = q[k] * inv;
+    const cxd v = q[k] * inv;
+    if (g.qsplit) reinterpret_cast<cdfl*>(q)[k] = csplit(v);   // basis stored as double-floats
+    else q[k] = v;
   }
   if (threadIdx.x == 0 && b.sweeps) b.sweeps[(size_t)kf * g.p + i] = 0;
   if (i == 0 && threadIdx.x == 0) {
@@ -261,6 +263,24 @@ cudaError_t launch_gather(const Geo& g, const Bufs& b, int K, const cxd* nat, cx
 cudaError_t launch_scatter(const Geo& g, const Bufs& b, int K, const cxd* dd, cxd* nat,
                            size_t dd_stride, cudaStream_t st) {
   k_scatter<<<flat_grid(g, K), DY_THREADS, 0, st>>>(g, b.dd2nat, dd, nat, dd_stride);
+  return cudaGetLastError();
+}
+
+// Vector 0 of each frequency's basis, written in binary64 (dyson_xmatvec's
+// caller vector), rewritten in place as double-floats when the basis is split.
+__global__ void k_qsplit(Geo g, Bufs b) {
+  const int kf = blockIdx.y;
+  cxd* q = b.Q + (size_t)kf * (g.k_max + g.nb) * g.Ndd;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < (size_t)g.Ndd;
+       k += (size_t)gridDim.x * blockDim.x) {
+    const cxd v = q[k];
+    reinterpret_cast<cdfl*>(q)[k] = csplit(v);
+  }
+}
+
+cudaError_t launch_qsplit(const Geo& g, const Bufs& b, int K, cudaStream_t st) {
+  if (!g.qsplit) return cudaSuccess;
+  k_qsplit<<<flat_grid(g, K), DY_THREADS, 0, st>>>(g, b);
   return cudaGetLastError();
 }
 

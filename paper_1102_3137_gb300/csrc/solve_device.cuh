@@ -1606,6 +1606,18 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 4 : 2) k_xmatvec(Geo g, Bufs b
   const size_t Ndd = g.Ndd, nsub = (size_t)g.Lx * g.W;
   const cxd* q = b.Q + ((size_t)f * (g.k_max + g.nb) + (size_t)j * g.nb + c) * Ndd;
   cxd* u = b.u + (size_t)vs * Ndd;
+  if (g.qsplit) {
+    // the basis is stored as double-floats: widen this CTA's entries of q_j into u,
+    // which is free until the first H solve writes it, and read q_j from there
+    const cdfl* qs = reinterpret_cast<const cdfl*>(q);
+    const int n = own_count(g, i);
+    for (int e = threadIdx.x; e < n; e += (int)blockDim.x) {
+      const size_t k = own_idx(g, i, e, (int)nsub);
+      u[k] = cwiden(qs[k]);
+    }
+    __syncthreads();
+    q = u;
+  }
   int iters = 0, solves = 0, refines = 0, conv_all = 1, conv = 1;
 
   if (!mixed) {
