@@ -464,6 +464,12 @@ def run_ours(a, rank, world, local_rank):
         if a.workload != SIDE_WORKLOAD:
             extra["side_" + SIDE_WORKLOAD] = side_measurements(a, dev, stream)
         torch.cuda.empty_cache()
+        if not a.no_serving_sample:
+            extra["serving"] = serving_stream(SAMPLE_SIZES, 16, 48, 12, [0.8, 2.0], 8)
+            extra["serving"]["sample"] = ("bounded sample of the serving stream: 12 requests over "
+                                          "64^2, 128^2, 256^2 and 24^3, K in 16..48 (the full stream, "
+                                          "with 48^3 and K up to 256: bench.py --serving)")
+            torch.cuda.empty_cache()
 
     e2e = None
     if True:
@@ -558,44 +564,47 @@ def run_reference(a, rank, world):
 
 
 # ----------------------------------------------------------------- serving stream
-# lattices of the serving stream with their (p, k); 48^3 (p = 8 gives slice width 288 > 256)
-# is not taken
-SERVE_SIZES = [((64, 64), 4, 32), ((128, 128), 4, 32), ((256, 256), 8, 48), ((24, 24, 24), 4, 48)]
-SERVE_KMAX = 128
+# lattices of the serving stream: (L, p, k, frequencies a resident plan holds; a request
+# with more runs as consecutive chunks on its plan).  48^3 takes p = 16 (slice width 144),
+# so both forms run it (p = 8 gives W = 288, complex64 form only).
+SERVE_SIZES = [((64, 64), 4, 32, 128), ((128, 128), 4, 32, 128), ((256, 256), 8, 48, 64),
+               ((24, 24, 24), 4, 48, 64), ((48, 48, 48), 16, 64, 16)]
+# the bounded sample in the bench line: the 2D lattices and 24^3 (a 48^3 request alone
+# takes ~17 s mixed and ~50 s in FP64 at K = 16), K in 16..48, 12 requests
+SAMPLE_SIZES = SERVE_SIZES[:4]
 
 
-def run_serving(a):
+def serving_stream(sizes, kmin, kmax, nreq, rate_fracs, inflight, seed=5):
     """Open-loop Poisson arrivals of Dyson solves from simulated IDMFT loops.
 
-    Lattices drawn uniformly from 64^2 (p=4, k=32), 128^2 (p=4, k=32), 256^2 (p=8,
-    k=48) and 24^3 (p=4, k=48), K uniform in [16, 128], a fresh seeded self-energy
-    per request; every geometry's plan holds 128 frequencies.  The plain-FP64 capacity
-    is measured first by solving every request alone, one after the other;
-    the stream then arrives at rate_frac x that capacity and is served by the
-    continuous-batching server (mixed form, plans resident and reused).
+    Lattices drawn uniformly from `sizes`, K uniform in [kmin, kmax], a fresh seeded
+    self-energy per request (seed 1000 + request index).  The plain-FP64 capacity is
+    measured first by solving every request alone, one after the other (after one
+    untimed pass that creates the plans and captures their graphs); the stream then
+    arrives at rate_frac x that capacity and is served by the continuous-batching server
+    (mixed form, plans resident and reused).  Reports delivered site-frequencies/s,
+    p50/p99 latency from submission, and the served results' error against the plain
+    FP64 per-request results.
     """
     import numpy as np
     import torch
-    from paper_1102_3137_gb300 import build as B
     from paper_1102_3137_gb300 import dyson as D
     from paper_1102_3137_gb300 import inputs as I
-    B.build()
-    D.load()
-    torch.cuda.set_device(0)
-    rng = np.random.default_rng(5)
+    rng = np.random.default_rng(seed)
     reqs = []
-    for n in range(a.requests):
-        L, p, k = SERVE_SIZES[int(rng.integers(len(SERVE_SIZES)))]
-        K = int(rng.integers(16, SERVE_KMAX + 1))
+    pin = lambda x: torch.from_numpy(np.ascontiguousarray(x)).pin_memory().numpy()
+    for n in range(nreq):
+        L, p, k, cap = sizes[int(rng.integers(len(sizes)))]
+        K = int(rng.integers(kmin, kmax + 1))
         w = I.Workload("serve", L, -1.0, 0.0, 0.01, 0.5, 20.0, K, p, k, 1000 + n)
         omega, V, sigma, q1 = I.make_inputs(w)
-        pin = lambda x: torch.from_numpy(x).pin_memory().numpy()
-        reqs.append(dict(w=w, omega=pin(omega), V=pin(V), sigma=pin(sigma), q1=pin(q1),
-                         out=torch.zeros((K, w.N), dtype=torch.complex128).pin_memory().numpy()))
+        zero = lambda: torch.zeros((K, w.N), dtype=torch.complex128).pin_memory().numpy()
+        reqs.append(dict(w=w, cap=cap, omega=pin(omega), V=pin(V), sigma=pin(sigma), q1=pin(q1),
+                         out=zero(), plain=zero()))
     work = sum(r["w"].N * r["w"].K for r in reqs)
 
-    def serve(prec, arrivals, inflight):
-        srv = D.dyson_server_create(96 << 30, max_inflight=inflight)
+    def serve(prec, arrivals, nflight, key):
+        srv = D.dyson_server_create(96 << 30, max_inflight=nflight)
         t0 = time.perf_counter()
         tickets = []
         for r, ta in zip(reqs, arrivals):
@@ -603,37 +612,64 @@ def run_serving(a):
             if dt > 0:
                 time.sleep(dt)
             w = r["w"]
-            geom = D.make_geometry(w.L, w.t, w.mu, w.p, w.k, prec, max_freqs=SERVE_KMAX)
-            tickets.append(D.dyson_submit(srv, geom, w.K, r["omega"], r["V"], r["sigma"], r["q1"], r["out"]))
+            geom = D.make_geometry(w.L, w.t, w.mu, w.p, w.k, prec, max_freqs=r["cap"])
+            tickets.append(D.dyson_submit(srv, geom, w.K, r["omega"], r["V"], r["sigma"], r["q1"], r[key]))
         lat = [D.dyson_wait(srv, t)[0] for t in tickets]
         wall = time.perf_counter() - t0
         st = D.dyson_server_stats(srv)
         D.dyson_server_destroy(srv)
         return wall, lat, st
 
-    # warm plans and graphs for both forms, then the plain-FP64 one-at-a-time capacity
-    serve(D.DYSON_FP64, [0.0] * len(reqs), 1)
-    wall_plain, lat_plain, _ = serve(D.DYSON_FP64, [0.0] * len(reqs), 1)
+    serve(D.DYSON_FP64, [0.0] * len(reqs), 1, "plain")               # plans and graphs
+    wall_plain, _, _ = serve(D.DYSON_FP64, [0.0] * len(reqs), 1, "plain")
     capacity = work / wall_plain
     mean_work = work / len(reqs)
-    out = dict(metric="serving: site-frequencies/s and p50/p99 request latency (continuous batching)",
-               unit="site-frequencies/s", requests=len(reqs),
-               config=dict(lattices="64x64 p=4 k=32 | 128x128 p=4 k=32 | 256x256 p=8 k=48 | 24^3 p=4 k=48",
-                           K="uniform 16..128",
-                           arrivals="open-loop Poisson, seed 5", served_form="mixed",
-                           max_inflight=a.inflight),
+    out = dict(unit="site-frequencies/s", requests=len(reqs), site_frequencies=work,
+               config=dict(lattices=" | ".join(f"{'x'.join(map(str, L))} p={p} k={k} plan={c}"
+                                               for L, p, k, c in sizes),
+                           K=f"uniform {kmin}..{kmax}", arrivals=f"open-loop Poisson, seed {seed}",
+                           served_form="mixed", max_inflight=inflight, hbm_budget_gb=96),
                plain_fp64_capacity=capacity, plain_fp64_sequential_wall_s=wall_plain, rates=[])
-    serve(D.DYSON_MIXED, [0.0] * len(reqs), a.inflight)            # warm mixed plans
-    for frac in a.rate_fracs:
-        lam = frac * capacity / mean_work                          # requests per second
+    serve(D.DYSON_MIXED, [0.0] * len(reqs), inflight, "out")         # mixed plans and graphs
+    for frac in rate_fracs:
+        lam = frac * capacity / mean_work                              # requests per second
         gaps = np.random.default_rng(int(frac * 1000)).exponential(1.0 / lam, len(reqs))
         arrivals = np.cumsum(gaps) - gaps[0]
-        wall, lat, st = serve(D.DYSON_MIXED, list(arrivals), a.inflight)
+        wall, lat, st = serve(D.DYSON_MIXED, list(arrivals), inflight, "out")
         sl = sorted(lat)
         out["rates"].append(dict(rate_frac=frac, offered=frac * capacity, value=work / wall,
                                  p50_ms=sl[len(sl) // 2], p99_ms=sl[min(len(sl) - 1, int(0.99 * len(sl)))],
                                  peak_running=st["peak_running"], plans_created=st["plans_created"],
                                  plans_evicted=st["plans_evicted"]))
+    # served (mixed) against the plain FP64 per-request results, per lattice: the truncated
+    # rank-k diagonal of the 3D slabs is not reproducible at 1e-6 even between two FP64
+    # runs (its rounding amplification), so the lattices are reported apart
+    per = {}
+    for r in reqs:
+        name = "x".join(map(str, r["w"].L))
+        rel = (np.abs(r["out"] - r["plain"]) / np.abs(r["plain"])).ravel()
+        e = per.setdefault(name, dict(requests=0, max=0.0, sites=0, sites_above_1e_6=0, med=[]))
+        e["requests"] += 1
+        e["max"] = max(e["max"], float(rel.max()))
+        e["sites"] += int(rel.size)
+        e["sites_above_1e_6"] += int((rel > 1e-6).sum())
+        e["med"].append(float(np.median(rel)))
+    for e in per.values():
+        e["median"] = float(np.median(e.pop("med")))
+    out["err_vs_plain"] = per
+    return out
+
+
+def run_serving(a):
+    """The serving stream on all five lattices (`--serving`): K in 16..256, --requests."""
+    import torch
+    from paper_1102_3137_gb300 import build as B
+    from paper_1102_3137_gb300 import dyson as D
+    B.build()
+    D.load()
+    torch.cuda.set_device(0)
+    out = serving_stream(SERVE_SIZES, 16, 256, a.requests, a.rate_fracs, a.inflight)
+    out["metric"] = "serving: site-frequencies/s and p50/p99 request latency (continuous batching)"
     return out
 
 
@@ -682,6 +718,7 @@ def main():
                     help="frequencies per oracle sample (0: 1 for the 512^2 workload, 16 otherwise)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip the plain-FP64 and per-launch extras")
+    ap.add_argument("--no-serving-sample", action="store_true", help="skip the bounded serving sample")
     ap.add_argument("--serving", action="store_true", help="run the continuous-batching serving stream")
     ap.add_argument("--requests", type=int, default=48)
     ap.add_argument("--inflight", type=int, default=8)
