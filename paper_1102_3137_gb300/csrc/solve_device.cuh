@@ -1307,8 +1307,10 @@ __device__ void layer_diag(const Geo& g, const Bufs& b, int vs, int i) {
 // res = rhs - H x (mode 0: full H; mode 1: B only, no interface coupling),
 // FP64, on this CTA's entries.  Returns partials (||res||^2, ||rhs||^2).
 // H_ii comes from the per-solve DD-layout copy (coalesced); each thread takes
-// RU sites per pass and issues all their loads before any arithmetic, so the
-// loads of a pass are in flight together.
+// RU sites per pass and issues all their loads before any store, so the loads
+// of a pass are in flight together; every term enters by one fused
+// multiply-add (the FP64 pipe is what bounds this pass when all frequencies
+// run it together).
 __device__ __noinline__ void residual_H(const Geo& g, const Bufs& b, int vs, int i, const cxd* rhs,
                                         const cxd* x, cxd* res, int mode, double* rn, double* qn) {
   constexpr int RU = 4;
@@ -1324,38 +1326,44 @@ __device__ __noinline__ void residual_H(const Geo& g, const Bufs& b, int vs, int
   const cxd* xlo = (mode == 0 && i > 0) ? x + g.ifc_off + (size_t)(i - 1) * A : nullptr;
   const cxd* xhi = (mode == 0 && i < g.p - 1) ? x + g.ifc_off + (size_t)i * A : nullptr;
   double sr = 0, sq = 0;
+  const double mt = -t;
   for (int e0 = threadIdx.x; e0 < nsub; e0 += RU * nt) {
-    cxd d[RU], xv[RU], nb[RU], q[RU];
+    cxd q[RU], rr[RU];
     bool on[RU];
 #pragma unroll
     for (int u = 0; u < RU; ++u) {
       const int e = e0 + u * nt;
       const int s = e / W, j = e - s * W;
       on[u] = e < nsub && j < w;
-      d[u] = xv[u] = nb[u] = q[u] = cxd{0, 0};
+      q[u] = rr[u] = cxd{0, 0};
       if (on[u]) {
         const int tr = j % T, sl = j / T;
-        d[u] = hs[e];
-        xv[u] = xs[e];
-        q[u] = rs_[e];
-        cxd n = {0, 0};
-        if (s > 0) n = n + xs[e - W];
-        if (s < Lx - 1) n = n + xs[e + W];
-        if (tr > 0) n = n + xs[e - 1];
-        if (tr < T - 1) n = n + xs[e + 1];
-        if (sl > 0) n = n + xs[e - T];
-        if (sl < h - 1) n = n + xs[e + T];
-        if (sl == 0 && xlo) n = n + xlo[s + Lx * tr];
-        if (sl == h - 1 && xhi) n = n + xhi[s + Lx * tr];
-        nb[u] = n;
+        const cxd dv = hs[e], xc = xs[e];
+        cxd r = rs_[e];
+        q[u] = r;
+        // r = q - t (sum of neighbours) - H_ii x, one fused multiply-add per term
+        auto sub = [&](cxd v) {
+          r.x = fma(mt, v.x, r.x);
+          r.y = fma(mt, v.y, r.y);
+        };
+        if (s > 0) sub(xs[e - W]);
+        if (s < Lx - 1) sub(xs[e + W]);
+        if (tr > 0) sub(xs[e - 1]);
+        if (tr < T - 1) sub(xs[e + 1]);
+        if (sl > 0) sub(xs[e - T]);
+        if (sl < h - 1) sub(xs[e + T]);
+        if (sl == 0 && xlo) sub(xlo[s + Lx * tr]);
+        if (sl == h - 1 && xhi) sub(xhi[s + Lx * tr]);
+        r.x = fma(-dv.x, xc.x, fma(dv.y, xc.y, r.x));
+        r.y = fma(-dv.x, xc.y, fma(-dv.y, xc.x, r.y));
+        rr[u] = r;
       }
     }
 #pragma unroll
     for (int u = 0; u < RU; ++u) {
       if (!on[u]) continue;
-      const cxd rr = q[u] - (d[u] * xv[u] + t * nb[u]);
-      ro[e0 + u * nt] = rr;
-      sr += cabs2(rr);
+      ro[e0 + u * nt] = rr[u];
+      sr += cabs2(rr[u]);
       sq += cabs2(q[u]);
     }
   }
@@ -1730,10 +1738,20 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 4 : 2) k_xmatvec(Geo g, Bufs b
       conv_all &= conv;
       ++solves;
       __syncthreads();
-      const int n = own_count(g, i);
-      for (int e = threadIdx.x; e < n; e += (int)blockDim.x) {
-        size_t k = own_idx(g, i, e, (int)nsub);
-        u[k] = u[k] + wv[k];
+      const int n = own_count(g, i), nt = (int)blockDim.x;
+      for (int e0 = threadIdx.x; e0 < n; e0 += 4 * nt) {   // four entries' loads in flight
+        cxd a4[4], b4[4];
+        size_t k4[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const int e = e0 + m * nt;
+          k4[m] = e < n ? own_idx(g, i, e, (int)nsub) : 0;
+          a4[m] = e < n ? u[k4[m]] : cxd{0, 0};
+          b4[m] = e < n ? wv[k4[m]] : cxd{0, 0};
+        }
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+          if (e0 + m * nt < n) u[k4[m]] = a4[m] + b4[m];
       }
     }
   }
