@@ -579,8 +579,9 @@ def serving_stream(sizes, kmin, kmax, nreq, rate_fracs, inflight, seed=5):
 
     Lattices drawn uniformly from `sizes`, K uniform in [kmin, kmax], a fresh seeded
     self-energy per request (seed 1000 + request index).  The plain-FP64 capacity is
-    measured first by solving every request alone, one after the other (after one
-    untimed pass that creates the plans and captures their graphs); the stream then
+    measured first by solving every request alone, one after the other (each submitted
+    after the previous one finished, so none is fused; after one untimed pass that
+    creates the plans and captures their graphs); the stream then
     arrives at rate_frac x that capacity and is served by the continuous-batching server
     (mixed form, plans resident and reused).  Reports delivered site-frequencies/s,
     p50/p99 latency from submission, and the served results' error against the plain
@@ -593,20 +594,29 @@ def serving_stream(sizes, kmin, kmax, nreq, rate_fracs, inflight, seed=5):
     rng = np.random.default_rng(seed)
     reqs = []
     pin = lambda x: torch.from_numpy(np.ascontiguousarray(x)).pin_memory().numpy()
+    # one simulated IDMFT client per lattice: its trap V and Lanczos start vector stay
+    # fixed over its iterations (seeded 5000 + lattice index), Sigma is fresh per request
+    client = {}
     for n in range(nreq):
-        L, p, k, cap = sizes[int(rng.integers(len(sizes)))]
+        li = int(rng.integers(len(sizes)))
+        L, p, k, cap = sizes[li]
         K = int(rng.integers(kmin, kmax + 1))
         w = I.Workload("serve", L, -1.0, 0.0, 0.01, 0.5, 20.0, K, p, k, 1000 + n)
-        omega, V, sigma, q1 = I.make_inputs(w)
+        omega, _, sigma, _ = I.make_inputs(w)
+        if li not in client:
+            wc = I.Workload("client", L, -1.0, 0.0, 0.01, 0.5, 20.0, 1, p, k, 5000 + li)
+            _, Vc, _, qc = I.make_inputs(wc)
+            client[li] = (pin(Vc), pin(qc))
+        V, q1 = client[li]
         zero = lambda: torch.zeros((K, w.N), dtype=torch.complex128).pin_memory().numpy()
-        reqs.append(dict(w=w, cap=cap, omega=pin(omega), V=pin(V), sigma=pin(sigma), q1=pin(q1),
+        reqs.append(dict(w=w, cap=cap, omega=pin(omega), V=V, sigma=pin(sigma), q1=q1,
                          out=zero(), plain=zero()))
     work = sum(r["w"].N * r["w"].K for r in reqs)
 
-    def serve(prec, arrivals, nflight, key):
+    def serve(prec, arrivals, nflight, key, one_by_one=False):
         srv = D.dyson_server_create(96 << 30, max_inflight=nflight)
         t0 = time.perf_counter()
-        tickets = []
+        tickets, lat = [], []
         for r, ta in zip(reqs, arrivals):
             dt = ta - (time.perf_counter() - t0)
             if dt > 0:
@@ -614,14 +624,16 @@ def serving_stream(sizes, kmin, kmax, nreq, rate_fracs, inflight, seed=5):
             w = r["w"]
             geom = D.make_geometry(w.L, w.t, w.mu, w.p, w.k, prec, max_freqs=r["cap"])
             tickets.append(D.dyson_submit(srv, geom, w.K, r["omega"], r["V"], r["sigma"], r["q1"], r[key]))
-        lat = [D.dyson_wait(srv, t)[0] for t in tickets]
+            if one_by_one:                   # per-request solves: nothing queues, nothing fuses
+                lat.append(D.dyson_wait(srv, tickets.pop())[0])
+        lat += [D.dyson_wait(srv, t)[0] for t in tickets]
         wall = time.perf_counter() - t0
         st = D.dyson_server_stats(srv)
         D.dyson_server_destroy(srv)
         return wall, lat, st
 
-    serve(D.DYSON_FP64, [0.0] * len(reqs), 1, "plain")               # plans and graphs
-    wall_plain, _, _ = serve(D.DYSON_FP64, [0.0] * len(reqs), 1, "plain")
+    serve(D.DYSON_FP64, [0.0] * len(reqs), 1, "plain", True)          # plans and graphs
+    wall_plain, _, _ = serve(D.DYSON_FP64, [0.0] * len(reqs), 1, "plain", True)
     capacity = work / wall_plain
     mean_work = work / len(reqs)
     out = dict(unit="site-frequencies/s", requests=len(reqs), site_frequencies=work,
@@ -640,7 +652,7 @@ def serving_stream(sizes, kmin, kmax, nreq, rate_fracs, inflight, seed=5):
         out["rates"].append(dict(rate_frac=frac, offered=frac * capacity, value=work / wall,
                                  p50_ms=sl[len(sl) // 2], p99_ms=sl[min(len(sl) - 1, int(0.99 * len(sl)))],
                                  peak_running=st["peak_running"], plans_created=st["plans_created"],
-                                 plans_evicted=st["plans_evicted"]))
+                                 plans_evicted=st["plans_evicted"], fused_requests=st["fused"]))
     # served (mixed) against the plain FP64 per-request results, per lattice: the truncated
     # rank-k diagonal of the 3D slabs is not reproducible at 1e-6 even between two FP64
     # runs (its rounding amplification), so the lattices are reported apart

@@ -266,6 +266,10 @@ int dyson_xmatvec(dyson_plan plan, int K, const double* omega, const double* V,
  * device-memory budget (bytes of resident plans) and a stream slot allow;
  * while the oldest request waits for memory, later requests whose plan is
  * resident and idle run in its place (at most 64 per waiting request).
+ * Queued requests with the geometry of an admitted one and bitwise the same V
+ * and start vector(s) join its solve as further frequencies, while they fit
+ * the plan's max_freqs (at most 32 requests per solve): requests of uneven K
+ * share one batched launch sequence.
  * Admitted requests run concurrently, each as one batched, graph-replayed
  * solve on its own stream.  Plans (factors, Lanczos bases, workspace) stay
  * resident and are reused by later requests with the same geometry; idle
@@ -292,6 +296,7 @@ typedef struct {
   int queued, running, resident_plans, peak_running;
   size_t bytes_in_use, peak_bytes;
   uint64_t admitted, completed, plans_created, plans_evicted;
+  uint64_t fused;        /* requests that ran as a segment of a fused solve */
 } dyson_server_stats_t;
 
 /* hbm_budget: most device bytes of resident plans; max_inflight: concurrent requests (1..64).

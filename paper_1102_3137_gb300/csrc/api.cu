@@ -14,6 +14,7 @@
 
 #include "dyson.h"
 #include "dyson_common.cuh"
+#include "host_internal.h"
 
 namespace {
 
@@ -690,6 +691,46 @@ int dyson_internal_solve_enqueue(dyson_plan p, int K, const double* omega, const
   }
   CK(cudaMemcpyAsync(diagG, p->b.out, (size_t)K * p->g.N * sizeof(cxd), cudaMemcpyDefault, s));
   if (status) CK(cudaMemcpyAsync(status, p->status_d, K * sizeof(int), cudaMemcpyDefault, s));
+  return DYSON_OK;
+}
+
+int dyson_internal_solve_enqueue_segs(dyson_plan p, int nseg, const SolveSeg* segs, const double* V,
+                                      const double* q1, int mem_kind, void* stream) {
+  int rc;
+  if ((rc = check_plan(p)) || (rc = check_mem(mem_kind))) return rc;
+  if (nseg < 1 || !segs || !V || !q1) return fail(DYSON_E_BAD_ARG, "fused solve: no segments, V or q1");
+  int K = 0;
+  for (int n = 0; n < nseg; ++n) {
+    if (segs[n].K < 1 || !segs[n].omega || !segs[n].sigma || !segs[n].diagG)
+      return fail(DYSON_E_BAD_ARG, "fused solve: a segment without frequencies or buffers");
+    K += segs[n].K;
+  }
+  if ((rc = check_K(p, K))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  const Geo& g = p->g;
+  const size_t N = g.N;
+  for (int n = 0, k0 = 0; n < nseg; k0 += segs[n].K, ++n) {
+    CK(cudaMemcpyAsync(at<double>(p, B_OMEGA) + k0, segs[n].omega, segs[n].K * sizeof(double),
+                       cudaMemcpyDefault, s));
+    CK(cudaMemcpyAsync(at<cxd>(p, B_SIGMA) + (size_t)k0 * N, segs[n].sigma, (size_t)segs[n].K * N * sizeof(cxd),
+                       cudaMemcpyDefault, s));
+  }
+  CK(cudaMemcpyAsync(at<double>(p, B_V), V, N * sizeof(double), cudaMemcpyDefault, s));
+  CK(cudaMemcpyAsync(at<double>(p, B_Q1), q1, (size_t)g.nb * N * sizeof(double), cudaMemcpyDefault, s));
+  if (!p->tuned && (rc = autotune(p, K, s))) return rc;
+  if (p->use_graph) {
+    cudaGraphExec_t ex;
+    if ((rc = get_graph(p, K, &ex))) return rc;
+    CK(cudaGraphLaunch(ex, s));
+  } else if ((rc = enqueue_solve(p, K, s, false))) {
+    return rc;
+  }
+  for (int n = 0, k0 = 0; n < nseg; k0 += segs[n].K, ++n) {
+    CK(cudaMemcpyAsync(segs[n].diagG, p->b.out + (size_t)k0 * N, (size_t)segs[n].K * N * sizeof(cxd),
+                       cudaMemcpyDefault, s));
+    if (segs[n].status)
+      CK(cudaMemcpyAsync(segs[n].status, p->status_d + k0, segs[n].K * sizeof(int), cudaMemcpyDefault, s));
+  }
   return DYSON_OK;
 }
 

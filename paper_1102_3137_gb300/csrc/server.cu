@@ -16,8 +16,11 @@
 //     only when evicting them makes room);
 //   - each admitted request runs its whole batched solve (one captured graph
 //     per chunk of at most the plan's max_freqs frequencies) on its own
-//     stream; completion is detected with events, and the latency from
-//     submission to completion is recorded per request.
+//     stream; queued requests of the same geometry with the same V and start
+//     vector join it as further frequencies (one fused launch sequence for
+//     requests of uneven K, up to the plan's capacity); completion is detected
+//     with events, and the latency from submission to completion is recorded
+//     per request.
 // A request's result does not depend on what else runs: every frequency is
 // computed by its own thread-block cluster with fixed-order reductions.
 #include <algorithm>
@@ -35,6 +38,7 @@
 
 #include "dyson.h"
 #include "dyson_common.cuh"
+#include "host_internal.h"
 
 namespace {
 
@@ -80,6 +84,10 @@ struct Req {
 // among the first BACKFILL_WINDOW queued requests.
 constexpr int BACKFILL_PER_HEAD = 64;
 constexpr size_t BACKFILL_WINDOW = 256;
+// Fusion: queued requests with the admitted request's geometry, the same V and the
+// same start vector(s) join its solve as further frequency segments, up to the
+// plan's frequency capacity and FUSE_MAX requests per solve.
+constexpr int FUSE_MAX = 32;
 
 }  // namespace
 
@@ -95,12 +103,13 @@ struct dyson_server_s {
   std::vector<cudaStream_t> streams;
   std::vector<cudaEvent_t> events;
   std::vector<uint64_t> stream_owner;      // ticket running on each stream, 0 = free
+  std::vector<std::vector<uint64_t>> stream_group;   // every ticket of that stream's (fused) solve
   size_t used = 0;                         // bytes of all live plans
   uint64_t next_ticket = 1;
   bool stop = false;
   std::thread worker;
   // statistics
-  uint64_t completed = 0, admitted = 0, plans_created = 0, plans_evicted = 0;
+  uint64_t completed = 0, admitted = 0, plans_created = 0, plans_evicted = 0, fused = 0;
   size_t peak_used = 0;
   int peak_running = 0;
 };
@@ -185,19 +194,24 @@ void worker_main(dyson_server_s* s) {
       if (!t) continue;
       cudaError_t q = cudaEventQuery(s->events[k]);
       if (q == cudaErrorNotReady) continue;
-      Req& r = s->reqs[t];
-      r.t_done = now_s();
-      if (q == cudaSuccess) {
-        r.state = Q_DONE;
-      } else {
-        r.state = Q_FAILED;
-        r.rc = DYSON_E_CUDA;
-        r.err = std::string("request failed on the device: ") + cudaGetErrorString(q);
+      const double td = now_s();
+      for (uint64_t tg : s->stream_group[k]) {
+        Req& r = s->reqs[tg];
+        r.t_done = td;
+        if (q == cudaSuccess) {
+          r.state = Q_DONE;
+        } else {
+          r.state = Q_FAILED;
+          r.rc = DYSON_E_CUDA;
+          r.err = std::string("request failed on the device: ") + cudaGetErrorString(q);
+        }
+        s->completed++;
       }
+      Req& r = s->reqs[t];
       r.slot->busy = false;
-      r.slot->last_use = r.t_done;
+      r.slot->last_use = td;
       s->stream_owner[k] = 0;
-      s->completed++;
+      s->stream_group[k].clear();
       s->cv_done.notify_all();
     }
     if (s->stop && s->queue.empty() && running_count(s) == 0) break;
@@ -240,28 +254,61 @@ void worker_main(dyson_server_s* s) {
       int k = 0;
       while (s->stream_owner[k]) ++k;
       s->stream_owner[k] = t;
+      s->stream_group[k].assign(1, t);
+      const double t0 = now_s();
       q.slot = ps;
       q.stream = k;
       q.state = Q_RUNNING;
-      q.t_start = now_s();
+      q.t_start = t0;
       s->admitted++;
+      const dyson_request r = q.r;
+      const int cap = r.geom.max_freqs;
+      const size_t N = (size_t)r.geom.L[0] * r.geom.L[1] * (r.geom.dim == 3 ? r.geom.L[2] : 1);
+      const size_t nq1 = N * (size_t)(r.geom.block_size > 1 ? r.geom.block_size : 1);
+      // fusion: queued requests of this geometry with the same V and start vector(s)
+      // join this solve while the frequencies fit the plan
+      std::vector<SolveSeg> segs(1, SolveSeg{r.K, r.omega, r.sigma, r.diagG, r.status});
+      int Ktot = r.K;
+      for (size_t jq = 0; jq < s->queue.size() && (int)segs.size() < FUSE_MAX && Ktot < cap;) {
+        Req& c = s->reqs[s->queue[jq]];
+        const bool same = c.key == q.key && Ktot + c.r.K <= cap &&
+                          (c.r.V == r.V || !std::memcmp(c.r.V, r.V, N * sizeof(double))) &&
+                          (c.r.q1 == r.q1 || !std::memcmp(c.r.q1, r.q1, nq1 * sizeof(double)));
+        if (!same) {
+          ++jq;
+          continue;
+        }
+        const uint64_t tc = s->queue[jq];
+        s->queue.erase(s->queue.begin() + (long)jq);
+        c.slot = ps;
+        c.stream = k;
+        c.state = Q_RUNNING;
+        c.t_start = t0;
+        s->admitted++;
+        s->stream_group[k].push_back(tc);
+        segs.push_back(SolveSeg{c.r.K, c.r.omega, c.r.sigma, c.r.diagG, c.r.status});
+        Ktot += c.r.K;
+      }
+      if (segs.size() > 1) s->fused += segs.size();
       const int run = running_count(s);
       if (run > s->peak_running) s->peak_running = run;
       if (s->used > s->peak_used) s->peak_used = s->used;
-      const dyson_request r = q.r;
       cudaStream_t st = s->streams[k];
       cudaEvent_t ev = s->events[k];
       lk.unlock();
-      // a request with more frequencies than its plan holds runs as consecutive
-      // chunks of max_freqs on the same plan and stream (frequencies are independent)
       int e = DYSON_OK;
-      const int cap = r.geom.max_freqs;
-      const size_t N = (size_t)r.geom.L[0] * r.geom.L[1] * (r.geom.dim == 3 ? r.geom.L[2] : 1);
-      for (int k0 = 0; k0 < r.K && !e; k0 += cap) {
-        const int kc = r.K - k0 < cap ? r.K - k0 : cap;
-        e = dyson_internal_solve_enqueue(ps->plan, kc, r.omega + k0, r.V, r.sigma + 2 * (size_t)k0 * N, r.q1,
-                                         r.diagG + 2 * (size_t)k0 * N, r.status ? r.status + k0 : nullptr,
-                                         DYSON_MEM_HOST, st);
+      if (segs.size() > 1) {
+        e = dyson_internal_solve_enqueue_segs(ps->plan, (int)segs.size(), segs.data(), r.V, r.q1, DYSON_MEM_HOST,
+                                              st);
+      } else {
+        // a request with more frequencies than its plan holds runs as consecutive
+        // chunks of max_freqs on the same plan and stream (frequencies are independent)
+        for (int k0 = 0; k0 < r.K && !e; k0 += cap) {
+          const int kc = r.K - k0 < cap ? r.K - k0 : cap;
+          e = dyson_internal_solve_enqueue(ps->plan, kc, r.omega + k0, r.V, r.sigma + 2 * (size_t)k0 * N, r.q1,
+                                           r.diagG + 2 * (size_t)k0 * N, r.status ? r.status + k0 : nullptr,
+                                           DYSON_MEM_HOST, st);
+        }
       }
       std::string msg = e ? dyson_last_error() : "";
       if (!e) {
@@ -273,13 +320,17 @@ void worker_main(dyson_server_s* s) {
       }
       lk.lock();
       if (e) {
-        Req& qq = s->reqs[t];
-        qq.state = Q_FAILED;
-        qq.rc = e;
-        qq.err = msg;
-        qq.t_done = now_s();
+        const double td = now_s();
+        for (uint64_t tg : s->stream_group[k]) {
+          Req& qq = s->reqs[tg];
+          qq.state = Q_FAILED;
+          qq.rc = e;
+          qq.err = msg;
+          qq.t_done = td;
+        }
         ps->busy = false;
         s->stream_owner[k] = 0;
+        s->stream_group[k].clear();
         s->cv_done.notify_all();
       }
     }
@@ -307,6 +358,7 @@ int dyson_server_create(size_t hbm_budget, int max_inflight, dyson_server* out) 
   s->streams.resize(max_inflight);
   s->events.resize(max_inflight);
   s->stream_owner.assign(max_inflight, 0);
+  s->stream_group.assign(max_inflight, {});
   for (int k = 0; k < max_inflight; ++k) {
     cudaError_t e = cudaStreamCreateWithFlags(&s->streams[k], cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->events[k], cudaEventDisableTiming);
@@ -417,6 +469,7 @@ int dyson_server_stats(dyson_server s, dyson_server_stats_t* out) {
   out->completed = s->completed;
   out->plans_created = s->plans_created;
   out->plans_evicted = s->plans_evicted;
+  out->fused = s->fused;
   return DYSON_OK;
 }
 

@@ -65,7 +65,7 @@ class dyson_server_stats_t(C.Structure):
     _fields_ = [("queued", C.c_int), ("running", C.c_int), ("resident_plans", C.c_int),
                 ("peak_running", C.c_int), ("bytes_in_use", C.c_size_t), ("peak_bytes", C.c_size_t),
                 ("admitted", C.c_uint64), ("completed", C.c_uint64),
-                ("plans_created", C.c_uint64), ("plans_evicted", C.c_uint64)]
+                ("plans_created", C.c_uint64), ("plans_evicted", C.c_uint64), ("fused", C.c_uint64)]
 
 
 class DysonError(RuntimeError):

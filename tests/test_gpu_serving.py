@@ -150,3 +150,38 @@ def test_small_request_backfills_past_one_waiting_for_memory():
     stats = D.dyson_server_stats(srv)
     assert stats["completed"] == 4 and stats["peak_bytes"] <= need[big_a] + 2 * need[small]
     D.dyson_server_destroy(srv)
+
+
+@pytest.mark.parametrize("prec,tol", [(D.DYSON_FP64, 1e-10), (D.DYSON_MIXED, 1e-6)])
+def test_requests_of_one_geometry_fuse_into_one_solve(prec, tol):
+    """Four requests of uneven K (3, 5, 2, 6) on one geometry, with the same V and start
+    vector, queue behind a running request and then run as one fused solve of 16
+    frequencies; each result matches its own solve alone and the exact diagonal (16^2,
+    p = 2: m = 16, the cap of 24 closes the Krylov space)."""
+    from oracle import dyson_oracle as O
+    srv = D.dyson_server_create(8 << 30, max_inflight=1)
+    wb, ob, Vb, sb, qb = request_inputs((128, 128), 4, 32, 16, 60)      # runs first, the rest queue
+    gb = D.make_geometry(wb.L, wb.t, wb.mu, 4, 32, prec, max_freqs=16)
+    outb = np.zeros((16, wb.N), complex)
+    tb = D.dyson_submit(srv, gb, 16, ob, Vb, sb, qb, outb)
+    _, _, V, _, q1 = request_inputs((16, 16), 2, 24, 1, 70)              # shared V and start vector
+    geom = D.make_geometry((16, 16), -1.0, 0.0, 2, 24, prec, max_freqs=16)
+    jobs = []
+    for n, K in enumerate((3, 5, 2, 6)):
+        w, omega, _, sigma, _ = request_inputs((16, 16), 2, 24, K, 71 + n)
+        out = np.zeros((K, w.N), complex)
+        st = np.zeros(K, np.int32)
+        jobs.append((D.dyson_submit(srv, geom, K, omega, V, sigma, q1, out, st), w, omega, sigma, out, st))
+    D.dyson_wait(srv, tb)
+    for t, w, omega, sigma, out, st in jobs:
+        D.dyson_wait(srv, t)
+    stats = D.dyson_server_stats(srv)
+    D.dyson_server_destroy(srv)
+    assert stats["fused"] == 4 and stats["completed"] == 5
+    for t, w, omega, sigma, out, st in jobs:
+        assert np.all(st & D.DYSON_ST_TERMINATED)
+        ref = alone(w, omega, V, sigma, q1, prec)
+        assert np.max(np.abs(out - ref) / np.abs(ref)) <= tol
+        for k in range(w.K):
+            ex = O.exact_diag(w.L, (False,) * 3, w.t, O.dyson_diagonal(omega[k], w.mu, V, sigma[k]))
+            assert np.max(np.abs(out[k] - ex) / np.abs(ex)) <= tol
