@@ -123,7 +123,9 @@ typedef struct {
                          iterations.  BANDED keeps the entries of S_ll within two sites.
                          LAYER where it does not apply: DYSON_E_UNSUPPORTED. */
   int freq_groups;    /* frequencies of a solve are split into this many contiguous groups
-                         (0: default 4, at most 8; 1: one batch), each run as its own branch
+                         (0: default, one group per 16 frequencies of max_freqs in the mixed
+                         form and per 8 in FP64, between 1 and 4; at most 8; 1: one batch),
+                         each run as its own branch
                          of the solve's CUDA graph on its own stream, the lowest-index group
                          at the highest stream priority.  Frequencies stay independent, so
                          results do not depend on the grouping.  Plans whose slice width

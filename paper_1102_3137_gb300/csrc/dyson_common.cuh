@@ -29,7 +29,7 @@
 #define DY_LPRE_MAXLX 160   // widest interface line of the shared-memory layer preconditioner
 #define DY_LPRE_MAXLX_G 1024 // widest interface line of its global-memory form
 #define DY_LPRE_MAXW 32     // widest slice it takes
-#define DY_FREQ_GROUPS 4    // default frequency groups of a solve (parallel graph branches)
+#define DY_FREQ_GROUPS 4    // most frequency groups of a solve by default (parallel graph branches)
 #define DY_MAX_GROUPS 8
 #define DY_BLOCK_H 1024     // block Lanczos: k_max * nb bound (CGS2 coefficients kept in shared memory)
 #define DY_FACTOR_CTAS 304  // persistent grid of the wide-slice factor kernel (2 per SM on 152 SMs)
