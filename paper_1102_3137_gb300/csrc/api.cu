@@ -79,14 +79,21 @@ int build_part(const dyson_geometry* in, Part* out, bool gpu) {
   if (in->precond < DYSON_PRECOND_AUTO || in->precond > DYSON_PRECOND_LAYER)
     return fail(DYSON_E_BAD_ARG, "precond must be DYSON_PRECOND_AUTO, _BANDED or _LAYER");
   {
-    const bool fits = g.T == 1 && g.p > 1 && g.W <= DY_LPRE_MAXW &&
-                      (g.Lx <= DY_LPRE_MAXLX || (g.Lx <= DY_LPRE_MAXLX_G && g.W == DY_LPRE_MAXW));
+    // 2D strips: lines up to 160 sites (shared memory) or up to 1024 with slices of 32;
+    // 3D slabs: layers of A = Lx Ly <= 1024 sites with slices wider than 64 (their
+    // factorization is the one-sided global-memory one the surface recursion reads)
+    const bool fits2 = g.T == 1 && g.p > 1 && g.W <= DY_LPRE_MAXW &&
+                       (g.Lx <= DY_LPRE_MAXLX || (g.Lx <= DY_LPRE_MAXLX_G && g.W == DY_LPRE_MAXW));
+    const bool fits3 = g.T > 1 && g.p > 1 && g.W > DY_MAXW_SMEM && g.A <= DY_LPRE_MAXLX_G;
+    const bool fits = fits2 || fits3;
     if (in->precond == DYSON_PRECOND_LAYER && !fits)
-      return fail(DYSON_E_UNSUPPORTED, "exact layer preconditioner: 2D strips with p > 1 and either Lx <= " +
+      return fail(DYSON_E_UNSUPPORTED, "exact layer preconditioner: p > 1 and either 2D strips with Lx <= " +
                                            std::to_string(DY_LPRE_MAXLX) + " and slice width <= " +
                                            std::to_string(DY_LPRE_MAXW) + ", or Lx <= " +
                                            std::to_string(DY_LPRE_MAXLX_G) + " and slice width " +
-                                           std::to_string(DY_LPRE_MAXW) + " only");
+                                           std::to_string(DY_LPRE_MAXW) + ", or 3D slabs with Lx Ly <= " +
+                                           std::to_string(DY_LPRE_MAXLX_G) + " and slice width > " +
+                                           std::to_string(DY_MAXW_SMEM));
     g.lpre = (fits && in->precond != DYSON_PRECOND_BANDED) ? 1 : 0;
   }
   g.k_max = in->k_max;
@@ -138,7 +145,7 @@ int build_part(const dyson_geometry* in, Part* out, bool gpu) {
 enum {
   B_V, B_OMEGA, B_SIGMA, B_Q1, B_DD2NAT, B_G, B_G64, B_DIAGB, B_Q, B_ACC, B_U, B_V1, B_V2, B_V3,
   B_YSCR, B_BND, B_IFV, B_PRE, B_LAN, B_MAXT, B_ST, B_OUT, B_STATUS, B_SWEEPS, B_FWORK, B_OFFB, B_OFF2,
-  B_LPT, B_LPM, B_LPG, B_LPV, B_HDIAG, B_COUNT
+  B_LPT, B_LPM, B_LPG, B_LPV, B_HDIAG, B_LPW, B_COUNT
 };
 
 size_t layout(const Geo& g, int K, bool mixed, size_t off[B_COUNT]) {
@@ -173,11 +180,12 @@ size_t layout(const Geo& g, int K, bool mixed, size_t off[B_COUNT]) {
   sz[B_FWORK] = g.W > DY_MAXW_SMEM ? (size_t)DY_FACTOR_CTAS * 2 * g.W * g.W * sizeof(cxd) : 0;
   sz[B_OFFB] = Kz * g.p * nsub * sizeof(cxd);
   sz[B_OFF2] = g.penta ? Kz * g.p * nsub * sizeof(cxd) : 0;
-  const size_t Lx2 = (size_t)g.Lx * g.Lx;
-  sz[B_LPT] = g.lpre ? Kz * g.p * 2 * Lx2 * sizeof(cxf) : 0;
-  sz[B_LPM] = g.lpre ? Kz * (g.p - 1) * Lx2 * cs : 0;
-  sz[B_LPG] = g.lpre ? Kz * g.p * nsub * g.W * sizeof(cxf) : 0;
-  sz[B_LPV] = (g.lpre && g.Lx > DY_LPRE_MAXLX) ? Kz * g.p * 2 * (size_t)g.Lx * g.W * sizeof(cxf) : 0;
+  const size_t A2 = (size_t)g.A * g.A;   // layer blocks (A = Lx in 2D)
+  sz[B_LPT] = g.lpre ? Kz * g.p * 2 * A2 * sizeof(cxf) : 0;
+  sz[B_LPM] = g.lpre ? Kz * (g.p - 1) * A2 * cs : 0;
+  sz[B_LPG] = (g.lpre && g.T == 1) ? Kz * g.p * nsub * g.W * sizeof(cxf) : 0;
+  sz[B_LPV] = (g.lpre && g.T == 1 && g.Lx > DY_LPRE_MAXLX) ? Kz * g.p * 2 * (size_t)g.Lx * g.W * sizeof(cxf) : 0;
+  sz[B_LPW] = (g.lpre && g.T > 1) ? (size_t)DY_FACTOR_CTAS * 2 * g.W * 2 * (size_t)g.Lx * g.T * sizeof(cxf) : 0;
   sz[B_HDIAG] = mixed ? Kz * Ndd * sizeof(cxd) : 0;
   size_t o = 0;
   for (int k = 0; k < B_COUNT; ++k) {
@@ -370,8 +378,9 @@ Bufs sub_bufs(const Geo& g, const Bufs& b, bool mixed, int k0) {
   s.st = b.st + K0 * ST_N;
   s.out = b.out + K0 * g.N;
   s.sweeps = b.sweeps ? b.sweeps + S0 * g.p : nullptr;
-  s.lpt = b.lpt ? b.lpt + K0 * g.p * 2 * Lx2 : nullptr;
-  s.lpm = adv(reinterpret_cast<char*>(b.lpm), K0 * (g.p > 1 ? g.p - 1 : 0) * Lx2 * cs);
+  const size_t A2 = (size_t)g.A * g.A;
+  s.lpt = b.lpt ? b.lpt + K0 * g.p * 2 * A2 : nullptr;
+  s.lpm = adv(reinterpret_cast<char*>(b.lpm), K0 * (g.p > 1 ? g.p - 1 : 0) * A2 * cs);
   s.lpg = b.lpg ? b.lpg + K0 * g.p * nsub * g.W : nullptr;
   s.lpv = b.lpv ? b.lpv + K0 * g.p * 2 * (size_t)g.Lx * g.W : nullptr;
   return s;
@@ -610,7 +619,8 @@ int dyson_plan_create(const dyson_geometry* geom, dyson_plan* out) {
   b.lpt = p->g.lpre ? at<cxf>(p, B_LPT) : nullptr;
   b.lpm = p->g.lpre ? (void*)at<char>(p, B_LPM) : nullptr;
   b.lpg = p->g.lpre ? at<cxf>(p, B_LPG) : nullptr;
-  b.lpv = (p->g.lpre && p->g.Lx > DY_LPRE_MAXLX) ? at<cxf>(p, B_LPV) : nullptr;
+  b.lpv = (p->g.lpre && p->g.T == 1 && p->g.Lx > DY_LPRE_MAXLX) ? at<cxf>(p, B_LPV) : nullptr;
+  b.lpw = (p->g.lpre && p->g.T > 1) ? at<cxf>(p, B_LPW) : nullptr;
   p->status_d = at<int>(p, B_STATUS);
   p->profile = false;
   p->tuned = false;

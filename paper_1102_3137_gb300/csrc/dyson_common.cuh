@@ -244,6 +244,8 @@ struct Bufs {
   cx<float>* lpg;       // [K][p][Lx][W][W] complex64 slice factors of that recursion (lpre scratch)
   void* lpm;            // [K][p-1][Lx][Lx] inverse layer blocks of S, precision of the form (lpre)
   cx<float>* lpv;       // [K][p][2][Lx][W] boundary columns of the surface recursion (lpre, Lx > 160)
+  cx<float>* lpw;       // [DY_FACTOR_CTAS][2][W][2 Lx T] boundary-column chains of the 3D slab
+                        // surface recursion (lpre with T > 1), not per frequency
 };
 
 // interface Krylov vector slots inside ifv

@@ -29,6 +29,15 @@
 //                block Gauss-Jordan on 32 x 32 blocks (pivot block by the sweep
 //                operator in shared memory, row panel, rank-32 update of the
 //                rest, column panel), then writes the symmetrised inverse.
+// 3D slabs (slice width W = T h, T = Ly > 1) have interface layers of
+// A = Lx T sites, S_ll is A x A (in-plane hopping along x and y), and
+//   k_surface_3d forms P_bot(i), P_top(i) from the factorization's
+//                left-connected g_s (read in binary64), by the backward
+//                recursion G_ss = g_s + t^2 g_s G_{s+1,s+1} g_s and the chains
+//                G_{s,c} = -t g_s G_{s+1,c} carried on the T boundary columns
+//                of each slice c, with 32 x 32 tiles through shared memory
+//                (persistent grid, one (slab, frequency) at a time per CTA);
+//   k_layer_inv_g  inverts the A x A blocks as above (A <= 1024).
 #include "solve_device.cuh"
 #include "tc_tf32.cuh"
 
@@ -334,6 +343,127 @@ __global__ void __launch_bounds__(DY_THREADS) k_surface_g(Geo g, Bufs b) {
 // (i, j != k), which leaves A^-1; pivots come from the sweep operator on the
 // diagonal block (Im S_ll > 0 keeps them away from zero).  The symmetrised
 // inverse is written in the form's precision.
+// C (M x N, row stride ldc) = alpha X Y (+ D), X: M x K, Y: K x N, D: M x N, all in
+// global memory in any of binary64 / complex64 (converted to complex64 on load),
+// 32 x 32 tiles through shared memory; thread (warp lr, lane lc) of 256 forms
+// rows lr + 8 m, column lc of each output tile.  Callers keep C apart from X, Y.
+template <typename TX, typename TY, typename TD>
+__device__ void gmm_c64(cxf_* C, int ldc, const TX* X, int ldx, const TY* Y, int ldy, const TD* D, int ldd,
+                        int M, int N, int K, float alpha, cxf_ (&tx)[32][32], cxf_ (&ty)[32][32]) {
+  auto f32 = [](auto v) -> cxf_ {
+    if constexpr (sizeof(v) == sizeof(cxd)) return cxf_{d2f_bits(v.x), d2f_bits(v.y)};
+    else return v;
+  };
+  const int lr = threadIdx.x >> 5, lc = threadIdx.x & 31;
+  for (int r0 = 0; r0 < M; r0 += 32)
+    for (int c0 = 0; c0 < N; c0 += 32) {
+      cxf_ acc[4] = {};
+      for (int k0 = 0; k0 < K; k0 += 32) {
+        __syncthreads();                     // previous tiles fully read
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const int r = lr + 8 * m;
+          tx[r][lc] = (r0 + r < M && k0 + lc < K) ? f32(X[(size_t)(r0 + r) * ldx + k0 + lc]) : cxf_{0.f, 0.f};
+          ty[r][lc] = (k0 + r < K && c0 + lc < N) ? f32(Y[(size_t)(k0 + r) * ldy + c0 + lc]) : cxf_{0.f, 0.f};
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int k = 0; k < 32; ++k) {
+          const cxf_ yv = ty[k][lc];
+#pragma unroll
+          for (int m = 0; m < 4; ++m) acc[m] = cfma(tx[lr + 8 * m][k], yv, acc[m]);
+        }
+      }
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const int r = r0 + lr + 8 * m, c = c0 + lc;
+        if (r < M && c < N) {
+          cxf_ v = {alpha * acc[m].x, alpha * acc[m].y};
+          if (D) v = v + f32(D[(size_t)r * ldd + c]);
+          C[(size_t)r * ldc + c] = v;
+        }
+      }
+    }
+  __syncthreads();
+}
+
+// Surface Green's functions of 3D slabs (see the top of the file).  Chains are kept
+// as one W x NV matrix per CTA, NV = 2 Lx T columns: [side][slice c][boundary column b]
+// (side 0 top, 1 bottom), updated by one product per step into the other half of
+// the ping-pong pair.  G_{s+1,s+1} and the product g_s G_{s+1,s+1} (complex64) use
+// the factor's per-CTA workspace, free once the factorization has run.
+__global__ void __launch_bounds__(DY_THREADS) k_surface_3d(Geo g, Bufs b, int K, int two) {
+  __shared__ __align__(16) cxf_ tx[32][32];
+  __shared__ __align__(16) cxf_ ty[32][32];
+  const int W = g.W, Lx = g.Lx, T = g.T, A = g.A;
+  const size_t n = (size_t)W * W, NV = (size_t)2 * Lx * T;
+  cxf_* Gd = reinterpret_cast<cxf_*>(b.fwork + (size_t)blockIdx.x * 2 * n);   // G_{s+1,s+1}
+  cxf_* Tm = Gd + n;
+  cxf_* Va = b.lpw + (size_t)blockIdx.x * 2 * W * NV;
+  cxf_* Vb = Va + (size_t)W * NV;
+  const float t = d2f_bits(g.t), t2 = t * t;
+  for (int unit = blockIdx.x; unit < g.p * K; unit += gridDim.x) {
+    const int i = unit % g.p, f = unit / g.p, w = T * g.h[i];
+    const cxd* gs = (two ? b.g64 : reinterpret_cast<const cxd*>(b.g)) + ((size_t)f * g.p + i) * (size_t)Lx * n;
+    cxf_* P[2] = {b.lpt + (((size_t)f * g.p + i) * 2 + 0) * (size_t)A * A,
+                  b.lpt + (((size_t)f * g.p + i) * 2 + 1) * (size_t)A * A};
+    const bool need[2] = {i < g.p - 1, i > 0};
+    // boundary row / column j of slice for side sd and in-plane index b: top rows
+    // (slow row h-1) and bottom rows (slow row 0); its layer index is x + Lx b
+    auto bj = [&](int sd, int bb) { return sd == 0 ? w - T + bb : bb; };
+    cxf_* V = Va;
+    cxf_* Vn = Vb;
+    for (int s = Lx - 1; s >= 0; --s) {
+      const cxd* g_s = gs + (size_t)s * n;
+      if (s < Lx - 1) {
+        // G_{s,c}[:, bnd(c)] = -t g_s G_{s+1,c}[:, bnd(c)] for every c > s, both sides
+        const int c0 = (s + 1) * T, nc = (Lx - 1 - s) * T;
+        for (int sd = 0; sd < 2; ++sd) {
+          if (!need[sd]) continue;
+          const size_t off = (size_t)sd * Lx * T + c0;
+          gmm_c64(Vn + off, (int)NV, g_s, W, V + off, (int)NV, (const cxf_*)nullptr, 0, W, nc, W, -t, tx, ty);
+        }
+        cxf_* tmp = V;
+        V = Vn;
+        Vn = tmp;
+        // P[s][c] = rows bnd(s) of the chains, and its mirror (G is complex symmetric)
+        for (int sd = 0; sd < 2; ++sd) {
+          if (!need[sd]) continue;
+          for (int e = threadIdx.x; e < T * nc; e += DY_THREADS) {
+            const int ra = e / nc, q = e - ra * nc;            // row b_s, chain column (c, b_c)
+            const int c = s + 1 + q / T, bc = q % T;
+            const cxf_ v = V[(size_t)bj(sd, ra) * NV + (size_t)sd * Lx * T + c0 + q];
+            const size_t a = (size_t)s + (size_t)Lx * ra, a2 = (size_t)c + (size_t)Lx * bc;
+            P[sd][a * A + a2] = v;
+            P[sd][a2 * A + a] = v;
+          }
+        }
+      }
+      // G_ss = g_s + t^2 g_s G_{s+1,s+1} g_s  (g_{Lx-1} itself at the end of the slab)
+      if (s == Lx - 1) {
+        for (size_t e = threadIdx.x; e < n; e += DY_THREADS) Gd[e] = cxf_{d2f_bits(g_s[e].x), d2f_bits(g_s[e].y)};
+        __syncthreads();
+      } else {
+        gmm_c64(Tm, W, g_s, W, Gd, W, (const cxf_*)nullptr, 0, W, W, W, 1.f, tx, ty);
+        gmm_c64(Gd, W, Tm, W, g_s, W, g_s, W, W, W, W, t2, tx, ty);
+      }
+      // start the chains of column c = s, and the diagonal block P[s][s]
+      for (int sd = 0; sd < 2; ++sd) {
+        if (!need[sd]) continue;
+        for (int e = threadIdx.x; e < W * T; e += DY_THREADS) {
+          const int r = e / T, bc = e - r * T;
+          V[(size_t)r * NV + (size_t)sd * Lx * T + (size_t)s * T + bc] = Gd[(size_t)r * W + bj(sd, bc)];
+        }
+        for (int e = threadIdx.x; e < T * T; e += DY_THREADS) {
+          const int ra = e / T, bc = e - ra * T;
+          P[sd][((size_t)s + (size_t)Lx * ra) * A + (size_t)s + (size_t)Lx * bc] = Gd[(size_t)bj(sd, ra) * W + bj(sd, bc)];
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
 constexpr int LINV_NB = 32;
 template <typename R>
 __global__ void __launch_bounds__(DY_THREADS) k_layer_inv_g(Geo g, Bufs b) {
@@ -342,7 +472,9 @@ __global__ void __launch_bounds__(DY_THREADS) k_layer_inv_g(Geo g, Bufs b) {
   __shared__ __align__(16) cxf_ Y[LINV_NB * LINV_NB];
   __shared__ cxf_ prow[LINV_NB], fcol[LINV_NB];
   constexpr int NB = LINV_NB;
-  const int l = blockIdx.x, f = blockIdx.y, Lx = g.Lx;
+  // the layer has A = Lx T sites (T = 1 in 2D), layer index a = x + Lx y; below,
+  // "Lx" is the matrix dimension A
+  const int l = blockIdx.x, f = blockIdx.y, Lx = g.A, lx = g.Lx;
   const size_t n2 = (size_t)Lx * Lx;
   cxf_* A = b.lpt + (((size_t)f * g.p + l) * 2 + 0) * n2;          // P_top(l), overwritten
   const cxf_* Pb = b.lpt + (((size_t)f * g.p + l + 1) * 2 + 1) * n2;
@@ -353,8 +485,8 @@ __global__ void __launch_bounds__(DY_THREADS) k_layer_inv_g(Geo g, Bufs b) {
     if (r == c) {
       const cxd d = dyson_diag(g, b, f, r + g.A * g.ylayer[l]);
       v = cxf_{d2f_bits(d.x), d2f_bits(d.y)};
-    } else if (r == c + 1 || c == r + 1) {
-      v = cxf_{t, 0.f};
+    } else if (((r == c + 1 || c == r + 1) && r / lx == c / lx) || r == c + lx || c == r + lx) {
+      v = cxf_{t, 0.f};                                             // in-plane neighbours along x and y
     }
     A[e] = cfma(cxf_{-t2, 0.f}, A[e] + Pb[e], v);
   }
@@ -482,6 +614,12 @@ static size_t surface_g_smem() { return (3 * 32 * 32 + 2 * 32 + DY_WARPS * 32) *
 
 cudaError_t launch_surface(const Geo& g, const Bufs& b, int K, cudaStream_t st) {
   if (!g.lpre) return cudaSuccess;
+  if (g.T > 1) {                           // 3D slabs: persistent grid over (slab, frequency)
+    if (!b.lpw || !b.fwork || g.W <= DY_MAXW_SMEM || g.A > DY_LPRE_MAXLX_G) return cudaErrorInvalidValue;
+    const int units = g.p * K;
+    k_surface_3d<<<units < DY_FACTOR_CTAS ? units : DY_FACTOR_CTAS, DY_THREADS, 0, st>>>(g, b, K, b.g64 ? 1 : 0);
+    return cudaGetLastError();
+  }
   if (g.W > SURF_MAXW || g.Lx > DY_LPRE_MAXLX_G) return cudaErrorInvalidValue;
   if (g.Lx > DY_LPRE_MAXLX) {
     if (g.W != 32 || !b.lpv) return cudaErrorInvalidValue;
@@ -504,7 +642,7 @@ cudaError_t launch_surface(const Geo& g, const Bufs& b, int K, cudaStream_t st) 
 template <typename R>
 cudaError_t launch_layer_inv(const Geo& g, const Bufs& b, int K, cudaStream_t st) {
   if (!g.lpre) return cudaSuccess;
-  if (g.Lx > DY_LPRE_MAXLX) {
+  if (g.T > 1 || g.Lx > DY_LPRE_MAXLX) {
     k_layer_inv_g<R><<<dim3(g.p - 1, K), DY_THREADS, 0, st>>>(g, b);
     return cudaGetLastError();
   }

@@ -1164,7 +1164,7 @@ template <typename R>
 __device__ __noinline__ void lpre_apply(const Geo& g, const Bufs& b, int vs, int i, const cx<R>* r,
                                         cx<R>* z) {
   using C = cx<R>;
-  const int Lx = g.Lx;
+  const int Lx = g.A;               // the layer's sites (Lx in 2D, Lx Ly in 3D)
   const C* rsh = r;                 // every thread reads all of r: served by L1
   const C* M = reinterpret_cast<const C*>(b.lpm) + ((size_t)slot_freq(g, vs) * (g.p - 1) + i) * (size_t)Lx * Lx;
   // eight entries of the column in flight per thread before any is used: M is

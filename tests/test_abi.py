@@ -127,7 +127,7 @@ def test_precond_choice_validated(lib):
     assert D.dyson_plan_footprint(g) > 0
     g3 = D.make_geometry((8, 8, 9), p=2, k_max=8, max_freqs=2, precond=D.DYSON_PRECOND_LAYER)
     with pytest.raises(D.DysonError) as e:
-        D.dyson_plan_footprint(g3)                  # 3D slabs: only the banded form
+        D.dyson_plan_footprint(g3)                  # 3D slabs of slice width <= 64: only the banded form
     assert e.value.code == -4
     g.precond = 7
     with pytest.raises(D.DysonError) as e:
@@ -173,3 +173,12 @@ def test_layer_preconditioner_limits(lib):
     g = D.make_geometry((160, 33), p=1, k_max=4, max_freqs=1, precond=D.DYSON_PRECOND_LAYER)
     with pytest.raises(D.DysonError):                    # no interface: nothing to precondition
         D.dyson_plan_footprint(g)
+    # 3D slabs with slices wider than 64 and layers of Lx Ly <= 1024 sites take them too
+    for L, p in (((6, 9, 16), 2), ((4, 16, 17), 2), ((32, 32, 32), 8)):
+        ok = D.make_geometry(L, p=p, k_max=4, max_freqs=1, precond=D.DYSON_PRECOND_LAYER)
+        banded = D.make_geometry(L, p=p, k_max=4, max_freqs=1, precond=D.DYSON_PRECOND_BANDED)
+        assert D.dyson_plan_footprint(ok) > D.dyson_plan_footprint(banded)
+    g = D.make_geometry((33, 32, 32), p=8, k_max=4, max_freqs=1, precond=D.DYSON_PRECOND_LAYER)
+    with pytest.raises(D.DysonError) as e:               # layer of 33 x 32 = 1056 sites
+        D.dyson_plan_footprint(g)
+    assert e.value.code == -4
