@@ -257,13 +257,15 @@ __global__ void __launch_bounds__(DY_THREADS) k_factor(Geo g, Bufs b) {
 // symmetric sweep operator (see gj_invert): the upper triangle only, then
 // negation and mirror.  Step k caches column k (unscaled in prow, scaled by
 // the pivot inverse in fcol, -1/a_kk at fcol[k]) on chip.
-__device__ void gj_invert_global(cxd* A, int W, cxd* prow, cxd* fcol) {
+template <typename R>
+__device__ void gj_invert_global(cx<R>* A, int W, cx<R>* prow, cx<R>* fcol) {
+  using C = cx<R>;
   const int n = W * W;
   for (int k = 0; k < W; ++k) {
     __syncthreads();                         // step k-1 finished by every thread
     for (int e = threadIdx.x; e < W; e += DY_THREADS) {
-      const cxd piv = cinv(A[(size_t)k * W + k]);
-      const cxd a = (e < k) ? A[(size_t)e * W + k] : A[(size_t)k * W + e];
+      const C piv = cinv(A[(size_t)k * W + k]);
+      const C a = (e < k) ? A[(size_t)e * W + k] : A[(size_t)k * W + e];
       prow[e] = a;
       fcol[e] = (e == k) ? -piv : a * piv;
     }
@@ -291,25 +293,27 @@ __device__ void gj_invert_global(cxd* A, int W, cxd* prow, cxd* fcol) {
 // C = base + scale * X Y for global W x W matrices (base may be null: C = X Y),
 // in 32 x 32 output tiles staged through shared memory; W need not be a
 // multiple of 32.  C must not alias X or Y.
-__device__ void gmem_matmul(cxd* C, const cxd* X, const cxd* Y, const cxd* base, double scale,
-                            int W, cxd (*tx)[32], cxd (*ty)[32]) {
+template <typename R>
+__device__ void gmem_matmul(cx<R>* C, const cx<R>* X, const cx<R>* Y, const cx<R>* base, R scale,
+                            int W, cx<R> (*tx)[32], cx<R> (*ty)[32]) {
+  using CC = cx<R>;
   const int tid = threadIdx.x, lc = tid & 31, lr = tid >> 5;   // 8 row groups x 32 columns
   const int nt = (W + 31) / 32;
   for (int tile = 0; tile < nt * nt; ++tile) {
     const int r0 = (tile / nt) * 32, c0 = (tile % nt) * 32;
-    cxd acc[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    CC acc[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
     for (int k0 = 0; k0 < W; k0 += 32) {
       __syncthreads();                       // previous tiles fully read
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
         const int r = lr + 8 * m;
-        tx[r][lc] = (r0 + r < W && k0 + lc < W) ? X[(size_t)(r0 + r) * W + k0 + lc] : cxd{0, 0};
-        ty[r][lc] = (k0 + r < W && c0 + lc < W) ? Y[(size_t)(k0 + r) * W + c0 + lc] : cxd{0, 0};
+        tx[r][lc] = (r0 + r < W && k0 + lc < W) ? X[(size_t)(r0 + r) * W + k0 + lc] : CC{0, 0};
+        ty[r][lc] = (k0 + r < W && c0 + lc < W) ? Y[(size_t)(k0 + r) * W + c0 + lc] : CC{0, 0};
       }
       __syncthreads();
 #pragma unroll 8
       for (int k = 0; k < 32; ++k) {
-        const cxd yv = ty[k][lc];
+        const CC yv = ty[k][lc];
 #pragma unroll
         for (int m = 0; m < 4; ++m) acc[m] = cfma(tx[lr + 8 * m][k], yv, acc[m]);
       }
@@ -326,48 +330,53 @@ __device__ void gmem_matmul(cxd* C, const cxd* X, const cxd* Y, const cxd* base,
   __syncthreads();
 }
 
-template <typename S>
+// R: the recursion's arithmetic, binary64 (FP64 form) or double-float (mixed
+// form, R12: on the FP32 pipe), stored in b.g (FP64 form) or b.g64 (mixed: the
+// double-float factors, beside their complex64 copy in b.g for the sweeps).
+template <typename R, typename S>
 __global__ void __launch_bounds__(DY_THREADS) k_factor_big(Geo g, Bufs b, int K) {
-  __shared__ cxd prow[DY_MAXW], fcol[DY_MAXW];
-  __shared__ cxd tx[32][32], ty[32][32];
+  using C = cx<R>;
+  __shared__ C prow[DY_MAXW], fcol[DY_MAXW];
+  __shared__ C tx[32][32], ty[32][32];
   constexpr bool two = sizeof(S) != sizeof(double);
+  static_assert(sizeof(C) == sizeof(cxd), "factor storage holds 16 bytes per entry");
   const int W = g.W, Lx = g.Lx, T = g.T;
   const size_t n = (size_t)W * W;
-  const double t = g.t, t2 = g.t * g.t;
-  cxd* Gw = b.fwork + (size_t)blockIdx.x * 2 * n;   // G_{s+1,s+1}
-  cxd* Pw = Gw + n;                                  // g_s G_{s+1,s+1}
+  const R t = (R)g.t, t2 = (R)(g.t * g.t);
+  C* Gw = reinterpret_cast<C*>(b.fwork) + (size_t)blockIdx.x * 2 * n;   // G_{s+1,s+1}
+  C* Pw = Gw + n;                                                    // g_s G_{s+1,s+1}
   for (int unit = blockIdx.x; unit < g.p * K; unit += gridDim.x) {
     const int i = unit % g.p, kf = unit / g.p, w = T * g.h[i];
     const size_t uoff = ((size_t)kf * g.p + i) * (size_t)Lx * n;
-    cxd* gout = (two ? b.g64 : reinterpret_cast<cxd*>(b.g)) + uoff;
+    C* gout = reinterpret_cast<C*>(two ? b.g64 : b.g) + uoff;
     cx<S>* gsw = reinterpret_cast<cx<S>*>(b.g) + uoff;
     cxd* dB = b.diagB + (size_t)kf * g.Ndd + (size_t)i * Lx * W;
     // forward: g_s = (D_s - t^2 g_{s-1})^-1, formed and inverted in place
     for (int s = 0; s < Lx; ++s) {
-      cxd* A = gout + (size_t)s * n;
-      const cxd* Ap = A - n;
+      C* A = gout + (size_t)s * n;
+      const C* Ap = A - n;
       __syncthreads();                       // g_{s-1} complete
       for (int e = threadIdx.x; e < (int)n; e += DY_THREADS) {
         const int r = e / W, c = e - r * W;
-        cxd v = {0, 0};
+        C v = {0, 0};
         if (r < w && c < w) {
           if (s > 0) v = (-t2) * Ap[e];
           if (r == c) {
-            v = v + dyson_diag(g, b, kf, sub_nat(g, i, s, r));
-          } else if (slice_adjacent<double>(r, c, T)) {
+            v = v + cconv<R>(dyson_diag(g, b, kf, sub_nat(g, i, s, r)));
+          } else if (slice_adjacent<R>(r, c, T)) {
             v.x += t;
           }
         } else if (r == c) {
-          v = cxd{1, 0};                     // padding: identity, inverted to itself
+          v = C{1, 0};                       // padding: identity, inverted to itself
         }
         A[e] = v;
       }
-      gj_invert_global(A, W, prow, fcol);
+      gj_invert_global<R>(A, W, prow, fcol);
       for (int e = threadIdx.x; e < (int)n; e += DY_THREADS) {
         const int r = e / W, c = e - r * W;
-        cxd v = A[e];
+        C v = A[e];
         if (r >= w || c >= w) {
-          v = cxd{0, 0};
+          v = C{0, 0};
           A[e] = v;
         }
         if (two) gsw[(size_t)s * n + e] = cconv<S>(v);
@@ -375,21 +384,21 @@ __global__ void __launch_bounds__(DY_THREADS) k_factor_big(Geo g, Bufs b, int K)
     }
     __syncthreads();
     // backward: Gw holds G_{s+1,s+1}
-    const cxd* glast = gout + (size_t)(Lx - 1) * n;
+    const C* glast = gout + (size_t)(Lx - 1) * n;
     for (int e = threadIdx.x; e < (int)n; e += DY_THREADS) Gw[e] = glast[e];
     for (int r = threadIdx.x; r < W; r += DY_THREADS)
-      dB[(size_t)(Lx - 1) * W + r] = (r < w) ? glast[(size_t)r * W + r] : cxd{0, 0};
+      dB[(size_t)(Lx - 1) * W + r] = (r < w) ? cconv<double>(glast[(size_t)r * W + r]) : cxd{0, 0};
     for (int s = Lx - 2; s >= 0; --s) {
-      const cxd* gs = gout + (size_t)s * n;
-      gmem_matmul(Pw, gs, Gw, nullptr, 0.0, W, tx, ty);   // g_s G_{s+1}
-      if (b.offB) {                                        // diag of G_{s,s+1} = -t g_s G_{s+1}
+      const C* gs = gout + (size_t)s * n;
+      gmem_matmul<R>(Pw, gs, Gw, nullptr, R(0), W, tx, ty);   // g_s G_{s+1}
+      if (b.offB) {                                           // diag of G_{s,s+1} = -t g_s G_{s+1}
         cxd* oB = b.offB + ((size_t)kf * g.p + i) * (size_t)Lx * W + (size_t)s * W;
         for (int r = threadIdx.x; r < W; r += DY_THREADS)
-          oB[r] = (r < w) ? (-t) * Pw[(size_t)r * W + r] : cxd{0, 0};
+          oB[r] = (r < w) ? cconv<double>((-t) * Pw[(size_t)r * W + r]) : cxd{0, 0};
       }
-      gmem_matmul(Gw, Pw, gs, gs, t2, W, tx, ty);         // g_s + t^2 g_s G_{s+1} g_s
+      gmem_matmul<R>(Gw, Pw, gs, gs, t2, W, tx, ty);          // g_s + t^2 g_s G_{s+1} g_s
       for (int r = threadIdx.x; r < W; r += DY_THREADS)
-        dB[(size_t)s * W + r] = (r < w) ? Gw[(size_t)r * W + r] : cxd{0, 0};
+        dB[(size_t)s * W + r] = (r < w) ? cconv<double>(Gw[(size_t)r * W + r]) : cxd{0, 0};
     }
     if (i == g.p - 1) {
       cxd* dI = b.diagB + (size_t)kf * g.Ndd + g.ifc_off;
@@ -475,11 +484,16 @@ cudaError_t launch_factor(const Geo& g, const Bufs& b, int K, cudaStream_t st) {
     if (e != cudaSuccess) return e;
   }
   if (g.W > DY_MAXW_SMEM) {
-    // wide slices: FP64 recursion in global memory (both forms recurse in FP64)
-    if (sizeof(R) != sizeof(double) || g.W > DY_MAXW || !b.fwork) return cudaErrorInvalidValue;
-    int units = g.p * K;
-    k_factor_big<S><<<units < DY_FACTOR_CTAS ? units : DY_FACTOR_CTAS, DY_THREADS, 0, st>>>(g, b, K);
-    return cudaGetLastError();
+    // wide slices: the recursion in global memory (binary64, or double-float in the
+    // mixed form)
+    if constexpr (sizeof(cx<R>) == sizeof(cxd)) {
+      if (g.W > DY_MAXW || !b.fwork) return cudaErrorInvalidValue;
+      int units = g.p * K;
+      k_factor_big<R, S><<<units < DY_FACTOR_CTAS ? units : DY_FACTOR_CTAS, DY_THREADS, 0, st>>>(g, b, K);
+      return cudaGetLastError();
+    } else {
+      return cudaErrorInvalidValue;
+    }
   }
   size_t smem = (3 * (size_t)g.W * g.W + 6 * (size_t)g.W) * sizeof(cx<R>);
   cudaError_t e = raise_smem_limit((const void*)k_factor<R, S>, smem);

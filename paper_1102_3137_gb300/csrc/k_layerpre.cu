@@ -36,8 +36,11 @@
 //                recursion G_ss = g_s + t^2 g_s G_{s+1,s+1} g_s and the chains
 //                G_{s,c} = -t g_s G_{s+1,c} carried on the T boundary columns
 //                of each slice c, with 32 x 32 tiles through shared memory
-//                (persistent grid, one (slab, frequency) at a time per CTA);
+//                multiplied on the tensor cores (3xTF32; persistent grid, one
+//                (slab, frequency) at a time per CTA);
 //   k_layer_inv_g  inverts the A x A blocks as above (A <= 1024).
+#include <type_traits>
+
 #include "solve_device.cuh"
 #include "tc_tf32.cuh"
 
@@ -345,19 +348,24 @@ __global__ void __launch_bounds__(DY_THREADS) k_surface_g(Geo g, Bufs b) {
 // inverse is written in the form's precision.
 // C (M x N, row stride ldc) = alpha X Y (+ D), X: M x K, Y: K x N, D: M x N, all in
 // global memory in any of binary64 / complex64 (converted to complex64 on load),
-// 32 x 32 tiles through shared memory; thread (warp lr, lane lc) of 256 forms
-// rows lr + 8 m, column lc of each output tile.  Callers keep C apart from X, Y.
+// 32 x 32 tiles staged through shared memory and multiplied on the tensor cores
+// (3xTF32, binary32 accuracy): warp w forms the 16 x 8 sub-tile at rows 16 (w / 4),
+// columns 8 (w % 4) of each output tile.  Callers keep C apart from X, Y.
 template <typename TX, typename TY, typename TD>
 __device__ void gmm_c64(cxf_* C, int ldc, const TX* X, int ldx, const TY* Y, int ldy, const TD* D, int ldd,
                         int M, int N, int K, float alpha, cxf_ (&tx)[32][32], cxf_ (&ty)[32][32]) {
   auto f32 = [](auto v) -> cxf_ {
-    if constexpr (sizeof(v) == sizeof(cxd)) return cxf_{d2f_bits(v.x), d2f_bits(v.y)};
+    using V = decltype(v);
+    if constexpr (std::is_same_v<V, cxd>) return cxf_{d2f_bits(v.x), d2f_bits(v.y)};
+    else if constexpr (std::is_same_v<V, cx<dfl>>) return cxf_{v.x.hi + v.x.lo, v.y.hi + v.y.lo};
     else return v;
   };
+  static_assert(DY_THREADS == 256, "eight 16 x 8 tensor-core tiles per 32 x 32 output tile");
   const int lr = threadIdx.x >> 5, lc = threadIdx.x & 31;
+  const int tm = 16 * (lr >> 2), tn = 8 * (lr & 3);
   for (int r0 = 0; r0 < M; r0 += 32)
     for (int c0 = 0; c0 < N; c0 += 32) {
-      cxf_ acc[4] = {};
+      tc::CTile acc = {};
       for (int k0 = 0; k0 < K; k0 += 32) {
         __syncthreads();                     // previous tiles fully read
 #pragma unroll
@@ -367,20 +375,16 @@ __device__ void gmm_c64(cxf_* C, int ldc, const TX* X, int ldx, const TY* Y, int
           ty[r][lc] = (k0 + r < K && c0 + lc < N) ? f32(Y[(size_t)(k0 + r) * ldy + c0 + lc]) : cxf_{0.f, 0.f};
         }
         __syncthreads();
-#pragma unroll 8
-        for (int k = 0; k < 32; ++k) {
-          const cxf_ yv = ty[k][lc];
-#pragma unroll
-          for (int m = 0; m < 4; ++m) acc[m] = cfma(tx[lr + 8 * m][k], yv, acc[m]);
-        }
+        tc::cgemm_tile_3xtf32(acc, &tx[0][0], &ty[0][0], 32, tm, tn);
       }
 #pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        const int r = r0 + lr + 8 * m, c = c0 + lc;
-        if (r < M && c < N) {
-          cxf_ v = {alpha * acc[m].x, alpha * acc[m].y};
-          if (D) v = v + f32(D[(size_t)r * ldd + c]);
-          C[(size_t)r * ldc + c] = v;
+      for (int e = 0; e < 4; ++e) {
+        int r, c;
+        tc::tile_pos(e, tm, tn, r, c);
+        if (r0 + r < M && c0 + c < N) {
+          cxf_ v = {alpha * acc.re[e], alpha * acc.im[e]};
+          if (D) v = v + f32(D[(size_t)(r0 + r) * ldd + c0 + c]);
+          C[(size_t)(r0 + r) * ldc + c0 + c] = v;
         }
       }
     }
@@ -392,7 +396,8 @@ __device__ void gmm_c64(cxf_* C, int ldc, const TX* X, int ldx, const TY* Y, int
 // (side 0 top, 1 bottom), updated by one product per step into the other half of
 // the ping-pong pair.  G_{s+1,s+1} and the product g_s G_{s+1,s+1} (complex64) use
 // the factor's per-CTA workspace, free once the factorization has run.
-__global__ void __launch_bounds__(DY_THREADS) k_surface_3d(Geo g, Bufs b, int K, int two) {
+template <typename FT>   // the factors' element: binary64 (FP64 form) or double-float (mixed)
+__global__ void __launch_bounds__(DY_THREADS) k_surface_3d(Geo g, Bufs b, int K) {
   __shared__ __align__(16) cxf_ tx[32][32];
   __shared__ __align__(16) cxf_ ty[32][32];
   const int W = g.W, Lx = g.Lx, T = g.T, A = g.A;
@@ -404,7 +409,7 @@ __global__ void __launch_bounds__(DY_THREADS) k_surface_3d(Geo g, Bufs b, int K,
   const float t = d2f_bits(g.t), t2 = t * t;
   for (int unit = blockIdx.x; unit < g.p * K; unit += gridDim.x) {
     const int i = unit % g.p, f = unit / g.p, w = T * g.h[i];
-    const cxd* gs = (two ? b.g64 : reinterpret_cast<const cxd*>(b.g)) + ((size_t)f * g.p + i) * (size_t)Lx * n;
+    const FT* gs = reinterpret_cast<const FT*>(b.g64 ? (const void*)b.g64 : b.g) + ((size_t)f * g.p + i) * (size_t)Lx * n;
     cxf_* P[2] = {b.lpt + (((size_t)f * g.p + i) * 2 + 0) * (size_t)A * A,
                   b.lpt + (((size_t)f * g.p + i) * 2 + 1) * (size_t)A * A};
     const bool need[2] = {i < g.p - 1, i > 0};
@@ -414,7 +419,7 @@ __global__ void __launch_bounds__(DY_THREADS) k_surface_3d(Geo g, Bufs b, int K,
     cxf_* V = Va;
     cxf_* Vn = Vb;
     for (int s = Lx - 1; s >= 0; --s) {
-      const cxd* g_s = gs + (size_t)s * n;
+      const FT* g_s = gs + (size_t)s * n;
       if (s < Lx - 1) {
         // G_{s,c}[:, bnd(c)] = -t g_s G_{s+1,c}[:, bnd(c)] for every c > s, both sides
         const int c0 = (s + 1) * T, nc = (Lx - 1 - s) * T;
@@ -441,7 +446,10 @@ __global__ void __launch_bounds__(DY_THREADS) k_surface_3d(Geo g, Bufs b, int K,
       }
       // G_ss = g_s + t^2 g_s G_{s+1,s+1} g_s  (g_{Lx-1} itself at the end of the slab)
       if (s == Lx - 1) {
-        for (size_t e = threadIdx.x; e < n; e += DY_THREADS) Gd[e] = cxf_{d2f_bits(g_s[e].x), d2f_bits(g_s[e].y)};
+        for (size_t e = threadIdx.x; e < n; e += DY_THREADS) {
+          if constexpr (std::is_same_v<FT, cxd>) Gd[e] = cxf_{d2f_bits(g_s[e].x), d2f_bits(g_s[e].y)};
+          else Gd[e] = cxf_{g_s[e].x.hi + g_s[e].x.lo, g_s[e].y.hi + g_s[e].y.lo};
+        }
         __syncthreads();
       } else {
         gmm_c64(Tm, W, g_s, W, Gd, W, (const cxf_*)nullptr, 0, W, W, W, 1.f, tx, ty);
@@ -617,7 +625,9 @@ cudaError_t launch_surface(const Geo& g, const Bufs& b, int K, cudaStream_t st) 
   if (g.T > 1) {                           // 3D slabs: persistent grid over (slab, frequency)
     if (!b.lpw || !b.fwork || g.W <= DY_MAXW_SMEM || g.A > DY_LPRE_MAXLX_G) return cudaErrorInvalidValue;
     const int units = g.p * K;
-    k_surface_3d<<<units < DY_FACTOR_CTAS ? units : DY_FACTOR_CTAS, DY_THREADS, 0, st>>>(g, b, K, b.g64 ? 1 : 0);
+    const int grid = units < DY_FACTOR_CTAS ? units : DY_FACTOR_CTAS;
+    if (b.g64) k_surface_3d<cx<dfl>><<<grid, DY_THREADS, 0, st>>>(g, b, K);   // mixed: double-float factors
+    else k_surface_3d<cxd><<<grid, DY_THREADS, 0, st>>>(g, b, K);
     return cudaGetLastError();
   }
   if (g.W > SURF_MAXW || g.Lx > DY_LPRE_MAXLX_G) return cudaErrorInvalidValue;
