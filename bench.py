@@ -195,12 +195,15 @@ class Clocks:
                     power_w_max=max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit()))
 
 
+REC_MIN_SITES = 1024
+
+
 def side_measurements(a, dev, stream):
     """The 128x128, 64-frequency workload (p = 4, k = 32) beside the headline: its own
     batched throughput in the headline's form and in plain FP64 (with the error between
     them), one frequency per launch against the batch, the exact diagonal (p = 1) and
-    the low-rank truncation error against it, block Lanczos, and the complex64 stencil
-    SpMV on a batch far larger than L2."""
+    the low-rank truncation error against it, block Lanczos, the recursive
+    decomposition, and the complex64 stencil SpMV on a batch far larger than L2."""
     import numpy as np
     import torch
     from paper_1102_3137_gb300 import dyson as D
@@ -280,6 +283,29 @@ def side_measurements(a, dev, stream):
                                  form=a.form, status_flags=sorted(set(stb.cpu().tolist())),
                                  truncation_error=dict(max=float(tb.max()), median=float(np.median(tb))))
     pb.close()
+    # the recursive decomposition (Sec. 2.3, last paragraph; domains alternating
+    # (2,1), (1,2), ...) down to boxes of 1024 sites, the same rank cap in every
+    # box, in the headline form: throughput and truncation error against the exact
+    # diagonal
+    rp = D.RecursivePlan(w.L, w.t, w.mu, w.k, prec, max_freqs=w.K, min_sites=REC_MIN_SITES,
+                         first_cut=D.DYSON_CUT_X)
+    outr = torch.zeros_like(out)
+    str_ = torch.zeros_like(st)
+    D.dyson_recursive_solve(rp.handle, w.K, w.N, om, Vd, sg, qd, outr, str_, ss)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(nrep):
+        D.dyson_recursive_solve(rp.handle, w.K, w.N, om, Vd, sg, qd, outr, str_, ss)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_r = e0.elapsed_time(e1) / nrep
+    trr = np.abs(outr.cpu().numpy() - exact) / np.abs(exact)
+    info = rp.info()
+    side["recursive"] = dict(min_sites=REC_MIN_SITES, levels=info["levels"], boxes=info["boxes"],
+                             leaves=info["leaves"], value=w.K * w.N / (ms_r / 1e3), ms_per_step=ms_r,
+                             form=a.form, status_flags=sorted(set(str_.cpu().tolist())),
+                             truncation_error=dict(max=float(trr.max()), median=float(np.median(trr))))
+    rp.close()
     # the complex64 stencil SpMV (row a1, y = H(i w_k) x) on a batch far larger than L2:
     # algorithmic 32 B per site-frequency (x c64 8 + y c64 8 + Sigma c128 16; V stays in L2)
     Ks = 4096

@@ -262,6 +262,66 @@ int dyson_xmatvec(dyson_plan plan, int K, const double* omega, const double* V,
                   const double* sigma, const double* q, double* u, int mem_kind, void* stream);
 
 /*
+ * Recursive decomposition (Sec. 2.3, last paragraph), square lattices (dim 2):
+ * the lattice is cut in two by one interface line, each half across the other
+ * axis, and so on, the number of domains alternating (d_x, d_y) = (2, 1),
+ * (1, 2), (2, 1), ... level by level (first_cut DYSON_CUT_X; DYSON_CUT_Y
+ * starts with (1, 2)).  A box (the principal submatrix H_box of H on its
+ * sites, open at its edges) gets
+ *     [diag of each half's inverse, by the same rule one level down; 0 on the
+ *      cut line] + diag(Q_k T_k Q_k^T),
+ * the rank-k Lanczos approximation (Eq. 10) of X_box = H_box^-1 -
+ * blkdiag(H_1^-1, H_2^-1, 0) (Eqs. 5-8 on the box) started from q1 restricted
+ * to the box.  The line sits at the middle site of the cut axis; with an even
+ * extent the half before it is one site shorter.  An axis shorter than 3
+ * sites is not cut (the other one is); boxes of at most min_sites sites, or
+ * shorter than 3 along both axes, are inverted exactly.  The paper states
+ * only the alternation; these rules are this library's reading.
+ *
+ * dyson_recursive_plan_create: from geom it reads L (dim must be 2), t, mu,
+ * k_max (the rank cap of every box), precision, eta, krylov_tol/maxit,
+ * refine_tol/max, precond, freq_groups and max_freqs; p and block_size are
+ * not used (block_size must be 0 or 1).  It builds the box tree and one
+ * ordinary plan per box shape and stream (streams: boxes of one level run
+ * concurrently on up to this many streams, 0 = 4, at most 16), all device
+ * memory allocated here.  Every box must fit an ordinary plan: its slow-axis
+ * extent (the cut axis) at most 641, its leaves' shorter extent at most 320.
+ * Errors: DYSON_E_BAD_ARG (dim != 2, min_sites < 1, first_cut, block_size,
+ * streams, k_max or max_freqs out of range), DYSON_E_UNSUPPORTED or
+ * DYSON_E_OOM from a box plan (the message names the box shape).
+ *
+ * dyson_recursive_solve: diag(G) for K <= max_freqs frequencies, arguments as
+ * dyson_solve (q1 [N] real).  status[K]: DYSON_ST_NO_CONVERGENCE, _BREAKDOWN
+ * and _WAIT_TIMEOUT of any box OR-ed; DYSON_ST_TERMINATED only when every box
+ * terminated, in which case the result is the exact diagonal.  With
+ * DYSON_MEM_DEVICE the call only enqueues on `stream`; the plan's own streams
+ * wait for it and it waits for them.  Calls on one recursive plan must not
+ * overlap on the GPU (they share the box plans).
+ *
+ * dyson_recursive_plan_info: levels of the tree, internal boxes, leaves,
+ * ordinary plans created and device bytes held (each pointer may be NULL).
+ *
+ * dyson_recursive_boxes: the box tree alone, host only (no GPU needed).  *n
+ * receives the number of boxes; if boxes is not NULL it receives, per box,
+ * level by level, 8 ints: x0, y0, nx, ny (origin and extents), level, leaf
+ * (1: inverted exactly), the cut axis (0: the line is the column x = line,
+ * 1: the row y = line; -1 for a leaf) and the line's coordinate (-1 for a
+ * leaf).  Call once with boxes = NULL to learn *n.
+ */
+#define DYSON_CUT_X 0
+#define DYSON_CUT_Y 1
+typedef struct dyson_rplan_s* dyson_rplan;
+int dyson_recursive_plan_create(const dyson_geometry* geom, int min_sites, int first_cut, int streams,
+                                dyson_rplan* out);
+int dyson_recursive_plan_destroy(dyson_rplan rplan);
+int dyson_recursive_boxes(const dyson_geometry* geom, int min_sites, int first_cut, int* n, int* boxes);
+int dyson_recursive_plan_info(dyson_rplan rplan, int* levels, int* boxes, int* leaves, int* plans,
+                              size_t* bytes);
+int dyson_recursive_solve(dyson_rplan rplan, int K, const double* omega, const double* V,
+                          const double* sigma, const double* q1, double* diagG, int* status,
+                          int mem_kind, void* stream);
+
+/*
  * Serving: continuous batching of Dyson solves from many IDMFT clients (each
  * self-consistency iteration needs all frequencies again with a new
  * self-energy, Sec. 3).  Requests are admitted in arrival order as soon as the

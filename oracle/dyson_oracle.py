@@ -540,7 +540,7 @@ def lowrank_diag_block(L, periodic, t, mu, V, sigma_k, omega_k, Q1, p: int, k_ma
     return res
 
 
-def recursive_diag(L, t, z, q1, k_max: int, min_sites: int = 64, first_cut: str = "x"):
+def recursive_diag(L, t, z, q1, k_max: int, min_sites: int = 64, first_cut: str = "x", boxes=None):
     """diag(H^-1) by the recursive decomposition of Sec. 2.3 (end): 2D only.
 
     A box of the lattice (its principal submatrix of H, open at the box edges) is
@@ -551,7 +551,10 @@ def recursive_diag(L, t, z, q1, k_max: int, min_sites: int = 64, first_cut: str 
     H_2^-1, 0) (Eqs. 5-9 applied to the box), with the start vector q1
     restricted to the box.  Boxes of at most min_sites sites are inverted
     directly.  With k_max past every level's closure the result is exact.
-    Returns the diagonal in natural order.
+    Returns the diagonal in natural order.  If `boxes` is a list, every box
+    visited is appended to it as (x0, y0, nx, ny, level, leaf, axis, line): the
+    line is the column x = line (axis 0) or the row y = line (axis 1); axis and
+    line are -1 for a leaf.
     """
     Lx, Ly = L
     z = np.asarray(z, dtype=np.complex128)
@@ -563,12 +566,14 @@ def recursive_diag(L, t, z, q1, k_max: int, min_sites: int = 64, first_cut: str 
     def box_H(idx, nx, ny):
         return dense_H((nx, ny), (False, False), t, z[idx])
 
-    def rec(x0, x1, y0, y1, cut):
+    def rec(x0, x1, y0, y1, cut, level=0):
         nx, ny = x1 - x0 + 1, y1 - y0 + 1
         idx = sites(x0, x1, y0, y1)
         Hb = box_H(idx, nx, ny)
         if idx.size <= min_sites or (cut == "x" and nx < 3) or (cut == "y" and ny < 3):
             if idx.size <= min_sites or (nx < 3 and ny < 3):
+                if boxes is not None:
+                    boxes.append((x0, y0, nx, ny, level, 1, -1, -1))
                 return idx, np.diag(np.linalg.inv(Hb))
             cut = "y" if cut == "x" else "x"
         if cut == "x":
@@ -577,11 +582,13 @@ def recursive_diag(L, t, z, q1, k_max: int, min_sites: int = 64, first_cut: str 
         else:
             ym = (y0 + y1) // 2
             halves = [(x0, x1, y0, ym - 1), (x0, x1, ym + 1, y1)]
+        if boxes is not None:
+            boxes.append((x0, y0, nx, ny, level, 0, 0, xm) if cut == "x" else (x0, y0, nx, ny, level, 0, 1, ym))
         nxt = "y" if cut == "x" else "x"
         pos = {int(v): k for k, v in enumerate(idx)}
         parts = []
         for h in halves:
-            hidx, hdiag = rec(*h, nxt)
+            hidx, hdiag = rec(*h, nxt, level + 1)
             parts.append((np.array([pos[int(v)] for v in hidx]), hidx, hdiag))
         d = np.zeros(idx.size, dtype=np.complex128)
         Hh = [box_H(hidx, h[1] - h[0] + 1, h[3] - h[2] + 1) for (_, hidx, _), h in zip(parts, halves)]

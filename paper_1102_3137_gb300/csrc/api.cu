@@ -751,6 +751,42 @@ int dyson_internal_solve_enqueue_segs(dyson_plan p, int nseg, const SolveSeg* se
 
 size_t dyson_internal_plan_bytes(dyson_plan p) { return p ? p->bytes : 0; }
 
+int dyson_internal_plan_dev(dyson_plan p, PlanDev* out) {
+  int rc;
+  if ((rc = check_plan(p))) return rc;
+  out->omega = at<double>(p, B_OMEGA);
+  out->V = at<double>(p, B_V);
+  out->sigma = at<double>(p, B_SIGMA);
+  out->q1 = at<double>(p, B_Q1);
+  out->acc = reinterpret_cast<const double*>(p->b.acc);
+  out->diagB = reinterpret_cast<const double*>(p->b.diagB);
+  out->dd2nat = p->b.dd2nat;
+  out->status = p->status_d;
+  out->Ndd = p->g.Ndd;
+  out->N = p->g.N;
+  return DYSON_OK;
+}
+
+int dyson_internal_solve_resident(dyson_plan p, int K, void* stream) {
+  int rc;
+  if ((rc = check_plan(p)) || (rc = check_K(p, K))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!p->tuned && (rc = autotune(p, K, s))) return rc;
+  if (p->use_graph) {
+    cudaGraphExec_t ex;
+    if ((rc = get_graph(p, K, &ex))) return rc;
+    CK(cudaGraphLaunch(ex, s));
+    return DYSON_OK;
+  }
+  return enqueue_solve(p, K, s, false);
+}
+
+int dyson_internal_factor_resident(dyson_plan p, int K, void* stream) {
+  int rc;
+  if ((rc = check_plan(p)) || (rc = check_K(p, K))) return rc;
+  return enqueue_factor(p, K, (cudaStream_t)stream);
+}
+
 extern "C" {
 
 int dyson_solve(dyson_plan p, int K, const double* omega, const double* V, const double* sigma,

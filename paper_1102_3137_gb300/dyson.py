@@ -44,6 +44,8 @@ DYSON_ST_TERMINATED = 1
 DYSON_ST_BREAKDOWN = 2
 DYSON_ST_NO_CONVERGENCE = 4
 DYSON_ST_WAIT_TIMEOUT = 16
+DYSON_CUT_X = 0
+DYSON_CUT_Y = 1
 
 
 class dyson_geometry(C.Structure):
@@ -117,6 +119,11 @@ def load(path: str = LIB_PATH):
         "dyson_poll": ([P, C.c_uint64, C.POINTER(I)], I),
         "dyson_wait": ([P, C.c_uint64, C.POINTER(C.c_double), C.POINTER(C.c_double)], I),
         "dyson_server_stats": ([P, C.POINTER(dyson_server_stats_t)], I),
+        "dyson_recursive_plan_create": ([C.POINTER(dyson_geometry), I, I, I, C.POINTER(P)], I),
+        "dyson_recursive_plan_destroy": ([P], I),
+        "dyson_recursive_plan_info": ([P, P, P, P, P, P], I),
+        "dyson_recursive_solve": ([P, I, P, P, P, P, P, P, I, P], I),
+        "dyson_recursive_boxes": ([C.POINTER(dyson_geometry), I, I, C.POINTER(I), P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -417,6 +424,77 @@ def dyson_server_stats(server):
     st = dyson_server_stats_t()
     _check(load().dyson_server_stats(server, C.byref(st)))
     return {f: getattr(st, f) for f, _ in st._fields_}
+
+
+def dyson_recursive_plan_create(geom, min_sites, first_cut=DYSON_CUT_X, streams=0):
+    h = C.c_void_p()
+    _check(load().dyson_recursive_plan_create(C.byref(geom), int(min_sites), int(first_cut), int(streams),
+                                              C.byref(h)))
+    return h
+
+
+def dyson_recursive_boxes(geom, min_sites, first_cut=DYSON_CUT_X):
+    """Box tree of the recursive decomposition, host only: int array [n][8] of
+    (x0, y0, nx, ny, level, leaf, cut axis (0 x, 1 y) or -1, cut line coordinate or -1)."""
+    lib = load()
+    n = C.c_int()
+    _check(lib.dyson_recursive_boxes(C.byref(geom), int(min_sites), int(first_cut), C.byref(n), None))
+    out = np.zeros((n.value, 8), dtype=np.int32)
+    _check(lib.dyson_recursive_boxes(C.byref(geom), int(min_sites), int(first_cut), C.byref(n), out.ctypes.data))
+    return out
+
+
+def dyson_recursive_plan_destroy(rplan):
+    _check(load().dyson_recursive_plan_destroy(rplan))
+
+
+def dyson_recursive_plan_info(rplan):
+    lv, bx, lf, pl = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+    by = C.c_size_t()
+    _check(load().dyson_recursive_plan_info(rplan, C.addressof(lv), C.addressof(bx), C.addressof(lf),
+                                            C.addressof(pl), C.addressof(by)))
+    return dict(levels=lv.value, boxes=bx.value, leaves=lf.value, plans=pl.value, bytes=by.value)
+
+
+def dyson_recursive_solve(rplan, K, N, omega, V, sigma, q1, diagG, status=None, stream=None):
+    """Arguments as dyson_solve; N = Lx * Ly of the recursive plan's lattice."""
+    mk = _kinds(omega, V, sigma, q1, diagG, status)
+    _check(load().dyson_recursive_solve(rplan, K, _ptr(omega, "f8", K), _ptr(V, "f8", N), _ptr(sigma, "c16", K * N),
+                                        _ptr(q1, "f8", N), _ptr(diagG, "c16", K * N), _ptr(status, "i4", K),
+                                        mk, _stream(stream)))
+
+
+class RecursivePlan:
+    """Owning wrapper of a recursive-decomposition plan (2D)."""
+
+    def __init__(self, L, t=-1.0, mu=0.0, k_max=16, precision=DYSON_FP64, max_freqs=1, min_sites=64,
+                 first_cut=DYSON_CUT_X, streams=0, **kw):
+        if len(L) != 2:
+            raise ValueError("the recursive decomposition is defined for 2D lattices")
+        self.geom = make_geometry(L, t, mu, 2, k_max, precision, max_freqs, **kw)
+        self.L, self.N = tuple(L), int(np.prod(L))
+        self.handle = dyson_recursive_plan_create(self.geom, min_sites, first_cut, streams)
+
+    def close(self):
+        if self.handle is not None:
+            dyson_recursive_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        return dyson_recursive_plan_info(self.handle)
+
+    def solve(self, omega, V, sigma, q1, diagG=None, status=None, stream=None):
+        K = len(omega)
+        if diagG is None:
+            diagG = np.zeros((K, self.N), dtype=np.complex128)
+        dyson_recursive_solve(self.handle, K, self.N, omega, V, sigma, q1, diagG, status, stream)
+        return diagG
 
 
 class Plan:
