@@ -112,3 +112,28 @@ def test_recursive_device_buffers_repeat_bitwise():
     torch.cuda.synchronize()
     assert np.array_equal(out.cpu().numpy(), a)
     assert int(st.abs().sum()) == 0
+
+
+@pytest.mark.parametrize("precision,tol_trunc,tol_exact", [(D.DYSON_FP64, TOL_TRUNC_FP64, TOL_FP64),
+                                                           (D.DYSON_MIXED, TOL_MIXED, TOL_MIXED)])
+def test_recursive_real_axis(precision, tol_trunc, tol_exact):
+    """Real frequencies w + i eta (the remark after Eq. 1; eta = 0.1, w across the band):
+    every box plan takes eta from the geometry.  Rank 6: against the oracle's recursion
+    on the same diagonal (a 1e-13 perturbation of q1 moves it by at most 3.5e-11 here);
+    rank 30 (past every box's closure): against the exact diagonal."""
+    eta = 0.1
+    w = wl((20, 18), 2, 6, K=3, seed=6)
+    omega, V, sigma, q1 = I.make_inputs(w, axis="real")
+    zs = [O.dyson_diagonal_real(omega[k], eta, w.mu, V, sigma[k]) for k in range(3)]
+    for k, tol in ((6, tol_trunc), (30, tol_exact)):
+        rp = D.RecursivePlan(w.L, w.t, w.mu, k, precision, max_freqs=3, min_sites=40, eta=eta)
+        st = np.zeros(3, dtype=np.int32)
+        out = rp.solve(omega, V, sigma, q1, status=st)
+        for kf in range(3):
+            if k == 6:
+                ref = O.recursive_diag(w.L, w.t, zs[kf], q1, k, min_sites=40)
+            else:
+                ref = O.exact_diag(w.L, OPEN[:2], w.t, zs[kf])
+            assert relerr(out[kf], ref) <= tol, (k, kf)
+        assert np.all(st == (D.DYSON_ST_TERMINATED if k == 30 else 0))
+        rp.close()
