@@ -334,6 +334,19 @@ def side_measurements(a, dev, stream):
 
 
 # ----------------------------------------------------------------- our arm
+def aggregate_ranks(total_ms, units_per_step, steps, world, device="cpu"):
+    """(ms per step, whole-job units/s) of `world` replicas that each processed
+    units_per_step units per step for `steps` steps in total_ms: the job's time is
+    the slowest rank's (MAX over ranks), its work the sum over ranks."""
+    if world > 1:
+        import torch
+        tt = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    ms_per_step = total_ms / steps
+    return ms_per_step, world * units_per_step / (ms_per_step / 1e3)
+
+
 def run_ours(a, rank, world, local_rank):
     import numpy as np
     import torch
@@ -389,12 +402,7 @@ def run_ours(a, rank, world, local_rank):
     clk = clocks.stop() if clocks else None
     step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(a.steps)]
     total_ms = evs[0].elapsed_time(evs[-1])
-    if world > 1:
-        tt = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(tt.item())
-    ms_per_step = total_ms / a.steps
-    value = world * w.K * w.N / (ms_per_step / 1e3)
+    ms_per_step, value = aggregate_ranks(total_ms, w.K * w.N, a.steps, world, dev)
 
     # kernel profile of the last timed step (events captured inside the graph)
     kinds, kms = D.dyson_profile_read(plan.handle)
@@ -510,12 +518,9 @@ def run_ours(a, rank, world, local_rank):
         t0 = time.perf_counter()
         for _ in range(n_e2e):
             D.dyson_solve(plan.handle, w.K, h_om, h_V, h_sg, h_q, h_out, h_st, ss)
-        e2e_s = (time.perf_counter() - t0) / n_e2e
-        if world > 1:
-            tt = torch.tensor([e2e_s], device=dev)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            e2e_s = float(tt.item())
-        e2e = dict(value=world * w.K * w.N / e2e_s, unit=UNIT,
+        e2e_ms, e2e_value = aggregate_ranks((time.perf_counter() - t0) * 1e3, w.K * w.N, n_e2e, world, dev)
+        e2e_s = e2e_ms / 1e3
+        e2e = dict(value=e2e_value, unit=UNIT,
                    h2d_bytes_per_step=int(h_om.nbytes + h_V.nbytes + h_sg.nbytes + h_q.nbytes),
                    d2h_bytes_per_step=int(h_out.nbytes + h_st.nbytes), ms_per_step=e2e_s * 1e3)
     plan.close()
