@@ -451,13 +451,17 @@ def run_ours(a, rank, world, local_rank):
                 basis="achieved = algorithmic bytes (flops) of all X-matvec launches of a step / "
                       "the union of their intervals; traffic = ncu DRAM bytes of those launches per step")
     roof["share_of_step"] = float(xm_union_ms / ms_per_step) if ms_per_step > 0 else None
-    # the Lanczos step (row a7/a8): CGS2 reads the basis three times per step (g = Q^T u;
-    # r1 = u - Q g with h = Q^T r1 in the same pass; r = r1 - Q h), plus ~6 vectors
-    # (u three times, q_{j+1} written, the running diagonal read and written); complex128
-    # entries of 16 B per site.  A frequency that ran n steps moves sum_{j=1..n} (3 j + 6) N 16 B.
+    # the Lanczos step (row a7/a8), complex128-sized entries of 16 B per site.  The
+    # FP64 form's CGS2 reads the basis three times per step (g = Q^T u; r1 = u - Q g
+    # with h = Q^T r1 in the same pass; r = r1 - Q h); the mixed form's takes h from
+    # the Gram matrix of the basis and reads it twice (g = Q^T u; r = u - Q (g + h)
+    # with the next Gram column Q^T r in the same pass).  Plus ~6 vectors (u, q_j,
+    # q_{j-1}, r written, the running diagonal read and written).  A frequency that
+    # ran n steps moves sum_{j=1..n} (reads j + 6) N 16 B.
     lz = kms[kinds == 4]
     steps_k = np.asarray(info["steps"], dtype=np.float64)
-    lz_bytes = float(sum((3.0 * n * (n + 1) / 2 + 6.0 * n) * w.N * 16.0 for n in steps_k))
+    lz_reads = 2.0 if (prec == D.DYSON_MIXED and w.k <= 64) else 3.0
+    lz_bytes = float(sum((lz_reads * n * (n + 1) / 2 + 6.0 * n) * w.N * 16.0 for n in steps_k))
     lz_union = union_ms(t0[kinds == 4], t1[kinds == 4])
     lz_ach = lz_bytes / (lz_union / 1e3) / 1e9 if lz_union > 0 else float("nan")
     roof_lz = dict(bound="hbm", achieved=lz_ach, peak=hbm_peak, unit="GB/s", frac=lz_ach / hbm_peak,
@@ -465,8 +469,10 @@ def run_ours(a, rank, world, local_rank):
                    kernel="k_lanczos_dd" if prec == D.DYSON_MIXED else "k_lanczos", peak_source=peak_src,
                    per_step_algorithmic_bytes=lz_bytes, launches_per_step=int(len(lz)),
                    union_ms_per_step=lz_union, mean_launch_ms=float(lz.mean()) if len(lz) else None,
-                   basis="three reads of the basis per Lanczos step (CGS2) + 6 vectors, "
-                         "complex128, over the union of the step's Lanczos launch intervals")
+                   basis=("two reads of the basis per Lanczos step (CGS2, second-pass coefficients "
+                          "from the Gram matrix)" if lz_reads == 2.0 else
+                          "three reads of the basis per Lanczos step (CGS2)") +
+                         " + 6 vectors, complex128, over the union of the step's Lanczos launch intervals")
     phases = {D.KERNEL_NAMES[int(k)]: round(float(kms[kinds == k].sum()), 3) for k in sorted(set(kinds))}
     tuning = D.dyson_plan_tuning(plan.handle)
 

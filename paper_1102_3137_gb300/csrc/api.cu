@@ -145,7 +145,7 @@ int build_part(const dyson_geometry* in, Part* out, bool gpu) {
 enum {
   B_V, B_OMEGA, B_SIGMA, B_Q1, B_DD2NAT, B_G, B_G64, B_DIAGB, B_Q, B_ACC, B_U, B_V1, B_V2, B_V3,
   B_YSCR, B_BND, B_IFV, B_PRE, B_LAN, B_MAXT, B_ST, B_OUT, B_STATUS, B_SWEEPS, B_FWORK, B_OFFB, B_OFF2,
-  B_LPT, B_LPM, B_LPG, B_LPV, B_HDIAG, B_LPW, B_COUNT
+  B_LPT, B_LPM, B_LPG, B_LPV, B_HDIAG, B_LPW, B_GRAM, B_COUNT
 };
 
 size_t layout(const Geo& g, int K, bool mixed, size_t off[B_COUNT]) {
@@ -187,6 +187,7 @@ size_t layout(const Geo& g, int K, bool mixed, size_t off[B_COUNT]) {
   sz[B_LPV] = (g.lpre && g.T == 1 && g.Lx > DY_LPRE_MAXLX) ? Kz * g.p * 2 * (size_t)g.Lx * g.W * sizeof(cxf) : 0;
   sz[B_LPW] = (g.lpre && g.T > 1) ? (size_t)DY_FACTOR_CTAS * 2 * g.W * 2 * (size_t)g.Lx * g.T * sizeof(cxf) : 0;
   sz[B_HDIAG] = mixed ? Kz * Ndd * sizeof(cxd) : 0;
+  sz[B_GRAM] = g.qsplit ? Kz * (size_t)(g.k_max + 1) * (g.k_max + 1) * sizeof(cxd) : 0;
   size_t o = 0;
   for (int k = 0; k < B_COUNT; ++k) {
     off[k] = o;
@@ -383,6 +384,7 @@ Bufs sub_bufs(const Geo& g, const Bufs& b, bool mixed, int k0) {
   s.lpm = adv(reinterpret_cast<char*>(b.lpm), K0 * (g.p > 1 ? g.p - 1 : 0) * A2 * cs);
   s.lpg = b.lpg ? b.lpg + K0 * g.p * nsub * g.W : nullptr;
   s.lpv = b.lpv ? b.lpv + K0 * g.p * 2 * (size_t)g.Lx * g.W : nullptr;
+  s.gram = b.gram ? b.gram + K0 * (size_t)(g.k_max + 1) * (g.k_max + 1) : nullptr;
   return s;
 }
 
@@ -621,6 +623,7 @@ int dyson_plan_create(const dyson_geometry* geom, dyson_plan* out) {
   b.lpg = p->g.lpre ? at<cxf>(p, B_LPG) : nullptr;
   b.lpv = (p->g.lpre && p->g.T == 1 && p->g.Lx > DY_LPRE_MAXLX) ? at<cxf>(p, B_LPV) : nullptr;
   b.lpw = (p->g.lpre && p->g.T > 1) ? at<cxf>(p, B_LPW) : nullptr;
+  b.gram = p->g.qsplit ? at<cxd>(p, B_GRAM) : nullptr;
   p->status_d = at<int>(p, B_STATUS);
   p->profile = false;
   p->tuned = false;

@@ -246,6 +246,8 @@ struct Bufs {
   cx<float>* lpv;       // [K][p][2][Lx][W] boundary columns of the surface recursion (lpre, Lx > 160)
   cx<float>* lpw;       // [DY_FACTOR_CTAS][2][W][2 Lx T] boundary-column chains of the 3D slab
                         // surface recursion (lpre with T > 1), not per frequency
+  cxd* gram;            // [K][k_max+1][k_max+1] Gram matrix q_l^T q_m of the stored basis, entry
+                        // (l, m) at m (k_max+1) + l for l < m (double-float Lanczos step), or null
 };
 
 // interface Krylov vector slots inside ifv

@@ -7,25 +7,30 @@
 // passes over it read the split form directly; the X-matvec output u, the
 // running diagonal and every scalar of T stay in binary64.  What moves off the
 // binary64 pipe (GB300 issues binary32 FMAs at ~64x its binary64 rate) is the
-// arithmetic of the three passes over Q: products accumulated with
+// arithmetic of the passes over Q: products accumulated with
 // TwoProduct/TwoSum (~2^-47 relative per operation); u is split by integer
 // operations where it is read.
 //
-// Classical Gram-Schmidt twice, with the three-term part folded in:
+// Classical Gram-Schmidt twice, with the three-term part folded in and the
+// second pass's coefficients taken from the Gram matrix of the stored basis:
 //   pass A:  g  = Q_j^T u                     (alpha_j = g_j)
-//   pass B:  r1 = u - Q_j g,   h = Q_j^T r1   (r1 kept per tile only)
-//   pass C:  r  = u - Q_j (g + h)             (formed in binary64, stored split)
-// In exact arithmetic r1 = u - alpha_j q_j - beta_j q_{j-1} - Q_j h1 with
-// h1 = Q_j^T (u - alpha_j q_j - beta_j q_{j-1}) = g - alpha_j e_j - beta_j e_{j-1},
-// i.e. the first Gram-Schmidt pass of the recurrence's residual; pass C is
-// the second pass.  Three reads of Q per step instead of four.
-//
+//            h  = g - M g,  M = Q_j^T Q_j     (M kept per frequency, binary64)
+//   pass B:  r  = u - Q_j (g + h)             (formed in binary64, stored split)
+//            M's next column: Q_j^T r / beta_{j+1}
+// In exact arithmetic h = Q_j^T (u - Q_j g) is the second pass's coefficient
+// vector, so r is the classical Gram-Schmidt residual orthogonalised twice;
+// reading Q_j^T Q_j from M instead of re-projecting u - Q_j g saves a sweep
+// over the basis (two reads of Q per step instead of three, three multiply-
+// accumulates per basis entry instead of four).  With the unit diagonal of M
+// exact, M - I holds the basis's measured loss of orthogonality, which h
+// removes to second order (one-reduce CGS2 in the Gram-matrix form); the
+// remaining error is the rounding of g, ~2^-47 ||u|| / |beta_{j+1}|.
 // Thread layout.  The CTA's part of the DD layout is walked in groups of
-// TG = 128 consecutive entries.  Per-site sums over the basis (r1 and r) run
-// one thread per site along l (two threads per site in pass B, even and odd l),
-// reading each vector's entries coalesced across the warp.  Per-vector sums
-// (g and h) run one warp per eight vectors l = w + 8m, the lanes over the
-// group's sites, with the group's u (pass A) or r1 (pass B) staged in shared
+// TG = 128 consecutive entries.  The per-site sum over the basis (r) runs two
+// threads per site along l (even and odd l), reading each vector's entries
+// coalesced across the warp.  Per-vector sums (g and the Gram column) run one
+// warp per eight vectors l = w + 8m, the lanes over the
+// group's sites, with the group's u (pass A) or r (pass B) staged in shared
 // memory; pass B re-reads the group's basis entries right after its per-site
 // half, from L2.  Per-vector totals are warp-shuffled, then summed over the
 // cluster's CTAs in rank order in binary64, so every CTA of a frequency holds
@@ -44,6 +49,9 @@ static_assert(DY_THREADS == 2 * TG, "two threads per site of a group");
 // unit roundoff as TERM_TOL and BRK_TOL are of binary64's (2^-47 / 2^-53 = 64).
 constexpr double TERM_TOL_DD = 64.0 * TERM_TOL;
 constexpr double BRK_TOL_DD = 64.0 * BRK_TOL;
+// A step re-projects r when ||r|| < REORTH_ETA ||u||: the Gram form's orthogonality is
+// ~2^-47 ||u|| / ||r||, held below ~1.5e-13 this way.
+constexpr double REORTH_ETA = 0.05;
 
 __device__ __forceinline__ cdfl czero() { return {dfl(0.f, 0.f), dfl(0.f, 0.f)}; }
 
@@ -164,6 +172,8 @@ __global__ void __launch_bounds__(DY_THREADS, 2) k_lanczos_dd(Geo g, Bufs b, int
   const cxd* u = b.u + (size_t)kf * Ndd;
   cxd* acc = b.acc + (size_t)kf * Ndd;
   cxd* lan = b.lan + (size_t)kf * (g.k_max + g.nb) * 2;
+  const int K1 = g.k_max + 1;
+  cxd* gram = b.gram + (size_t)kf * K1 * K1;
   const cxd beta_j = (j > 0) ? lan[2 * j + 1] : cxd{0, 0};
   // read before the first cluster barrier: CTA 0 updates it once all CTAs passed the last one
   const double maxT_prev = b.maxT[kf];
@@ -201,18 +211,33 @@ __global__ void __launch_bounds__(DY_THREADS, 2) k_lanczos_dd(Geo g, Bufs b, int
   }
   cluster_vec_sum(cl, sm, vphase, P, j + 1);
   const cxd alpha = sm.vres[j];
+  for (int l = tid; l <= j; l += DY_THREADS) sm.gv[l] = sm.vres[l];
+  __syncthreads();
+  // ---- second Gram-Schmidt coefficients from the Gram matrix M = Q_j^T Q_j of the
+  // stored basis: h = Q_j^T (u - Q_j g) = g - M g, so g + h = g - (M - I) g (the unit
+  // diagonal of M taken as exact; binary64)
   for (int l = tid; l <= j; l += DY_THREADS) {
-    sm.gv[l] = sm.vres[l];
-    sm.coef[l] = csplit(sm.vres[l]);
+    cxd s = {0, 0};
+    for (int m = 0; m <= j; ++m) {
+      if (m == l) continue;
+      const cxd e = l < m ? gram[(size_t)m * K1 + l] : gram[(size_t)l * K1 + m];
+      s = cfma(e, sm.gv[m], s);
+    }
+    sm.coef[l] = csplit(sm.gv[l] - s);
   }
   __syncthreads();
 
-  // ---- pass B: r1 = u - Q g per site (two threads per site), then h = Q^T r1
+  // ---- pass B: r = u - Q (g + h) per site (two threads per site, even and odd l),
+  // finished in binary64 and stored split, with r^T r, ||r||^2 and the Eq. 9
+  // three-vector update; then h' = Q^T r (warp w: vectors w + 8m, lanes over the
+  // group's sites, r staged in shared memory), the Gram column of the next vector
+  cxd v2[3] = {{0, 0}, {0, 0}, {0, 0}};   // r^T r, ||r||^2, ||u||^2
+  const cdfl ad = csplit(alpha), bd = csplit(2.0 * beta_j);
+  const int c0 = tid & (TG - 1), half = tid / TG;
   {
     cdfl a[LPW];
 #pragma unroll
     for (int m = 0; m < LPW; ++m) a[m] = czero();
-    const int c0 = tid & (TG - 1), half = tid / TG;
     for (int gr = part; gr < ngrp; gr += SPLIT) {
       const int e0 = gr * TG;
       {
@@ -221,6 +246,34 @@ __global__ void __launch_bounds__(DY_THREADS, 2) k_lanczos_dd(Geo g, Bufs b, int
         if (e < n) s = basis_sum(Q, Ndd, own_idx(g, i, e, nsub), j, half, 2, sm.coef);
         sm.st[half][c0] = s;
       }
+      __syncthreads();
+      cdfl rd = czero();
+      if (half == 0 && e0 + c0 < n) {
+        const size_t k = own_idx(g, i, e0 + c0, nsub);
+        const cdfl tot = cadd(sm.st[0][c0], sm.st[1][c0]);
+        const cxd uv = u[k];
+        const cxd rv = {(uv.x - f2d_bits(tot.x.hi)) - f2d_bits(tot.x.lo),
+                        (uv.y - f2d_bits(tot.y.hi)) - f2d_bits(tot.y.lo)};
+        rd = csplit(rv);
+        r[k] = rd;
+        v2[0] = cfma(rv, rv, v2[0]);
+        v2[1].x += cabs2(rv);
+        v2[2].x += cabs2(uv);
+        const cdfl qjd = qj[k];
+        cdfl sq = czero(), d = czero();
+        cmac(sq, qjd, qjd);
+        cmac(d, ad, cnorm(sq));
+        if (qm) {
+          cdfl pr = czero();
+          cmac(pr, qm[k], qjd);
+          cmac(d, bd, cnorm(pr));
+        }
+        d = cnorm(d);
+        const cxd av = acc[k];
+        acc[k] = cxd{(av.x + f2d_bits(d.x.hi)) + f2d_bits(d.x.lo), (av.y + f2d_bits(d.y.hi)) + f2d_bits(d.y.lo)};
+      }
+      __syncthreads();                     // both halves have read st before it is overwritten
+      if (half == 0) sm.st[0][c0] = rd;
       __syncthreads();
       for (int c = lane; c < TG; c += 32) {
         const int e = e0 + c;
@@ -232,66 +285,64 @@ __global__ void __launch_bounds__(DY_THREADS, 2) k_lanczos_dd(Geo g, Bufs b, int
           const int l = w + DY_WARPS * m;
           qv[m] = l <= j ? Q[(size_t)l * Ndd + k] : czero();
         }
-        const cdfl r1 = csub(csub(csplit(u[k]), sm.st[0][c]), sm.st[1][c]);
+        const cdfl rc = sm.st[0][c];
 #pragma unroll
         for (int m = 0; m < LPW; ++m)
-          if (w + DY_WARPS * m <= j) cmac(a[m], qv[m], r1);
+          if (w + DY_WARPS * m <= j) cmac(a[m], qv[m], rc);
       }
       __syncthreads();
     }
     put_partials(sm, vphase, j, a);
   }
-  cluster_vec_sum(cl, sm, vphase, P, j + 1);
-  for (int l = tid; l <= j; l += DY_THREADS) sm.coef[l] = csplit(sm.gv[l] + sm.vres[l]);   // g + h
-  __syncthreads();
-
-  // ---- pass C (one thread per site): r = u - Q (g + h) in binary64, r^T r,
-  // ||r||^2, and the Eq. 9 three-vector update
-  cxd v2[2] = {{0, 0}, {0, 0}};
-  const cdfl ad = csplit(alpha), bd = csplit(2.0 * beta_j);
-  const int c0 = tid & (TG - 1), half = tid / TG;            // the two halves take alternate groups
-  for (int gr = part + half * SPLIT; gr < ngrp; gr += 2 * SPLIT) {
-    {
+  cluster_vec_sum(cl, sm, vphase, P, j + 1);   // sm.vres[l] = q_l^T r
+  cluster_sum<3>(cl, rs, phase, P, v2);
+  cxd rr = v2[0];
+  double rn2 = v2[1].x;
+  // ---- pass C, only when r lost most of u (||r|| < REORTH_ETA ||u||, near an
+  // invariant subspace): the Gram form leaves r's rounding error ~2^-47 ||u|| in
+  // place, so project r once more onto the complement, r -= Q (Q^T r), as the
+  // classical second pass would (the selective test of Daniel, Gragg, Kaufman and
+  // Stewart, 1976); the next vector's Gram column is then zero to working accuracy
+  const bool reorth = rn2 < REORTH_ETA * REORTH_ETA * v2[2].x;
+  if (reorth) {
+    for (int l = tid; l <= j; l += DY_THREADS) sm.coef[l] = csplit(sm.vres[l]);
+    __syncthreads();
+    cxd w2[2] = {{0, 0}, {0, 0}};
+    for (int gr = part + half * SPLIT; gr < ngrp; gr += 2 * SPLIT) {
       const int e = gr * TG + c0;
       if (e >= n) continue;
       const size_t k = own_idx(g, i, e, nsub);
       const cdfl tot = basis_sum(Q, Ndd, k, j, 0, 1, sm.coef);
-      const cxd uv = u[k];
-      const cxd rv = {(uv.x - f2d_bits(tot.x.hi)) - f2d_bits(tot.x.lo),
-                      (uv.y - f2d_bits(tot.y.hi)) - f2d_bits(tot.y.lo)};
-      r[k] = csplit(rv);
-      v2[0] = cfma(rv, rv, v2[0]);
-      v2[1].x += cabs2(rv);
-      const cdfl qjd = qj[k];
-      cdfl sq = czero(), d = czero();
-      cmac(sq, qjd, qjd);
-      cmac(d, ad, cnorm(sq));
-      if (qm) {
-        cdfl pr = czero();
-        cmac(pr, qm[k], qjd);
-        cmac(d, bd, cnorm(pr));
-      }
-      d = cnorm(d);
-      const cxd av = acc[k];
-      acc[k] = cxd{(av.x + f2d_bits(d.x.hi)) + f2d_bits(d.x.lo), (av.y + f2d_bits(d.y.hi)) + f2d_bits(d.y.lo)};
+      const cdfl rn = csub(r[k], tot);
+      r[k] = rn;
+      const cxd rv = cwiden(rn);
+      w2[0] = cfma(rv, rv, w2[0]);
+      w2[1].x += cabs2(rv);
     }
+    cluster_sum<2>(cl, rs, phase, P, w2);
+    rr = w2[0];
+    rn2 = w2[1].x;
   }
-  cluster_sum<2>(cl, rs, phase, P, v2);
-  const cxd rr = v2[0];
   const cxd beta = csqrt_principal(rr);
   const double maxT = fmax(maxT_prev, sqrt(cabs2(alpha)));
   const double babs = sqrt(cabs2(beta));
   int done = 0, flag = 0;
   if (j == g.k_max - 1) {
     done = 1;
-  } else if (sqrt(v2[1].x) <= TERM_TOL_DD * maxT) {     // r vanished: invariant subspace
+  } else if (sqrt(rn2) <= TERM_TOL_DD * maxT) {         // r vanished: invariant subspace
     done = 1;
     flag = 1;
-  } else if (sqrt(cabs2(rr)) <= BRK_TOL_DD * v2[1].x) {  // r != 0, (r, r)_C ~ 0: breakdown
+  } else if (sqrt(cabs2(rr)) <= BRK_TOL_DD * rn2) {     // r != 0, (r, r)_C ~ 0: breakdown
     done = 1;
     flag = 2;
   }
   if (!done) {
+    // Gram column of q_{j+1} = r / beta: q_l^T q_{j+1} = (q_l^T r) / beta, l <= j
+    if (blockIdx.x == 0) {
+      const cxd ibd = cinv(beta);
+      for (int l = tid; l <= j; l += DY_THREADS)
+        gram[(size_t)(j + 1) * K1 + l] = reorth ? cxd{0, 0} : sm.vres[l] * ibd;
+    }
     // q_{j+1} = r / beta in double-float
     const cdfl ib = csplit(cinv(beta));
     for (int gr = part + half * SPLIT; gr < ngrp; gr += 2 * SPLIT) {
