@@ -71,9 +71,14 @@ extern "C" {
 
 /* precision forms */
 #define DYSON_FP64 0   /* every step in complex128 */
-#define DYSON_MIXED 1  /* subdomain recursions and sweeps in complex64 with FP32 accumulation;
-                          Lanczos, re-orthogonalisation, the tridiagonal T_k and the
-                          iterative-refinement residuals in FP64 */
+#define DYSON_MIXED 1  /* sweeps, inner interface solves and the preconditioner in complex64
+                          with FP32 accumulation, every solve refined against FP64 residuals;
+                          diag(B^-1) from a double-float (two binary32, ~47-bit) recursion;
+                          the Lanczos step's re-orthogonalisation in double-float arithmetic
+                          on a double-float basis (k_max <= 64, scalar Lanczos; binary64
+                          otherwise), its scalars, T_k and the diagonal in binary64.  Within
+                          ~1e-6 of DYSON_FP64 where the truncated result is not amplified by
+                          rounding */
 
 /* interface preconditioner of the H solves (dyson_geometry.precond) */
 #define DYSON_PRECOND_AUTO 0    /* exact layer blocks where they apply, else banded */
