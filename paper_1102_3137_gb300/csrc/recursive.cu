@@ -82,14 +82,15 @@ __global__ void k_rec_gather(RMap m, int N, const double* V, const cxd* sigma, c
 // out += src at the box's sites (src in the plan's subdomain-first layout), and
 // the box's status flags folded into the running ones: every flag but
 // TERMINATED OR-ed, TERMINATED AND-ed (the result is exact only when every box
-// closed its Krylov space).
+// closed its Krylov space).  The boxes of a level are disjoint, so the adds never
+// meet; the flags are shared by all of them and folded atomically.
 __global__ void k_rec_add(RMap m, int N, int Ndd, const int* dd2nat, const cxd* src, cxd* out,
                           const int* st_box, int* st_or, int* st_and) {
   const int kf = blockIdx.y;
-  if (st_box && blockIdx.x == 0 && threadIdx.x == 0) {
+  if (st_box && blockIdx.x == 0 && threadIdx.x == 0) {   // boxes of a level run concurrently
     const int s = st_box[kf];
-    st_or[kf] |= s & ~DYSON_ST_TERMINATED;
-    st_and[kf] &= s;
+    atomicOr(st_or + kf, s & ~DYSON_ST_TERMINATED);
+    atomicAnd(st_and + kf, s);
   }
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < Ndd; k += gridDim.x * blockDim.x) {
     const int nat = dd2nat[k];
