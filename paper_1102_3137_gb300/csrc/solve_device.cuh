@@ -118,7 +118,9 @@ __device__ void block_sum(RedSmem& rs, cxd (&v)[NV]) {
 // g_s blocks stream from HBM into a ring of shared-memory slots with 1D bulk
 // copies (cp.async.bulk, completion counted on an mbarrier per slot).  Every
 // wait is bounded by the global timer: on time-out the kernel records
-// DYSON_ST_WAIT_TIMEOUT and goes on (no CTA may leave its cluster's barriers).
+// DYSON_ST_WAIT_TIMEOUT and goes on (no CTA may leave its cluster's barriers);
+// the thread then waits on the ring no more in that sweep, and no thread of the
+// CTA waits in its later sweeps.
 constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;   // 2 s
 constexpr int ST_WAIT_TIMEOUT = DYSON_ST_WAIT_TIMEOUT;
 
@@ -163,6 +165,17 @@ __device__ __forceinline__ bool mbar_wait_for(uint64_t* bar, uint32_t parity, un
 }
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   return mbar_wait_for(bar, parity, WAIT_LIMIT_NS);
+}
+// A copy-ring wait that gives up for good: once one of this thread's waits has
+// run out (dead, a register flag, seeded from the CTA's shared flag at the start
+// of each sweep), its later waits return at once, so a lost copy costs the
+// kernel one wait limit per thread and sweep instead of one per slice step.
+__device__ __forceinline__ void ring_wait(uint64_t* bar, uint32_t parity, bool& dead, int* err) {
+  if (dead) return;
+  if (!mbar_wait(bar, parity)) {
+    dead = true;
+    *err = 1;
+  }
 }
 
 // Per-CTA copy pipeline: S slots of one W x W block each, one mbarrier per slot.
@@ -439,6 +452,7 @@ template <int WF>
 __device__ void sweep_pair(const Geo& g, int i, const SweepArgs<float>& a, cxf* sm, Pipe& pp,
                            unsigned long long* cnt) {
   using C = cxf;
+  bool dead = *pp.err != 0;              // an earlier wait of this CTA ran out
   const int W = g.W, Lx = g.Lx, m = Lx / 2, qR = Lx - 1 - m;
   const int NLL = 2 * m + 1, NLR = 2 * qR;
   C* zL = sm;                            // [2][W] left chain z
@@ -468,7 +482,7 @@ __device__ void sweep_pair(const Geo& g, int i, const SweepArgs<float>& a, cxf* 
   // barrier, so the copy that overwrites it needs no proxy fence.
   auto stepL = [&](int n, const C* z, C& p0, C& p1) {
     const int sl = curL;
-    if (!mbar_wait(pp.bar + sl, phL)) *pp.err = 1;
+    ring_wait(pp.bar + sl, phL, dead, pp.err);
     pair_product<WF>(ring + (size_t)sl * WW, z, W, lane, p0, p1);
     __syncwarp();
     if (lane == 0 && n + SL < NLL) issue_at(sl, sliceL(n + SL));
@@ -479,7 +493,7 @@ __device__ void sweep_pair(const Geo& g, int i, const SweepArgs<float>& a, cxf* 
   };
   auto stepR = [&](int n, const C* z, C& p0, C& p1) {
     const int sl = curR;
-    if (!mbar_wait(pp.bar + sl, phR)) *pp.err = 1;
+    ring_wait(pp.bar + sl, phR, dead, pp.err);
     pair_product<WF>(ring + (size_t)sl * WW, z, W, lane, p0, p1);
     __syncwarp();
     if (lane == 0 && n + SR < NLR) issue_at(sl, sliceR(n + SR));
@@ -683,6 +697,7 @@ __device__ void sweep(const Geo& g, int i, const SweepArgs<R>& a, cx<R>* sm, Pip
     sweep_pair<WF>(g, i, a, sm, pp, cnt);
     return;
   }
+  bool dead = *pp.err != 0;              // an earlier wait of this CTA ran out
   const int W = g.W, Lx = g.Lx;
   const SweepLayout L = sweep_layout(W, W);
   cx<R>* zbuf = sm;                      // [2][W]: z of the current and of the next slice
@@ -729,7 +744,7 @@ __device__ void sweep(const Geo& g, int i, const SweepArgs<R>& a, cx<R>* sm, Pip
   auto product = [&](int n) -> cx<R> {
     const unsigned q = pp.seq + n;
     const int slot = (int)(q % S);
-    if (!mbar_wait(pp.bar + slot, (q / S) & 1u)) *pp.err = 1;
+    ring_wait(pp.bar + slot, (q / S) & 1u, dead, pp.err);
     const cx<R>* grow = ring + (size_t)slot * WW + (size_t)row * W;
     const cx<R>* zc = zbuf + (n & 1) * W;
     cx<R> acc = {0, 0};
@@ -806,6 +821,7 @@ __device__ void sweep(const Geo& g, int i, const SweepArgs<R>& a, cx<R>* sm, Pip
 template <typename R>
 __device__ void sweep_chunked(const Geo& g, int i, const SweepArgs<R>& a, cx<R>* sm, Pipe& pp,
                               unsigned long long* cnt) {
+  bool dead = *pp.err != 0;              // an earlier wait of this CTA ran out
   const int W = g.W, Lx = g.Lx, T = g.T, w = T * g.h[i];
   const int CR = pp.CR, NC = W / CR;
   const SweepLayout L = sweep_layout(CR, W);
@@ -865,7 +881,7 @@ __device__ void sweep_chunked(const Geo& g, int i, const SweepArgs<R>& a, cx<R>*
       const int q = n * NC + c;
       const unsigned qq = pp.seq + q;
       const int slot = (int)(qq % S);
-      if (!mbar_wait(pp.bar + slot, (qq / S) & 1u)) *pp.err = 1;
+      ring_wait(pp.bar + slot, (qq / S) & 1u, dead, pp.err);
       const cx<R>* grow = ring + (size_t)slot * CW + (size_t)lrow * W;
       cx<R> acc = {0, 0};
       if (rvalid) {
