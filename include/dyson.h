@@ -299,8 +299,9 @@ int dyson_xmatvec(dyson_plan plan, int K, const double* omega, const double* V,
  * dyson_solve (q1 [N] real).  status[K]: DYSON_ST_NO_CONVERGENCE, _BREAKDOWN
  * and _WAIT_TIMEOUT of any box OR-ed; DYSON_ST_TERMINATED only when every box
  * terminated, in which case the result is the exact diagonal.  With
- * DYSON_MEM_DEVICE the call only enqueues on `stream`; the plan's own streams
- * wait for it and it waits for them.  Calls on one recursive plan must not
+ * DYSON_MEM_DEVICE every buffer must be device (or managed) memory of the plan's
+ * device (checked before any work: DYSON_E_BAD_ARG) and the call only enqueues
+ * on `stream`; the plan's own streams wait for it and it waits for them.  Calls on one recursive plan must not
  * overlap on the GPU (they share the box plans).
  *
  * dyson_recursive_plan_info: levels of the tree, internal boxes, leaves,

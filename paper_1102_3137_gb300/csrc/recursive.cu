@@ -225,6 +225,19 @@ void destroy(dyson_rplan_s* r) {
 
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// With device buffers the kernels of every box dereference the caller's pointers
+// on the plan's device: anything else is refused before work is enqueued.
+int check_dev_ptr(const void* ptr, int dev, const char* what) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return rfail(DYSON_E_BAD_ARG, std::string("cannot query ") + what);
+  }
+  if ((at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) || at.device != dev)
+    return rfail(DYSON_E_BAD_ARG, std::string(what) + " is not device memory of the plan's device");
+  return DYSON_OK;
+}
+
 // one box: gather, solve (or factor a leaf), add its share into out
 int run_box(dyson_rplan_s* r, const RBox& b, int si, int K, const double* omega, const double* V,
             const cxd* sigma, const double* q1, cxd* out) {
@@ -423,6 +436,15 @@ int dyson_recursive_solve(dyson_rplan r, int K, const double* omega, const doubl
   if (mem_kind != DYSON_MEM_HOST && mem_kind != DYSON_MEM_DEVICE)
     return rfail(DYSON_E_BAD_ARG, "mem_kind must be DYSON_MEM_HOST or DYSON_MEM_DEVICE");
   RCK(cudaSetDevice(r->device));
+  if (mem_kind == DYSON_MEM_DEVICE) {
+    const void* ptrs[6] = {omega, V, sigma, q1, diagG, status};
+    const char* names[6] = {"omega", "V", "sigma", "q1", "diagG", "status"};
+    for (int k = 0; k < 6; ++k) {
+      if (!ptrs[k]) continue;
+      int rc = check_dev_ptr(ptrs[k], r->device, names[k]);
+      if (rc) return rc;
+    }
+  }
   cudaStream_t s = (cudaStream_t)stream;
   const size_t N = r->N;
   const double *om = omega, *Vd = V, *q1d = q1;

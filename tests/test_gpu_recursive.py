@@ -137,3 +137,17 @@ def test_recursive_real_axis(precision, tol_trunc, tol_exact):
             assert relerr(out[kf], ref) <= tol, (k, kf)
         assert np.all(st == (D.DYSON_ST_TERMINATED if k == 30 else 0))
         rp.close()
+
+
+def test_recursive_rejects_host_pointers_as_device_buffers():
+    """Device-memory calls check every pointer before any work is enqueued."""
+    import ctypes
+    w = wl((12, 10), 2, 4, K=1, seed=3)
+    omega, V, sigma, q1 = I.make_inputs(w)
+    rp = D.RecursivePlan(w.L, w.t, w.mu, 4, D.DYSON_FP64, max_freqs=1, min_sites=20)
+    out = np.zeros((1, w.N), complex)
+    rc = D.load().dyson_recursive_solve(rp.handle, 1, omega.ctypes.data, V.ctypes.data, sigma.ctypes.data,
+                                        q1.ctypes.data, out.ctypes.data, None, D.DYSON_MEM_DEVICE, None)
+    assert rc == -1 and "device memory" in D.dyson_last_error()
+    good = rp.solve(omega, V, sigma, q1)                     # the plan is still usable
+    assert np.all(np.isfinite(good)) and np.array_equal(good, rp.solve(omega, V, sigma, q1))
