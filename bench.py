@@ -60,6 +60,13 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
+def lanczos_algorithmic_bytes(steps, N, reads):
+    """Algorithmic DRAM bytes of the Lanczos steps of one solve: a frequency that ran n
+    steps read the basis `reads` times at step j (j vectors of N complex entries of 16 B)
+    plus ~6 N-vectors per step: sum over j = 1..n of (reads j + 6) N 16 B."""
+    return float(sum((reads * n * (n + 1) / 2 + 6.0 * n) * N * 16.0 for n in steps))
+
+
 def union_ms(starts, ends):
     """Total length of the union of intervals [starts[k], ends[k]]."""
     tot, cur_a, cur_b = 0.0, None, None
@@ -460,8 +467,8 @@ def run_ours(a, rank, world, local_rank):
     # ran n steps moves sum_{j=1..n} (reads j + 6) N 16 B.
     lz = kms[kinds == 4]
     steps_k = np.asarray(info["steps"], dtype=np.float64)
-    lz_reads = 2.0 if (prec == D.DYSON_MIXED and w.k <= 64) else 3.0
-    lz_bytes = float(sum((lz_reads * n * (n + 1) / 2 + 6.0 * n) * w.N * 16.0 for n in steps_k))
+    lz_reads = 2 if (prec == D.DYSON_MIXED and w.k <= 64) else 3
+    lz_bytes = lanczos_algorithmic_bytes(steps_k, w.N, lz_reads)
     lz_union = union_ms(t0[kinds == 4], t1[kinds == 4])
     lz_ach = lz_bytes / (lz_union / 1e3) / 1e9 if lz_union > 0 else float("nan")
     roof_lz = dict(bound="hbm", achieved=lz_ach, peak=hbm_peak, unit="GB/s", frac=lz_ach / hbm_peak,
@@ -470,7 +477,7 @@ def run_ours(a, rank, world, local_rank):
                    per_step_algorithmic_bytes=lz_bytes, launches_per_step=int(len(lz)),
                    union_ms_per_step=lz_union, mean_launch_ms=float(lz.mean()) if len(lz) else None,
                    basis=("two reads of the basis per Lanczos step (CGS2, second-pass coefficients "
-                          "from the Gram matrix)" if lz_reads == 2.0 else
+                          "from the Gram matrix)" if lz_reads == 2 else
                           "three reads of the basis per Lanczos step (CGS2)") +
                          " + 6 vectors, complex128, over the union of the step's Lanczos launch intervals")
     phases = {D.KERNEL_NAMES[int(k)]: round(float(kms[kinds == k].sum()), 3) for k in sorted(set(kinds))}

@@ -1,5 +1,6 @@
 """Host-side helpers of bench.py (no GPU): the union of kernel intervals used for
-the X-matvec roofline when frequency groups overlap, and the traffic record lookup."""
+the X-matvec roofline when frequency groups overlap, the Lanczos step's algorithmic
+bytes, and the traffic record lookup."""
 import json
 import os
 
@@ -26,3 +27,11 @@ def test_recorded_traffic_needs_matching_source():
             assert got is None or got == e["dram_bytes_per_step"]
             assert (got is not None) == (e["source_hash"] == bench.kernel_source_hash())
     assert bench.recorded_traffic("k_xmatvec<float>", "no such workload") is None
+
+
+def test_lanczos_algorithmic_bytes_counts_each_step():
+    N = 1000
+    for reads in (2, 3):
+        brute = sum(sum((reads * j + 6) * N * 16 for j in range(1, n + 1)) for n in (5, 1, 64))
+        assert bench.lanczos_algorithmic_bytes([5, 1, 64], N, reads) == brute
+    assert bench.lanczos_algorithmic_bytes([], N, 2) == 0.0
